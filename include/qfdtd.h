@@ -1,0 +1,172 @@
+/*
+ * qfdtd.h - C ABI of libqfdtd: the imaginary-time Schrodinger step of quantumfdtd v3
+ * (Delgado, Steinbeisser, Strickland, Weber, arXiv 2211.10185) on one GB300 GPU.
+ *
+ * The library advances a complex wavefunction psi on an N^3 lattice (spacing a) in
+ * imaginary time (Sec. 2, Eq. eq_iterat with the full H = H_K + V of Eq. eq_schro):
+ *
+ *     psi <- coef_A psi - coef_B dtau H_K psi,
+ *     coef_A = (1 - dtau V/2)/(1 + dtau V/2),  coef_B = 1/(1 + dtau V/2),
+ *
+ * (the time discretisation is deferred by the paper to its references; this
+ * Crank-Nicolson-in-V, explicit-in-H_K form is the reading implemented), with one of
+ * four kinetic terms (Sec. 2): the FDTD 7-point Laplacian under Dirichlet boundaries
+ * (Eq. HK0) or the FFT terms under periodic boundaries with the multipliers
+ * k^2/(2 a^2 m) (Eq. HK1), 4 sin^2(k/2)/(2 a^2 m) (Eq. HK2) and
+ * sqrt(4 sum sin^2(k/2) + (a m)^2)/a (Eq. HK3).  Energies are FP64 Rayleigh quotients,
+ * excited states come from Gram-Schmidt over nearby snapshots (Sec. 1), and the parity
+ * projectors are those of Sec. 3.
+ *
+ * Conventions for every call:
+ *  - Every function returns a qf_status; nothing throws or aborts across the ABI.  On
+ *    failure qf_last_error(handle) returns a NUL-terminated message owned by the handle.
+ *  - Host pointers are borrowed for the duration of the call only; the call has
+ *    finished reading or writing them when it returns.
+ *  - Device memory is owned by the caller: qf_workspace_bytes() sizes one workspace
+ *    that the caller allocates (e.g. a torch uint8 tensor) and passes to
+ *    qf_create_lattice(); the library never allocates or frees device memory.
+ *  - Host fields are FP64, interleaved (re, im), C order with x fastest: site
+ *    (ix, iy, iz) at index (iz*N + iy)*N + ix, coordinate x_i = (i - N/2) a.
+ *  - All GPU work of a handle is issued on the CUDA stream given at creation.  Calls
+ *    that return host data synchronise that stream.  A handle is not thread safe.
+ *  - N must be even, 8 <= N <= 512, and one of 8, 12, 16, 24, 32, 48, 64, 96, 128,
+ *    192, 256, 384, 512 (the FFT plans built into the library; FDTD lattices accept any
+ *    even N in [8, 1024]).  Odd N has no lattice momentum set (Sec. 2).
+ */
+#ifndef QFDTD_H
+#define QFDTD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qf_lattice qf_lattice; /* opaque, library-owned host object */
+
+typedef enum {
+  QF_OK = 0,
+  QF_EINVAL = 1,   /* bad argument (null pointer, size, enum value)                 */
+  QF_ENOMEM = 2,   /* workspace too small                                           */
+  QF_ECUDA = 3,    /* a CUDA call failed; the message names it                      */
+  QF_ESTATE = 4,   /* call out of order (e.g. step before potential/kinetic/psi)    */
+  QF_ETIMEOUT = 5, /* a bounded device wait ran out                                 */
+  QF_ENOTCONV = 6  /* qf_step_n reached max_steps before the tolerance was met      */
+} qf_status;
+
+/* Kinetic terms of Sec. 2. */
+typedef enum {
+  QF_KIN_FDTD = 0,          /* Eq. HK0, Dirichlet planes at index 0                  */
+  QF_KIN_FFT_NAIVE = 1,     /* Eq. HK1, multiplier k^2/(2 a^2 m), periodic           */
+  QF_KIN_FFT_SYMANZIK = 2,  /* Eq. HK2, multiplier 4 sin^2(k/2)/(2 a^2 m), periodic  */
+  QF_KIN_FFT_REL = 3        /* Eq. HK3, multiplier sqrt(4 sin^2(k/2) + (a m)^2)/a    */
+} qf_kinetic;
+
+/* Bulk precision: complex FP32 fields with FP64 reductions, or complex FP64 throughout. */
+typedef enum { QF_PREC_C64 = 0, QF_PREC_C128 = 1 } qf_precision;
+
+/* Parity projectors of Sec. 3. */
+typedef enum {
+  QF_P_PLUS = 0,     /* (psi(r) + psi(-r))/2                                             */
+  QF_P_MINUS = 1,    /* (psi(r) - psi(-r))/2                                             */
+  QF_P_MINUS_PK = 2  /* P^-_{p_k}: odd in axis k, even under flipping the other two; 1/4 */
+} qf_parity;
+
+typedef struct {
+  int n;              /* lattice sites per axis                                    */
+  double a;           /* lattice spacing (the paper's A), > 0                      */
+  int prec;           /* qf_precision                                              */
+  int n_snap;         /* snapshot ring length, 1..3 (Gram-Schmidt uses up to 3)    */
+} qf_lattice_desc;
+
+typedef struct {
+  double e_re, e_im;  /* Rayleigh quotient <psi|H|psi>/<psi|psi>                     */
+  double norm;        /* <psi|psi> of the measured field                              */
+  double de;          /* |E - E_previous check| (infinity before the second check)   */
+  int64_t step;       /* step index t of the measured psi_t                           */
+  double tau;         /* imaginary time of psi_t                                      */
+} qf_energy;
+
+typedef struct {
+  double dtau;        /* time step in use                                            */
+  int64_t step;       /* steps taken so far                                          */
+  double tau;         /* imaginary time reached                                      */
+  int kinetic;        /* qf_kinetic, -1 before qf_set_kinetic                         */
+  int n_snapshots;    /* snapshots currently held (<= n_snap)                        */
+  size_t workspace_bytes;
+} qf_info;
+
+/* Device workspace a lattice with this description needs (bytes, 256-byte aligned
+ * start expected).  QF_EINVAL for an unsupported description. */
+qf_status qf_workspace_bytes(const qf_lattice_desc* desc, size_t* bytes);
+
+/* Creates a lattice on the current CUDA device.  dev_ws: device pointer to at least
+ * qf_workspace_bytes() bytes, 256-byte aligned, owned by the caller and kept alive
+ * until qf_destroy_lattice.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * The fields start at zero; the potential and kinetic term are unset. */
+qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws, size_t ws_bytes, void* cuda_stream,
+                            qf_lattice** out);
+
+/* Releases the handle (never the caller's workspace).  NULL is accepted. */
+qf_status qf_destroy_lattice(qf_lattice* lat);
+
+/* V(r) of Eq. eq_schro from host FP64 arrays of N^3 values (v_im == NULL: real V,
+ * stored as real).  Complex V is the non-equilibrium case of Sec. 1. */
+qf_status qf_set_potential(qf_lattice* lat, const double* v_re, const double* v_im);
+
+/* Kinetic term (qf_kinetic), mass m > 0 (the paper's M) and time step dtau.  dtau <= 0
+ * selects 0.75 / T_max with T_max = 6/(m a^2) (HK0, HK2), 3 pi^2/(2 m a^2) (HK1),
+ * sqrt(12 + (a m)^2)/a (HK3). */
+qf_status qf_set_kinetic(qf_lattice* lat, int kinetic, double mass, double dtau);
+
+/* Live psi from a host array of 2 N^3 doubles (interleaved re, im).  Values on the
+ * Dirichlet planes are ignored by the FDTD term.  Cancels a pending renormalisation. */
+qf_status qf_set_wavefunction(qf_lattice* lat, const double* re_im);
+
+/* Copies a field to a host array of 2 N^3 doubles.  slot -1: live psi as stored;
+ * 0..2: Gram-Schmidt state i; 100 + j: snapshot j (0 = latest). */
+qf_status qf_get_wavefunction(qf_lattice* lat, int slot, double* re_im);
+
+/* Advances up to max_steps steps.  Step t maps psi_t to psi_{t+1}.  When
+ * t % check_every == 0 (check_every > 0) the energy of psi_t is measured in the same
+ * pass (FP64 sums), and the output of step t+1 is scaled by 1/sqrt(<psi_t|psi_t>).  The
+ * call returns QF_OK right after a check with |E_t - E_{t-check_every}| < tol_abs, else
+ * QF_ENOTCONV after max_steps.  After step t, when (t+1) % snap_every == 0
+ * (snap_every > 0), psi_{t+1} enters the snapshot ring.  steps_done may be NULL. */
+qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_abs, int check_every, int snap_every,
+                    int64_t* steps_done);
+
+/* Result of the last check of qf_step_n.  QF_ESTATE before the first check. */
+qf_status qf_energies(qf_lattice* lat, qf_energy* out);
+
+/* Excited states (Sec. 1): classical Gram-Schmidt with one re-orthogonalisation pass
+ * over the latest n_states snapshots (latest first, FP64 inner products), giving the
+ * states 0..n_states-1 and E_i = <v_i|H|v_i> in out[0..n_states).  1 <= n_states <=
+ * min(3, n_snap); QF_ESTATE when fewer snapshots are held. */
+qf_status qf_project_excited(qf_lattice* lat, int n_states, qf_energy* out);
+
+/* Applies a parity projector (qf_parity; axis 1..3 = x, y, z for QF_P_MINUS_PK) to the
+ * live psi (target -1) or to Gram-Schmidt state 0..2 in place and renormalises it to
+ * unit norm (a zero result stays zero).  Projection of the live psi cancels a pending
+ * renormalisation. */
+qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int target);
+
+/* Time step, counters and sizes of the handle. */
+qf_status qf_get_info(qf_lattice* lat, qf_info* out);
+
+/* Device pointer to a field (slot as in qf_get_wavefunction), for zero-copy access by
+ * the caller on the handle's stream.  Elements are complex FP32 or FP64 pairs. */
+qf_status qf_field_pointer(qf_lattice* lat, int slot, void** dev_ptr);
+
+/* Message of the last failure of this handle ("" if none); static text for NULL. */
+const char* qf_last_error(const qf_lattice* lat);
+
+/* Library version string. */
+const char* qf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QFDTD_H */

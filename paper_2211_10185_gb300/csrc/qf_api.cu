@@ -1,0 +1,575 @@
+// C ABI of libqfdtd (declared in include/qfdtd.h): lattice handles over a caller-owned
+// device workspace, the step loop with its checks and snapshots, Gram-Schmidt excited
+// states and parity projection.  Every arithmetic step on fields runs in the kernels of
+// qf_fft.cu, qf_stencil.cu and qf_fields.cu; this file only sequences them.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/qfdtd.h"
+#include "qf_common.cuh"
+
+namespace qf {
+int fft_twiddle_count(int n);
+void fft_twiddles(int n, double* re_im);
+template <typename R>
+cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, long long n, cudaStream_t st);
+}  // namespace qf
+
+using namespace qf;
+
+static const char* kVersion = "qfdtd-gb300 0.1 (sm_103a)";
+static const size_t kAlign = 256;
+static const size_t kStageBytes = size_t(32) << 20;  // host<->device staging, FP64 pairs
+
+static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t field = 0, f[2] = {0, 0}, v = 0, snaps = 0, states = 0, tw = 0, sym = 0, partials = 0, scalars = 0,
+         stage = 0, stage_bytes = 0, total = 0;
+  int max_blocks = 0;
+};
+
+static bool valid_n(int n) { return n >= 8 && n <= 1024 && n % 2 == 0; }
+
+static Layout make_layout(const qf_lattice_desc& d) {
+  Layout L;
+  const size_t sites = (size_t)d.n * d.n * d.n;
+  const size_t elem = d.prec == QF_PREC_C64 ? 8 : 16;
+  L.field = align_up(sites * elem);
+  size_t off = 0;
+  L.f[0] = off;
+  off += L.field;
+  L.f[1] = off;
+  off += L.field;
+  L.v = off;
+  off += L.field;  // complex V (a real V uses the first half)
+  L.snaps = off;
+  off += L.field * d.n_snap;
+  L.states = off;
+  off += L.field * 3;
+  L.tw = off;
+  off += align_up(2 * elem * (size_t)(d.n + 64));
+  L.sym = off;
+  off += align_up(elem * (size_t)d.n);
+  // partial sums: the largest grid of any reducing kernel
+  int mb = field_blocks();
+  if (fft_supported(d.n)) {
+    int fb = d.prec == QF_PREC_C64 ? fft_final_blocks<float>(d.n) : fft_final_blocks<double>(d.n);
+    if (fb > mb) mb = fb;
+  }
+  int sb = d.prec == QF_PREC_C64 ? stencil_blocks<float>(d.n) : stencil_blocks<double>(d.n);
+  if (sb > mb) mb = sb;
+  L.max_blocks = mb;
+  L.partials = off;
+  off += align_up((size_t)mb * kPartialStride * sizeof(double));
+  L.scalars = off;
+  off += align_up(sizeof(DevScalars));
+  L.stage_bytes = sites * 16 < kStageBytes ? sites * 16 : kStageBytes;
+  L.stage = off;
+  off += align_up(L.stage_bytes);
+  L.total = off;
+  return L;
+}
+
+struct qf_lattice {
+  qf_lattice_desc d;
+  Layout L;
+  char* ws = nullptr;
+  cudaStream_t st = nullptr;
+  long long sites = 0;
+  int live = 0;  // index of the live psi buffer (the other is scratch / next)
+  int kinetic = -1;
+  double mass = 0, dtau = 0;
+  bool have_v = false, v_real = false, have_psi = false;
+  int64_t step = 0;
+  double tau = 0;
+  bool pending_scale = false;
+  bool have_prev = false;
+  double prev_re = 0, prev_im = 0;
+  bool have_last = false;
+  qf_energy last{};
+  int snap_count = 0, snap_head = -1;  // snap_head: slot of the latest snapshot
+  bool have_states[3] = {false, false, false};
+  std::string err;
+
+  void* field(int i) const { return ws + L.f[i]; }
+  void* psi() const { return field(live); }
+  void* tmp() const { return field(1 - live); }
+  void* snap(int j) const { return ws + L.snaps + L.field * j; }
+  void* state(int i) const { return ws + L.states + L.field * i; }
+  double* partials() const { return reinterpret_cast<double*>(ws + L.partials); }
+  DevScalars* sc() const { return reinterpret_cast<DevScalars*>(ws + L.scalars); }
+  double* stage() const { return reinterpret_cast<double*>(ws + L.stage); }
+  bool c64() const { return d.prec == QF_PREC_C64; }
+};
+
+static qf_status fail(qf_lattice* lat, qf_status s, const std::string& msg) {
+  if (lat) lat->err = msg;
+  return s;
+}
+static qf_status cuda_fail(qf_lattice* lat, cudaError_t e, const char* where) {
+  return fail(lat, QF_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define QF_CUDA(lat, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(lat, e_, #call); \
+  } while (0)
+
+static bool desc_ok(const qf_lattice_desc* d) {
+  return d && valid_n(d->n) && d->a > 0 && isfinite(d->a) && (d->prec == QF_PREC_C64 || d->prec == QF_PREC_C128) &&
+         d->n_snap >= 1 && d->n_snap <= 3;
+}
+
+extern "C" qf_status qf_workspace_bytes(const qf_lattice_desc* desc, size_t* bytes) {
+  if (!desc_ok(desc) || !bytes) return QF_EINVAL;
+  *bytes = make_layout(*desc).total;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws, size_t ws_bytes, void* stream,
+                                       qf_lattice** out) {
+  if (!out) return QF_EINVAL;
+  *out = nullptr;
+  if (!desc_ok(desc) || !dev_ws) return QF_EINVAL;
+  if (reinterpret_cast<uintptr_t>(dev_ws) % kAlign) return QF_EINVAL;
+  Layout L = make_layout(*desc);
+  if (ws_bytes < L.total) return QF_ENOMEM;
+  qf_lattice* lat = new (std::nothrow) qf_lattice();
+  if (!lat) return QF_ENOMEM;
+  lat->d = *desc;
+  lat->L = L;
+  lat->ws = static_cast<char*>(dev_ws);
+  lat->st = static_cast<cudaStream_t>(stream);
+  lat->sites = (long long)desc->n * desc->n * desc->n;
+  cudaError_t e = cudaMemsetAsync(lat->ws, 0, L.total, lat->st);
+  if (e == cudaSuccess) {
+    DevScalars init{};
+    init.scale[0] = 1.0;
+    init.scale[1] = 1.0;
+    e = cudaMemcpyAsync(lat->sc(), &init, sizeof(init), cudaMemcpyHostToDevice, lat->st);
+  }
+  if (e == cudaSuccess && fft_supported(desc->n)) {
+    // per-stage twiddle table exp(-2 pi i r k/(Ns R)) in the lattice precision
+    const int cnt = fft_twiddle_count(desc->n);
+    double* tw = new double[2 * (size_t)cnt + 2];
+    fft_twiddles(desc->n, tw);
+    if (desc->prec == QF_PREC_C64) {
+      float* f = new float[2 * (size_t)cnt + 2];
+      for (int i = 0; i < 2 * cnt; ++i) f[i] = (float)tw[i];
+      e = cudaMemcpyAsync(lat->ws + L.tw, f, sizeof(float) * 2 * cnt, cudaMemcpyHostToDevice, lat->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+      delete[] f;
+    } else {
+      e = cudaMemcpyAsync(lat->ws + L.tw, tw, sizeof(double) * 2 * cnt, cudaMemcpyHostToDevice, lat->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    }
+    delete[] tw;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+  if (e != cudaSuccess) {
+    delete lat;
+    return QF_ECUDA;
+  }
+  *out = lat;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_destroy_lattice(qf_lattice* lat) {
+  if (!lat) return QF_OK;
+  cudaStreamSynchronize(lat->st);
+  delete lat;
+  return QF_OK;
+}
+
+// Uploads n doubles (host) to the staging area in chunks and runs fn(stage, first, count)
+// after each chunk.
+template <typename F>
+static qf_status staged_upload(qf_lattice* lat, const double* host, long long n, long long per_item, F fn) {
+  const long long chunk = (long long)(lat->L.stage_bytes / sizeof(double)) / per_item;
+  for (long long first = 0; first < n; first += chunk) {
+    const long long cnt = (n - first < chunk) ? n - first : chunk;
+    QF_CUDA(lat, cudaMemcpyAsync(lat->stage(), host + first * per_item, cnt * per_item * sizeof(double),
+                                 cudaMemcpyHostToDevice, lat->st));
+    QF_CUDA(lat, fn(lat->stage(), first, cnt));
+    // the staging area is reused by the next chunk
+    QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  }
+  return QF_OK;
+}
+
+extern "C" qf_status qf_set_potential(qf_lattice* lat, const double* v_re, const double* v_im) {
+  if (!lat || !v_re) return fail(lat, QF_EINVAL, "null potential");
+  const long long n = lat->sites;
+  char* vbase = lat->ws + lat->L.v;
+  qf_status s;
+  if (!v_im) {
+    s = staged_upload(lat, v_re, n, 1, [&](double* stg, long long first, long long cnt) {
+      return lat->c64() ? launch_real_from_f64<float>(reinterpret_cast<float*>(vbase) + first, stg, cnt, lat->st)
+                        : launch_real_from_f64<double>(reinterpret_cast<double*>(vbase) + first, stg, cnt, lat->st);
+    });
+  } else {
+    // real and imaginary halves of one chunk share the staging area
+    const long long chunk = (long long)(lat->L.stage_bytes / sizeof(double)) / 2;
+    s = QF_OK;
+    for (long long first = 0; first < n && s == QF_OK; first += chunk) {
+      const long long cnt = (n - first < chunk) ? n - first : chunk;
+      double* re = lat->stage();
+      double* im = lat->stage() + chunk;
+      QF_CUDA(lat, cudaMemcpyAsync(re, v_re + first, cnt * sizeof(double), cudaMemcpyHostToDevice, lat->st));
+      QF_CUDA(lat, cudaMemcpyAsync(im, v_im + first, cnt * sizeof(double), cudaMemcpyHostToDevice, lat->st));
+      cudaError_t e = lat->c64()
+                          ? launch_pack_f64<float>(reinterpret_cast<cpx<float>*>(vbase) + first, re, im, cnt, lat->st)
+                          : launch_pack_f64<double>(reinterpret_cast<cpx<double>*>(vbase) + first, re, im, cnt,
+                                                    lat->st);
+      QF_CUDA(lat, e);
+      QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+    }
+  }
+  if (s != QF_OK) return s;
+  lat->have_v = true;
+  lat->v_real = (v_im == nullptr);
+  return QF_OK;
+}
+
+static double default_dtau(int kin, double a, double m) {
+  double tmax;
+  if (kin == QF_KIN_FDTD || kin == QF_KIN_FFT_SYMANZIK) tmax = 6.0 / (m * a * a);
+  else if (kin == QF_KIN_FFT_NAIVE) tmax = 3.0 * M_PI * M_PI / (2.0 * m * a * a);
+  else tmax = sqrt(12.0 + (a * m) * (a * m)) / a;
+  return 0.75 / tmax;
+}
+
+extern "C" qf_status qf_set_kinetic(qf_lattice* lat, int kinetic, double mass, double dtau) {
+  if (!lat) return QF_EINVAL;
+  if (kinetic < QF_KIN_FDTD || kinetic > QF_KIN_FFT_REL) return fail(lat, QF_EINVAL, "unknown kinetic term");
+  if (!(mass > 0) || !isfinite(mass) || !isfinite(dtau)) return fail(lat, QF_EINVAL, "mass must be > 0");
+  if (kinetic != QF_KIN_FDTD && !fft_supported(lat->d.n))
+    return fail(lat, QF_EINVAL, "no FFT plan for this N (use 8,12,16,24,32,48,64,96,128,192,256,384,512)");
+  const double a = lat->d.a;
+  lat->kinetic = kinetic;
+  lat->mass = mass;
+  lat->dtau = dtau > 0 ? dtau : default_dtau(kinetic, a, mass);
+  if (kinetic != QF_KIN_FDTD) {
+    // per-axis symbol S[j]: k_j^2 (HK1) or 4 sin^2(k_j/2) (HK2, HK3), k_j in (-pi, pi]
+    const int n = lat->d.n;
+    double* s = new double[n];
+    for (int j = 0; j < n; ++j) {
+      const double k = 2.0 * M_PI * (double)(j <= n / 2 ? j : j - n) / (double)n;
+      s[j] = kinetic == QF_KIN_FFT_NAIVE ? k * k : 4.0 * sin(0.5 * k) * sin(0.5 * k);
+    }
+    cudaError_t e;
+    if (lat->c64()) {
+      float* f = new float[n];
+      for (int j = 0; j < n; ++j) f[j] = (float)s[j];
+      e = cudaMemcpyAsync(lat->ws + lat->L.sym, f, sizeof(float) * n, cudaMemcpyHostToDevice, lat->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+      delete[] f;
+    } else {
+      e = cudaMemcpyAsync(lat->ws + lat->L.sym, s, sizeof(double) * n, cudaMemcpyHostToDevice, lat->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    }
+    delete[] s;
+    if (e != cudaSuccess) return cuda_fail(lat, e, "symbol upload");
+  }
+  return QF_OK;
+}
+
+extern "C" qf_status qf_set_wavefunction(qf_lattice* lat, const double* re_im) {
+  if (!lat || !re_im) return fail(lat, QF_EINVAL, "null wavefunction");
+  void* dst = lat->psi();
+  qf_status s = staged_upload(lat, re_im, lat->sites, 2, [&](double* stg, long long first, long long cnt) {
+    return lat->c64() ? launch_from_f64<float>(reinterpret_cast<cpx<float>*>(dst) + first, stg, cnt, lat->st)
+                      : launch_from_f64<double>(reinterpret_cast<cpx<double>*>(dst) + first, stg, cnt, lat->st);
+  });
+  if (s != QF_OK) return s;
+  lat->have_psi = true;
+  lat->pending_scale = false;
+  return QF_OK;
+}
+
+static void* slot_ptr(qf_lattice* lat, int slot) {
+  if (slot == -1) return lat->psi();
+  if (slot >= 0 && slot < 3) return lat->have_states[slot] ? lat->state(slot) : nullptr;
+  if (slot >= 100 && slot < 100 + lat->d.n_snap) {
+    const int j = slot - 100;
+    if (j >= lat->snap_count) return nullptr;
+    const int idx = ((lat->snap_head - j) % lat->d.n_snap + lat->d.n_snap) % lat->d.n_snap;
+    return lat->snap(idx);
+  }
+  return nullptr;
+}
+
+extern "C" qf_status qf_get_wavefunction(qf_lattice* lat, int slot, double* re_im) {
+  if (!lat || !re_im) return fail(lat, QF_EINVAL, "null output");
+  void* src = slot_ptr(lat, slot);
+  if (!src) return fail(lat, QF_ESTATE, "slot holds no field");
+  const long long chunk = (long long)(lat->L.stage_bytes / sizeof(double)) / 2;
+  for (long long first = 0; first < lat->sites; first += chunk) {
+    const long long cnt = (lat->sites - first < chunk) ? lat->sites - first : chunk;
+    cudaError_t e = lat->c64()
+                        ? launch_to_f64<float>(lat->stage(), reinterpret_cast<cpx<float>*>(src) + first, nullptr, cnt,
+                                               lat->st)
+                        : launch_to_f64<double>(lat->stage(), reinterpret_cast<cpx<double>*>(src) + first, nullptr,
+                                                cnt, lat->st);
+    QF_CUDA(lat, e);
+    QF_CUDA(lat, cudaMemcpyAsync(re_im + 2 * first, lat->stage(), cnt * 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                 lat->st));
+    QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  }
+  return QF_OK;
+}
+
+extern "C" qf_status qf_field_pointer(qf_lattice* lat, int slot, void** dev_ptr) {
+  if (!lat || !dev_ptr) return QF_EINVAL;
+  void* p = slot_ptr(lat, slot);
+  if (!p) return fail(lat, QF_ESTATE, "slot holds no field");
+  *dev_ptr = p;
+  return QF_OK;
+}
+
+// One kinetic application on `in` (psi' written to `out` when write), with FP64 sums
+// when reduce; returns the number of partial rows written through nblocks.
+static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write, bool reduce, const double* scale,
+                                int* nblocks) {
+  const int n = lat->d.n;
+  const double a = lat->d.a, m = lat->mass, dt = lat->dtau;
+  const void* v = lat->ws + lat->L.v;
+  if (lat->kinetic == QF_KIN_FDTD) {
+    const double kc = 1.0 / (2.0 * m * a * a);
+    if (lat->c64()) {
+      StencilArgs<float> s{reinterpret_cast<const cpx<float>*>(in), reinterpret_cast<cpx<float>*>(out), v,
+                           lat->v_real, (float)kc, (float)(0.5 * dt), (float)dt, scale, lat->partials(),
+                           write ? 1 : 0, reduce ? 1 : 0};
+      return launch_stencil<float>(n, s, lat->st, nblocks);
+    }
+    StencilArgs<double> s{reinterpret_cast<const cpx<double>*>(in), reinterpret_cast<cpx<double>*>(out), v,
+                          lat->v_real, kc, 0.5 * dt, dt, scale, lat->partials(), write ? 1 : 0, reduce ? 1 : 0};
+    return launch_stencil<double>(n, s, lat->st, nblocks);
+  }
+  // FFT terms: in place on `in` (out must equal in when writing); tmp is scratch
+  const double n3 = (double)n * n * n;
+  const double tcoef = lat->kinetic == QF_KIN_FFT_REL ? 1.0 / (a * n3) : 1.0 / (2.0 * a * a * m * n3);
+  const double am2 = (a * m) * (a * m);
+  if (lat->c64()) {
+    FftPassArgs<float> p{};
+    p.twiddle = reinterpret_cast<const cpx<float>*>(lat->ws + lat->L.tw);
+    p.symbol = reinterpret_cast<const float*>(lat->ws + lat->L.sym);
+    p.kinetic = lat->kinetic;
+    p.tcoef = (float)tcoef;
+    p.am2 = (float)am2;
+    p.psi = reinterpret_cast<cpx<float>*>(in);
+    p.v = v;
+    p.v_real = lat->v_real;
+    p.half_dtau = (float)(0.5 * dt);
+    p.dtau = (float)dt;
+    p.scale = scale;
+    p.partials = lat->partials();
+    p.write_psi = write ? 1 : 0;
+    p.reduce = reduce ? 1 : 0;
+    return launch_fft_step<float>(n, p, reinterpret_cast<cpx<float>*>(lat->tmp()), lat->st, nblocks);
+  }
+  FftPassArgs<double> p{};
+  p.twiddle = reinterpret_cast<const cpx<double>*>(lat->ws + lat->L.tw);
+  p.symbol = reinterpret_cast<const double*>(lat->ws + lat->L.sym);
+  p.kinetic = lat->kinetic;
+  p.tcoef = tcoef;
+  p.am2 = am2;
+  p.psi = reinterpret_cast<cpx<double>*>(in);
+  p.v = v;
+  p.v_real = lat->v_real;
+  p.half_dtau = 0.5 * dt;
+  p.dtau = dt;
+  p.scale = scale;
+  p.partials = lat->partials();
+  p.write_psi = write ? 1 : 0;
+  p.reduce = reduce ? 1 : 0;
+  return launch_fft_step<double>(n, p, reinterpret_cast<cpx<double>*>(lat->tmp()), lat->st, nblocks);
+}
+
+static qf_status read_energy(qf_lattice* lat, double* e3) {
+  QF_CUDA(lat, cudaMemcpyAsync(e3, lat->sc()->energy, 3 * sizeof(double), cudaMemcpyDeviceToHost, lat->st));
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  return QF_OK;
+}
+
+extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_abs, int check_every, int snap_every,
+                               int64_t* steps_done) {
+  if (steps_done) *steps_done = 0;
+  if (!lat) return QF_EINVAL;
+  if (max_steps < 0 || check_every < 0 || snap_every < 0 || !(tol_abs >= 0))
+    return fail(lat, QF_EINVAL, "negative step counts or tolerance");
+  if (!lat->have_v || lat->kinetic < 0 || !lat->have_psi)
+    return fail(lat, QF_ESTATE, "set the potential, kinetic term and wavefunction first");
+  const bool fdtd = lat->kinetic == QF_KIN_FDTD;
+  int64_t done = 0;
+  qf_status status = QF_ENOTCONV;
+  while (done < max_steps) {
+    const int64_t t = lat->step;
+    const double tau_t = lat->tau;
+    const bool check = check_every > 0 && t % check_every == 0;
+    const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[0];
+    int nb = 0;
+    void* in = lat->psi();
+    void* out = fdtd ? lat->tmp() : in;
+    QF_CUDA(lat, kinetic_pass(lat, in, out, true, check, scale, &nb));
+    lat->pending_scale = false;
+    if (check) {
+      QF_CUDA(lat, launch_finish(lat->partials(), nb, lat->sc(), 1, lat->st));
+      lat->pending_scale = true;
+    }
+    if (fdtd) lat->live = 1 - lat->live;
+    lat->step += 1;
+    lat->tau += lat->dtau;
+    ++done;
+    if (snap_every > 0 && lat->step % snap_every == 0) {
+      lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
+      QF_CUDA(lat, cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(),
+                                   (size_t)lat->sites * (lat->c64() ? 8 : 16), cudaMemcpyDeviceToDevice, lat->st));
+      if (lat->snap_count < lat->d.n_snap) lat->snap_count++;
+    }
+    if (check) {
+      double e3[3];
+      qf_status s = read_energy(lat, e3);
+      if (s != QF_OK) return s;
+      qf_energy r{};
+      r.e_re = e3[0];
+      r.e_im = e3[1];
+      r.norm = e3[2];
+      r.de = lat->have_prev ? hypot(e3[0] - lat->prev_re, e3[1] - lat->prev_im) : INFINITY;
+      r.step = t;
+      r.tau = tau_t;
+      lat->last = r;
+      lat->have_last = true;
+      const bool conv = lat->have_prev && r.de < tol_abs;
+      lat->have_prev = true;
+      lat->prev_re = e3[0];
+      lat->prev_im = e3[1];
+      if (conv) {
+        status = QF_OK;
+        break;
+      }
+    }
+  }
+  if (steps_done) *steps_done = done;
+  // surface asynchronous launch failures before reporting
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  return status;
+}
+
+extern "C" qf_status qf_energies(qf_lattice* lat, qf_energy* out) {
+  if (!lat || !out) return QF_EINVAL;
+  if (!lat->have_last) return fail(lat, QF_ESTATE, "no check has run yet");
+  *out = lat->last;
+  return QF_OK;
+}
+
+// <v|H|v>/<v|v> of a field into out (FP64 sums; the field is not modified).
+static qf_status measure(qf_lattice* lat, void* f, qf_energy* out) {
+  int nb = 0;
+  // FFT terms transform through tmp and read f; FDTD reads f only
+  QF_CUDA(lat, kinetic_pass(lat, f, f, false, true, &lat->sc()->scale[0], &nb));
+  QF_CUDA(lat, launch_finish(lat->partials(), nb, lat->sc(), 0, lat->st));
+  double e3[3];
+  qf_status s = read_energy(lat, e3);
+  if (s != QF_OK) return s;
+  out->e_re = e3[0];
+  out->e_im = e3[1];
+  out->norm = e3[2];
+  out->de = 0;
+  out->step = lat->step;
+  out->tau = lat->tau;
+  return QF_OK;
+}
+
+template <typename R>
+static qf_status gram_schmidt(qf_lattice* lat, int n_states) {
+  double* coef = lat->sc()->gs_coef;
+  const int nblk = field_blocks();
+  for (int i = 0; i < n_states; ++i) {
+    const int j = i;  // i-th latest snapshot
+    const int idx = ((lat->snap_head - j) % lat->d.n_snap + lat->d.n_snap) % lat->d.n_snap;
+    const cpx<R>* src = reinterpret_cast<const cpx<R>*>(lat->snap(idx));
+    cpx<R>* w = reinterpret_cast<cpx<R>*>(lat->state(i));
+    const cpx<R>* basis[2] = {reinterpret_cast<const cpx<R>*>(lat->state(0)),
+                              reinterpret_cast<const cpx<R>*>(lat->state(1))};
+    const int nb = i;
+    // classical Gram-Schmidt against v_0..v_{i-1}, then one re-orthogonalisation pass
+    QF_CUDA(lat, launch_dots<R>(basis, nb, src, lat->sites, lat->partials(), nblk, lat->st));
+    QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st));
+    QF_CUDA(lat, launch_axpy_basis<R>(w, src, basis, nb, coef, lat->sites, lat->st));
+    if (nb > 0) {
+      QF_CUDA(lat, launch_dots<R>(basis, nb, w, lat->sites, lat->partials(), nblk, lat->st));
+      QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st));
+      QF_CUDA(lat, launch_axpy_basis<R>(w, w, basis, nb, coef, lat->sites, lat->st));
+      QF_CUDA(lat, launch_dots<R>(basis, 0, w, lat->sites, lat->partials(), nblk, lat->st));
+      QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st));
+    }
+    // normalise: coef[5] = 1/||w||
+    QF_CUDA(lat, launch_scale_copy<R>(w, w, coef + 5, lat->sites, lat->st));
+    lat->have_states[i] = true;
+  }
+  return QF_OK;
+}
+
+extern "C" qf_status qf_project_excited(qf_lattice* lat, int n_states, qf_energy* out) {
+  if (!lat || !out) return QF_EINVAL;
+  if (n_states < 1 || n_states > 3 || n_states > lat->d.n_snap) return fail(lat, QF_EINVAL, "n_states out of range");
+  if (lat->snap_count < n_states) return fail(lat, QF_ESTATE, "not enough snapshots");
+  if (!lat->have_v || lat->kinetic < 0) return fail(lat, QF_ESTATE, "set the potential and kinetic term first");
+  qf_status s = lat->c64() ? gram_schmidt<float>(lat, n_states) : gram_schmidt<double>(lat, n_states);
+  if (s != QF_OK) return s;
+  for (int i = 0; i < n_states; ++i) {
+    s = measure(lat, lat->state(i), &out[i]);
+    if (s != QF_OK) return s;
+  }
+  return QF_OK;
+}
+
+template <typename R>
+static qf_status parity_t(qf_lattice* lat, int which, int axis, void* target) {
+  const int nblk = field_blocks();
+  cpx<R>* tmp = reinterpret_cast<cpx<R>*>(lat->tmp());
+  QF_CUDA(lat, launch_parity<R>(tmp, reinterpret_cast<const cpx<R>*>(target), lat->d.n, which, axis, lat->partials(),
+                                nblk, lat->st));
+  double* coef = lat->sc()->gs_coef;
+  QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st));
+  QF_CUDA(lat, launch_scale_copy<R>(reinterpret_cast<cpx<R>*>(target), tmp, coef + 5, lat->sites, lat->st));
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  return QF_OK;
+}
+
+extern "C" qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int target) {
+  if (!lat) return QF_EINVAL;
+  if (which < QF_P_PLUS || which > QF_P_MINUS_PK) return fail(lat, QF_EINVAL, "unknown projector");
+  if (which == QF_P_MINUS_PK && (axis < 1 || axis > 3)) return fail(lat, QF_EINVAL, "axis must be 1..3");
+  if (target < -1 || target > 2) return fail(lat, QF_EINVAL, "target must be -1..2");
+  void* f = slot_ptr(lat, target);
+  if (!f || (target == -1 && !lat->have_psi)) return fail(lat, QF_ESTATE, "target holds no field");
+  qf_status s = lat->c64() ? parity_t<float>(lat, which, axis, f) : parity_t<double>(lat, which, axis, f);
+  if (s != QF_OK) return s;
+  if (target == -1) lat->pending_scale = false;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_get_info(qf_lattice* lat, qf_info* out) {
+  if (!lat || !out) return QF_EINVAL;
+  out->dtau = lat->dtau;
+  out->step = lat->step;
+  out->tau = lat->tau;
+  out->kinetic = lat->kinetic;
+  out->n_snapshots = lat->snap_count;
+  out->workspace_bytes = lat->L.total;
+  return QF_OK;
+}
+
+extern "C" const char* qf_last_error(const qf_lattice* lat) {
+  if (!lat) return "null handle";
+  return lat->err.c_str();
+}
+
+extern "C" const char* qf_version(void) { return kVersion; }

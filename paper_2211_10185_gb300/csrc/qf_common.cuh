@@ -1,0 +1,176 @@
+// Internal definitions shared by the kernels and the C ABI of libqfdtd (sm_103a).
+//
+// Field layout: complex N^3 array, site (ix, iy, iz) at (iz*N + iy)*N + ix (x fastest),
+// coordinate x_i = (i - N/2) a.  Complex values are interleaved (re, im) pairs of the
+// lattice precision R (float for the c64 path, double for the c128 path).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qf {
+
+template <typename R>
+struct __align__(2 * sizeof(R)) cpx {
+  R x, y;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R a, R b) {
+  cpx<R> c;
+  c.x = a;
+  c.y = b;
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return mk<R>(a.x + b.x, a.y + b.y); }
+template <typename R>
+__device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return mk<R>(a.x - b.x, a.y - b.y); }
+template <typename R>
+__device__ __forceinline__ cpx<R> cmul(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename R>
+__device__ __forceinline__ cpx<R> cmulc(cpx<R> a, cpx<R> b) {
+  return mk<R>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> cscale(cpx<R> a, R s) { return mk<R>(a.x * s, a.y * s); }
+
+// Kinetic-term identifiers (Eqs. HK0-HK3).
+enum Kinetic : int { KIN_FDTD = 0, KIN_FFT_NAIVE = 1, KIN_FFT_SYMANZIK = 2, KIN_FFT_REL = 3 };
+
+// Number of FP64 partial sums a reducing kernel writes per block.
+constexpr int kNumSums = 5;  // <psi|psi>, Re/Im <psi|H_K psi>, Re/Im <psi|V psi>
+constexpr int kPartialStride = 8;
+
+// Device-resident scalars of one lattice (lives in the caller's workspace).
+struct DevScalars {
+  double scale[2];     // [0] = 1 always; [1] = 1/sqrt(norm) of the last check
+  double sums[8];      // last finished reduction (kNumSums used)
+  double energy[4];    // e_re, e_im, norm of the last finished reduction
+  double gs_coef[8];   // Gram-Schmidt coefficients <v_i|w> (complex, up to 3) + spare
+  double gs_scale[2];  // 1/||w|| of the current Gram-Schmidt vector
+  double parity_scale[2];
+  double spare[6];
+};
+
+// Arguments of one pass of the FFT kinetic step.
+template <typename R>
+struct FftPassArgs {
+  cpx<R>* data;           // field transformed in place (pass input and output)
+  const cpx<R>* src;      // first pass only: read from here instead of data
+  const cpx<R>* twiddle;  // exp(-2 pi i m / N), m in [0, N)
+  const R* symbol;        // per-axis kinetic symbol S[j] (k_j^2 or 4 sin^2(k_j/2))
+  int kinetic;            // KIN_FFT_*
+  R tcoef;                // HK1/HK2: 1/(2 a^2 m N^3); HK3: 1/(a N^3)
+  R am2;                  // (a m)^2 for HK3
+  // final pass (inverse x + update) only:
+  cpx<R>* psi;            // psi_t in, psi_{t+1} out (same sites)
+  const void* v;          // potential: cpx<R> (complex) or R (real)
+  int v_real;
+  R half_dtau;            // dtau / 2
+  R dtau;
+  const double* scale;    // output scale (device scalar)
+  double* partials;       // per-block FP64 sums when reducing
+  int write_psi;          // 0: measure only (no write)
+  int reduce;             // accumulate the kNumSums sums
+};
+
+// FDTD stencil step arguments (Eq. HK0 with Dirichlet planes).
+template <typename R>
+struct StencilArgs {
+  const cpx<R>* in;
+  cpx<R>* out;            // may be null when only measuring
+  const void* v;
+  int v_real;
+  R kcoef;                // 1/(2 m a^2)
+  R half_dtau;
+  R dtau;
+  const double* scale;
+  double* partials;
+  int write_psi;
+  int reduce;
+};
+
+// ---- block-level FP64 reduction of kNumSums values (deterministic order) ----------
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&s)[NV]) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) s[i] += __shfl_down_sync(0xffffffffu, s[i], off);
+  }
+}
+
+// Sums s over the block; thread 0 writes the result to out[0..NV).  scratch must hold
+// 32*NV doubles.  Every thread of the block must call it.
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&s)[NV], double* scratch, double* out) {
+  warp_sum<NV>(s);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+  __syncthreads();  // scratch may alias memory used just before
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) scratch[warp * NV + i] = s[i];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double t[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) t[i] = (lane < nwarps) ? scratch[lane * NV + i] : 0.0;
+    warp_sum<NV>(t);
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) out[i] = t[i];
+    }
+  }
+}
+
+// ---- launchers (return cudaError_t of the launch) ------------------------------------
+// FFT kinetic step: psi_{t+1} = s (coef_A psi_t - coef_B dtau H_K psi_t); tmp is scratch.
+template <typename R>
+cudaError_t launch_fft_step(int n, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nblocks_final);
+// Number of blocks the reducing (final) pass of the FFT step uses for lattice size n.
+template <typename R>
+int fft_final_blocks(int n);
+// Whether the FFT path has kernels for this n.
+bool fft_supported(int n);
+
+template <typename R>
+cudaError_t launch_stencil(int n, StencilArgs<R> args, cudaStream_t st, int* nblocks);
+template <typename R>
+int stencil_blocks(int n);
+
+// Finishing reduction: sums nblocks partial rows in index order into sc->sums, then
+// energy and (when set_scale) sc->scale[1] = 1/sqrt(norm).
+cudaError_t launch_finish(const double* partials, int nblocks, DevScalars* sc, int set_scale,
+                          cudaStream_t st);
+
+// Gram-Schmidt and field helpers (FP64 accumulation).
+template <typename R>
+cudaError_t launch_dots(const cpx<R>* const* basis, int nb, const cpx<R>* w, long long n_sites,
+                        double* partials, int nblocks, cudaStream_t st);
+cudaError_t launch_finish_dots(const double* partials, int nblocks, int nb, double* coef_out,
+                               cudaStream_t st);
+template <typename R>
+cudaError_t launch_axpy_basis(cpx<R>* w, const cpx<R>* src, const cpx<R>* const* basis, int nb,
+                              const double* coef, long long n_sites, cudaStream_t st);
+template <typename R>
+cudaError_t launch_scale_copy(cpx<R>* dst, const cpx<R>* src, const double* s, long long n_sites,
+                              cudaStream_t st);
+template <typename R>
+cudaError_t launch_parity(cpx<R>* dst, const cpx<R>* src, int n, int which, int axis,
+                          double* partials, int nblocks, cudaStream_t st);
+template <typename R>
+cudaError_t launch_from_f64(cpx<R>* dst, const double* src, long long n_elems_complex, cudaStream_t st);
+template <typename R>
+cudaError_t launch_to_f64(double* dst, const cpx<R>* src, const double* s, long long n_complex,
+                          cudaStream_t st);
+template <typename R>
+cudaError_t launch_real_from_f64(R* dst, const double* src, long long n, cudaStream_t st);
+int field_blocks();
+
+}  // namespace qf

@@ -1,0 +1,533 @@
+// Fused 3D FFT kinetic step (Eqs. HK1-HK3) with the imaginary-time update, sm_103a.
+//
+// One step is five passes over the lattice, each a batch of 1D transforms of length N
+// held in registers and shared memory:
+//   1. x forward (reads psi, writes tmp)          2. y forward (tmp in place)
+//   3. z forward -> x T(k) -> z inverse (tmp)      4. y inverse (tmp in place)
+//   5. x inverse -> H_K psi in registers -> psi' = s (coef_A psi - coef_B dtau H_K psi),
+//      FP64 norm/energy partial sums on check steps (psi in place).
+// The 1D transforms use the self-sorting Stockham formulation of Govindaraju et al.,
+// "High performance discrete Fourier transforms on graphics processors" (SC08): at a
+// stage of radix R after sub-transforms of size Ns, butterfly j reads x[j + r N/R],
+// multiplies by exp(-+2 pi i r (j mod Ns)/(Ns R)), does an R-point DFT and writes
+// y[(j/Ns) Ns R + (j mod Ns) + r Ns], so the output is in natural order.  The first
+// stage reads global memory and the last writes it directly (both coalesced);
+// intermediate stages exchange through shared memory.
+#include "qf_common.cuh"
+
+namespace qf {
+
+// ------------------------------------------------------------------------------------
+// Radix plans.  EPT = elements per thread = lcm of the radices.
+// ------------------------------------------------------------------------------------
+constexpr int plan_stages(int n) {
+  return n == 8 ? 1 : n == 16 ? 1 : n == 12 ? 2 : n == 24 ? 2 : n == 32 ? 2 : n == 48 ? 3
+       : n == 64 ? 2 : n == 96 ? 3 : n == 128 ? 2 : n == 192 ? 3 : n == 256 ? 2 : n == 384 ? 4
+       : n == 512 ? 3 : 0;
+}
+constexpr int plan_radix(int n, int s) {
+  return n == 8 ? 8
+       : n == 16 ? 16
+       : n == 12 ? (s == 0 ? 4 : 3)
+       : n == 24 ? (s == 0 ? 8 : 3)
+       : n == 32 ? (s == 0 ? 8 : 4)
+       : n == 48 ? (s == 2 ? 3 : 4)
+       : n == 64 ? 8
+       : n == 96 ? (s == 0 ? 8 : s == 1 ? 4 : 3)
+       : n == 128 ? (s == 0 ? 16 : 8)
+       : n == 192 ? (s == 2 ? 3 : 8)
+       : n == 256 ? 16
+       : n == 384 ? (s == 0 ? 8 : s == 3 ? 3 : 4)
+       : n == 512 ? 8 : 0;
+}
+constexpr int plan_ept(int n) {
+  return n == 8 ? 8 : n == 16 ? 16 : n == 12 ? 12 : n == 24 ? 24 : n == 32 ? 8 : n == 48 ? 12
+       : n == 64 ? 8 : n == 96 ? 24 : n == 128 ? 16 : n == 192 ? 24 : n == 256 ? 16
+       : n == 384 ? 24 : n == 512 ? 8 : 0;
+}
+// product of the radices before stage s
+constexpr int plan_ns(int n, int s) { return s == 0 ? 1 : plan_ns(n, s - 1) * plan_radix(n, s - 1); }
+// offset of stage s in the per-stage twiddle table: entries [k][r-1], k < Ns, 1 <= r < R
+constexpr int plan_tw_off(int n, int s) {
+  return s == 0 ? 0 : plan_tw_off(n, s - 1) + plan_ns(n, s - 1) * (plan_radix(n, s - 1) - 1);
+}
+constexpr int plan_tw_size(int n) { return plan_tw_off(n, plan_stages(n)); }
+
+constexpr int largest_divisor_le(int n, int cap) {
+  int best = 1;
+  for (int d = 1; d <= n && d <= cap; ++d)
+    if (n % d == 0) best = d;
+  return best;
+}
+
+template <typename R, int N>
+struct Geom {
+  static constexpr int EPT = plan_ept(N);
+  static constexpr int S = plan_stages(N);
+  static constexpr int TARGET = sizeof(R) == 4 ? 4096 : 2048;  // elements per tile
+  // x pass: LC whole lines per block
+  static constexpr int LC = largest_divisor_le(N * N, TARGET / N > 0 ? TARGET / N : 1);
+  static constexpr int TL = N / EPT;                       // threads per line
+  static constexpr int THREADS_X = LC * TL;
+  static constexpr int PAD_SHIFT = sizeof(R) == 4 ? 4 : 3;  // one pad element per 128 B
+  static constexpr int PL = N + (N >> PAD_SHIFT) + 1;       // padded line length
+  // y/z passes: C = L contiguous columns x P outer slices
+  static constexpr int L = largest_divisor_le(N, sizeof(R) == 4 ? 16 : 8);
+  static constexpr int P = largest_divisor_le(N, TARGET / (L * N) > 0 ? TARGET / (L * N) : 1);
+  static constexpr int C = L * P;
+  static constexpr int THREADS_S = C * N / EPT;
+  static constexpr int TW = plan_tw_size(N);
+  static_assert(S > 0 && EPT > 0, "unsupported N");
+};
+
+// ------------------------------------------------------------------------------------
+// Small DFTs (forward: exp(-2 pi i rk/R); INV flips the sign of the exponent)
+// ------------------------------------------------------------------------------------
+template <typename R, bool INV>
+__device__ __forceinline__ cpx<R> mul_negi(cpx<R> a) {  // a * exp(-+ i pi/2)
+  return INV ? mk<R>(-a.y, a.x) : mk<R>(a.y, -a.x);
+}
+// a * exp(-+ i theta) given c = cos(theta), s = sin(theta)
+template <typename R, bool INV>
+__device__ __forceinline__ cpx<R> rot(cpx<R> a, R c, R s) {
+  return INV ? mk<R>(a.x * c - a.y * s, a.y * c + a.x * s) : mk<R>(a.x * c + a.y * s, a.y * c - a.x * s);
+}
+
+template <typename R, bool INV>
+__device__ __forceinline__ void dft2(cpx<R>& a, cpx<R>& b) {
+  cpx<R> t = a - b;
+  a = a + b;
+  b = t;
+}
+
+template <typename R, bool INV>
+__device__ __forceinline__ void dft4(cpx<R>& x0, cpx<R>& x1, cpx<R>& x2, cpx<R>& x3) {
+  cpx<R> a0 = x0 + x2, a1 = x0 - x2, a2 = x1 + x3, a3 = mul_negi<R, INV>(x1 - x3);
+  x0 = a0 + a2;
+  x2 = a0 - a2;
+  x1 = a1 + a3;
+  x3 = a1 - a3;
+}
+
+template <typename R, bool INV>
+__device__ __forceinline__ void dft3(cpx<R>& x0, cpx<R>& x1, cpx<R>& x2) {
+  const R h = R(0.86602540378443864676);  // sin(2 pi / 3)
+  cpx<R> s = x1 + x2, d = x1 - x2;
+  cpx<R> t = mk<R>(x0.x - R(0.5) * s.x, x0.y - R(0.5) * s.y);
+  x0 = x0 + s;
+  // forward: y1 = t - i h d, y2 = t + i h d
+  cpx<R> ihd = mk<R>(-h * d.y, h * d.x);  // i h d
+  if (INV) {
+    x1 = t + ihd;
+    x2 = t - ihd;
+  } else {
+    x1 = t - ihd;
+    x2 = t + ihd;
+  }
+}
+
+template <typename R, bool INV>
+__device__ __forceinline__ void dft8(cpx<R>* x) {
+  const R r2 = R(0.70710678118654752440);
+  dft4<R, INV>(x[0], x[2], x[4], x[6]);
+  dft4<R, INV>(x[1], x[3], x[5], x[7]);
+  // odd part times exp(-+ 2 pi i k/8), k = 1, 2, 3
+  x[3] = rot<R, INV>(x[3], r2, r2);
+  x[5] = mul_negi<R, INV>(x[5]);
+  x[7] = rot<R, INV>(x[7], -r2, r2);
+  cpx<R> y[8];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    y[k] = x[2 * k] + x[2 * k + 1];
+    y[k + 4] = x[2 * k] - x[2 * k + 1];
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = y[k];
+}
+
+template <typename R, bool INV>
+__device__ __forceinline__ void dft16(cpx<R>* x) {
+  const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173);  // pi/8
+  const R r2 = R(0.70710678118654752440);
+  // n = 4 n1 + n2: length-4 DFTs over n1 for each n2 -> A[n2][k1] stored at x[4 n1 + n2]
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<R, INV>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+  // after dft4, x[4 k1 + n2] holds A[n2][k1]; twiddle by exp(-+ 2 pi i n2 k1 / 16)
+  x[4 * 1 + 1] = rot<R, INV>(x[5], c1, s1);     // n2=1,k1=1: 1
+  x[4 * 2 + 1] = rot<R, INV>(x[9], r2, r2);     // n2=1,k1=2: 2
+  x[4 * 3 + 1] = rot<R, INV>(x[13], s1, c1);    // n2=1,k1=3: 3
+  x[4 * 1 + 2] = rot<R, INV>(x[6], r2, r2);     // n2=2,k1=1: 2
+  x[4 * 2 + 2] = mul_negi<R, INV>(x[10]);       // n2=2,k1=2: 4
+  x[4 * 3 + 2] = rot<R, INV>(x[14], -r2, r2);   // n2=2,k1=3: 6
+  x[4 * 1 + 3] = rot<R, INV>(x[7], s1, c1);     // n2=3,k1=1: 3
+  x[4 * 2 + 3] = rot<R, INV>(x[11], -r2, r2);   // n2=3,k1=2: 6
+  x[4 * 3 + 3] = rot<R, INV>(x[15], -c1, -s1);  // n2=3,k1=3: 9
+  // length-4 DFTs over n2 for each k1: y[k1 + 4 k2]
+  cpx<R> y[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    cpx<R> a = x[4 * k1], b = x[4 * k1 + 1], c = x[4 * k1 + 2], d = x[4 * k1 + 3];
+    dft4<R, INV>(a, b, c, d);
+    y[k1] = a;
+    y[k1 + 4] = b;
+    y[k1 + 8] = c;
+    y[k1 + 12] = d;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) x[k] = y[k];
+}
+
+template <typename R, int RAD, bool INV>
+__device__ __forceinline__ void dft(cpx<R>* x) {
+  if constexpr (RAD == 2) {
+    dft2<R, INV>(x[0], x[1]);
+  } else if constexpr (RAD == 3) {
+    dft3<R, INV>(x[0], x[1], x[2]);
+  } else if constexpr (RAD == 4) {
+    dft4<R, INV>(x[0], x[1], x[2], x[3]);
+  } else if constexpr (RAD == 8) {
+    dft8<R, INV>(x);
+  } else if constexpr (RAD == 16) {
+    dft16<R, INV>(x);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// One Stockham stage on the registers of one thread: EPT/RAD butterflies, butterfly b
+// of thread group g has index j = g + b * TL (TL = N/EPT threads per line).
+// ------------------------------------------------------------------------------------
+template <typename R, int N, int ST, bool INV>
+__device__ __forceinline__ void stage_compute(cpx<R> (&v)[plan_ept(N)], int g, const cpx<R>* tw_s) {
+  constexpr int EPT = plan_ept(N), RAD = plan_radix(N, ST), NS = plan_ns(N, ST), TL = N / EPT;
+  constexpr int OFF = plan_tw_off(N, ST);
+#pragma unroll
+  for (int b = 0; b < EPT / RAD; ++b) {
+    if constexpr (NS > 1) {
+      const int j = g + b * TL;
+      const int k = j % NS;
+      const cpx<R>* t = tw_s + OFF + k * (RAD - 1);
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        cpx<R> w = t[r - 1];
+        v[b * RAD + r] = INV ? cmulc<R>(v[b * RAD + r], w) : cmul<R>(v[b * RAD + r], w);
+      }
+    }
+    dft<R, RAD, INV>(&v[b * RAD]);
+  }
+}
+
+// element index read by (b, r) at stage ST
+template <int N, int ST>
+__device__ __forceinline__ int e_in(int g, int b, int r) {
+  constexpr int EPT = plan_ept(N), RAD = plan_radix(N, ST), TL = N / EPT;
+  return g + b * TL + r * (N / RAD);
+}
+// element index written by (b, r) at stage ST
+template <int N, int ST>
+__device__ __forceinline__ int e_out(int g, int b, int r) {
+  constexpr int EPT = plan_ept(N), RAD = plan_radix(N, ST), NS = plan_ns(N, ST), TL = N / EPT;
+  const int j = g + b * TL;
+  return (j / NS) * NS * RAD + (j % NS) + r * NS;
+}
+
+// ------------------------------------------------------------------------------------
+// Shared-memory accessors for the two tile layouts
+// ------------------------------------------------------------------------------------
+template <typename R, int N, bool STRIDED>
+struct Tile {
+  using G = Geom<R, N>;
+  cpx<R>* s;
+  int col;  // STRIDED: column; contiguous: line
+  __device__ __forceinline__ int idx(int e) const {
+    if constexpr (STRIDED) return e * G::C + col;
+    else return col * G::PL + e + (e >> G::PAD_SHIFT);
+  }
+  __device__ __forceinline__ cpx<R> ld(int e) const { return s[idx(e)]; }
+  __device__ __forceinline__ void st(int e, cpx<R> v) const { s[idx(e)] = v; }
+};
+
+// Runs stages [FIRST, LAST] of one transform direction.  Stage FIRST reads either global
+// memory (gsrc: element e of this thread's line at gsrc[e * gstride]) or shared memory;
+// stage LAST leaves its outputs in v (natural-order element e_out<N, LAST>).
+template <typename R, int N, bool STRIDED, bool INV, int ST, int LAST>
+__device__ __forceinline__ void run_stages(cpx<R> (&v)[plan_ept(N)], int g, const Tile<R, N, STRIDED>& t,
+                                           const cpx<R>* tw_s) {
+  constexpr int RAD = plan_radix(N, ST);
+  constexpr int EPT = plan_ept(N);
+  stage_compute<R, N, ST, INV>(v, g, tw_s);
+  if constexpr (ST < LAST) {
+    __syncthreads();  // all reads of this stage's inputs are done
+#pragma unroll
+    for (int b = 0; b < EPT / RAD; ++b)
+#pragma unroll
+      for (int r = 0; r < RAD; ++r) t.st(e_out<N, ST>(g, b, r), v[b * RAD + r]);
+    __syncthreads();
+    constexpr int RN = plan_radix(N, ST + 1);
+#pragma unroll
+    for (int b = 0; b < EPT / RN; ++b)
+#pragma unroll
+      for (int r = 0; r < RN; ++r) v[b * RN + r] = t.ld(e_in<N, ST + 1>(g, b, r));
+    run_stages<R, N, STRIDED, INV, ST + 1, LAST>(v, g, t, tw_s);
+  }
+}
+
+// Kinetic multiplier T(k)/N^3 for momenta indices (jx, jy, jz) (Eqs. HK1-HK3).
+template <typename R>
+__device__ __forceinline__ R kin_mult(int kinetic, R sxy, R sz, R tcoef, R am2) {
+  R s = sxy + sz;
+  if (kinetic == KIN_FFT_REL) return sqrt(s + am2) * tcoef;
+  return s * tcoef;
+}
+
+// ------------------------------------------------------------------------------------
+// Pass kernels
+// ------------------------------------------------------------------------------------
+enum PassOp : int { OP_FWD = 0, OP_INV = 1, OP_MID = 2, OP_FINAL = 3 };
+
+template <typename R, int N>
+__device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
+  for (int i = threadIdx.x; i < Geom<R, N>::TW; i += blockDim.x) tw_s[i] = tw[i];
+}
+
+// x pass: LC contiguous lines per block.  OP_FWD: src -> data.  OP_FINAL: data (H_K psi
+// in x-transformed space) -> inverse x -> update of psi.
+template <typename R, int N, int OP>
+__global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArgs<R> a) {
+  using G = Geom<R, N>;
+  constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
+  constexpr bool INV = (OP == OP_FINAL);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* tw_s = reinterpret_cast<cpx<R>*>(smem_raw);
+  cpx<R>* data_s = tw_s + G::TW;
+  double* red_s = reinterpret_cast<double*>(data_s + G::LC * G::PL);
+
+  const int line = threadIdx.x / G::TL, g = threadIdx.x % G::TL;
+  const long long gline = (long long)blockIdx.x * G::LC + line;
+  const long long base = gline * N;
+  load_twiddles<R, N>(tw_s, a.twiddle);
+
+  const cpx<R>* in = (OP == OP_FWD && a.src) ? a.src : a.data;
+  cpx<R> v[EPT];
+#pragma unroll
+  for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[b * R0 + r] = in[base + e_in<N, 0>(g, b, r)];
+  __syncthreads();  // twiddles visible
+
+  Tile<R, N, false> t{data_s, line};
+  run_stages<R, N, false, INV, 0, S - 1>(v, g, t, tw_s);
+
+  if constexpr (OP == OP_FWD) {
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r)] = v[b * RL + r];
+  } else {
+    // v = H_K psi at the sites of this line (the 1/N^3 is inside T).
+    double acc[kNumSums] = {0, 0, 0, 0, 0};
+    const R sc = R(*a.scale);
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const long long site = base + e_out<N, S - 1>(g, b, r);
+        const cpx<R> h = v[b * RL + r];
+        const cpx<R> p = a.psi[site];
+        cpx<R> vv;
+        if (a.v_real) vv = mk<R>(reinterpret_cast<const R*>(a.v)[site], R(0));
+        else vv = reinterpret_cast<const cpx<R>*>(a.v)[site];
+        if (a.reduce) {
+          const double px = p.x, py = p.y, hx = h.x, hy = h.y;
+          const double w = px * px + py * py;
+          acc[0] += w;
+          acc[1] += px * hx + py * hy;   // Re conj(psi) H psi
+          acc[2] += px * hy - py * hx;   // Im
+          acc[3] += w * double(vv.x);
+          acc[4] += w * double(vv.y);
+        }
+        if (a.write_psi) {
+          // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d
+          const cpx<R> d = mk<R>(R(1) + a.half_dtau * vv.x, a.half_dtau * vv.y);
+          const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), p) - cscale<R>(h, a.dtau);
+          const R inv = sc / (d.x * d.x + d.y * d.y);
+          a.psi[site] = cscale<R>(cmulc<R>(num, d), inv);
+        }
+      }
+    if (a.reduce) block_sum_store<kNumSums>(acc, red_s, a.partials + (long long)blockIdx.x * kPartialStride);
+  }
+}
+
+// y / z passes: C = L x P columns per block.  AXIS 1: points stride N, outer = z (stride
+// N^2).  AXIS 2: points stride N^2, outer = y (stride N).
+template <typename R, int N, int AXIS, int OP>
+__global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArgs<R> a) {
+  using G = Geom<R, N>;
+  constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
+  constexpr long long PSTRIDE = AXIS == 1 ? N : (long long)N * N;
+  constexpr long long OSTRIDE = AXIS == 1 ? (long long)N * N : N;
+  constexpr bool INV = (OP == OP_INV);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cpx<R>* tw_s = reinterpret_cast<cpx<R>*>(smem_raw);
+  R* sym_s = reinterpret_cast<R*>(tw_s + G::TW);
+  cpx<R>* data_s = reinterpret_cast<cpx<R>*>(sym_s + ((N * sizeof(R) + 15) / 16) * 16 / sizeof(R));
+
+  const int c = threadIdx.x % G::C, g = threadIdx.x / G::C;
+  const int l = c % G::L, p = c / G::L;
+  constexpr int XB = N / G::L;
+  const int xb = blockIdx.x % XB, ob = blockIdx.x / XB;
+  const int x = xb * G::L + l, o = ob * G::P + p;
+  const long long base = (long long)o * OSTRIDE + x;
+  load_twiddles<R, N>(tw_s, a.twiddle);
+  if (OP == OP_MID)
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sym_s[i] = a.symbol[i];
+
+  cpx<R> v[EPT];
+#pragma unroll
+  for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r) v[b * R0 + r] = a.data[base + e_in<N, 0>(g, b, r) * PSTRIDE];
+  __syncthreads();
+
+  Tile<R, N, true> t{data_s, c};
+  if constexpr (OP == OP_MID) {
+    run_stages<R, N, true, false, 0, S - 1>(v, g, t, tw_s);
+    // forward z transform done: natural-order kz; multiply by T and start the inverse
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1>(g, b, r), v[b * RL + r]);
+    __syncthreads();
+    const R sxy = sym_s[x] + sym_s[o];  // kx = x, ky = o (after the x and y passes)
+#pragma unroll
+    for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) {
+        const int kz = e_in<N, 0>(g, b, r);
+        const R tm = kin_mult<R>(a.kinetic, sxy, sym_s[kz], a.tcoef, a.am2);
+        v[b * R0 + r] = cscale<R>(t.ld(kz), tm);
+      }
+    run_stages<R, N, true, true, 0, S - 1>(v, g, t, tw_s);
+  } else {
+    run_stages<R, N, true, INV, 0, S - 1>(v, g, t, tw_s);
+  }
+#pragma unroll
+  for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r) * PSTRIDE] = v[b * RL + r];
+}
+
+// ------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------
+template <typename R, int N>
+static size_t smem_x() {
+  using G = Geom<R, N>;
+  return G::TW * sizeof(cpx<R>) + G::LC * G::PL * sizeof(cpx<R>) + 32 * kNumSums * sizeof(double);
+}
+template <typename R, int N>
+static size_t smem_s() {
+  using G = Geom<R, N>;
+  return G::TW * sizeof(cpx<R>) + ((N * sizeof(R) + 15) / 16) * 16 + (size_t)G::C * N * sizeof(cpx<R>);
+}
+
+template <typename R, int N>
+static cudaError_t step_n(FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
+  using G = Geom<R, N>;
+  const int gx = N * N / G::LC, gs = (N / G::L) * (N / G::P);
+  const size_t sx = smem_x<R, N>(), ss = smem_s<R, N>();
+  static bool attr_done = false;
+  if (!attr_done) {
+    // tiles stay below 48 KB for every supported N except the largest; raise the limit
+    cudaFuncSetAttribute(fft_x_kernel<R, N, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
+    cudaFuncSetAttribute(fft_x_kernel<R, N, OP_FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
+    cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    attr_done = true;
+  }
+  if (nfinal) *nfinal = gx;
+  if (a.write_psi || a.reduce) {
+    FftPassArgs<R> p = a;
+    p.src = a.psi;
+    p.data = tmp;
+    fft_x_kernel<R, N, OP_FWD><<<gx, G::THREADS_X, sx, st>>>(p);
+    fft_s_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p);
+    fft_s_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(p);
+    fft_s_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p);
+    p.src = nullptr;
+    fft_x_kernel<R, N, OP_FINAL><<<gx, G::THREADS_X, sx, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+bool fft_supported(int n) { return plan_stages(n) > 0; }
+
+template <typename R>
+cudaError_t launch_fft_step(int n, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
+  switch (n) {
+#define QF_CASE(NN) \
+  case NN:          \
+    return step_n<R, NN>(args, tmp, st, nfinal);
+    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
+    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
+#undef QF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+int fft_final_blocks(int n) {
+  switch (n) {
+#define QF_CASE(NN) \
+  case NN:          \
+    return NN * NN / Geom<R, NN>::LC;
+    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
+    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
+#undef QF_CASE
+    default:
+      return 0;
+  }
+}
+
+// Host-side twiddle table in the per-stage layout the kernels read.
+int fft_twiddle_count(int n) {
+  switch (n) {
+#define QF_CASE(NN) \
+  case NN:          \
+    return plan_tw_size(NN);
+    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
+    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
+#undef QF_CASE
+    default:
+      return 0;
+  }
+}
+
+// Fills tw[off(s) + k (R_s - 1) + r - 1] = exp(-2 pi i r k / (Ns R_s)) in double.
+void fft_twiddles(int n, double* re_im) {
+  const double two_pi = 6.283185307179586476925286766559;
+  int ns = 1, off = 0;
+  for (int s = 0; s < plan_stages(n); ++s) {
+    const int rad = plan_radix(n, s);
+    for (int k = 0; k < ns; ++k)
+      for (int r = 1; r < rad; ++r) {
+        const long long num = (long long)r * k;
+        const long long den = (long long)ns * rad;
+        const double ang = -two_pi * (double)num / (double)den;
+        const int idx = off + k * (rad - 1) + (r - 1);
+        re_im[2 * idx] = cos(ang);
+        re_im[2 * idx + 1] = sin(ang);
+      }
+    off += ns * (rad - 1);
+    ns *= rad;
+  }
+}
+
+template cudaError_t launch_fft_step<float>(int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
+template cudaError_t launch_fft_step<double>(int, FftPassArgs<double>, cpx<double>*, cudaStream_t, int*);
+template int fft_final_blocks<float>(int);
+template int fft_final_blocks<double>(int);
+
+}  // namespace qf

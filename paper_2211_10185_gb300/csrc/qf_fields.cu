@@ -1,0 +1,272 @@
+// Whole-field helpers: finishing reductions, Gram-Schmidt inner products and axpy
+// (Sec. 1, excited states from snapshots), parity projectors (Sec. 3) and precision
+// conversion at the host boundary.  All sums are FP64 and run in a fixed order, so
+// repeated runs give bitwise-identical results.
+#include <math.h>
+
+#include "qf_common.cuh"
+
+namespace qf {
+
+constexpr int kFieldThreads = 256;
+int field_blocks() { return 152 * 4; }  // 4 blocks per SM of the 152-SM GB300
+
+// ------------------------------------------------------------------------------------
+// Finishing reduction of per-block partial sums
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ partials, int nblocks,
+                                                     DevScalars* sc, int set_scale) {
+  __shared__ double red_s[32 * kNumSums];
+  __shared__ double tot[kNumSums];
+  double s[kNumSums] = {0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < kNumSums; ++i) s[i] += partials[(long long)b * kPartialStride + i];
+  block_sum_store<kNumSums>(s, red_s, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double nrm = tot[0];
+    for (int i = 0; i < kNumSums; ++i) sc->sums[i] = tot[i];
+    // E = (<psi|H_K psi> + <psi|V psi>) / <psi|psi>
+    sc->energy[0] = (tot[1] + tot[3]) / nrm;
+    sc->energy[1] = (tot[2] + tot[4]) / nrm;
+    sc->energy[2] = nrm;
+    if (set_scale) sc->scale[1] = nrm > 0 ? 1.0 / sqrt(nrm) : 1.0;
+  }
+}
+
+cudaError_t launch_finish(const double* partials, int nblocks, DevScalars* sc, int set_scale, cudaStream_t st) {
+  finish_kernel<<<1, 256, 0, st>>>(partials, nblocks, sc, set_scale);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Inner products <v_j|w> (j < nb <= 2) and <w|w>
+// ------------------------------------------------------------------------------------
+template <typename R>
+struct Basis2 {
+  const cpx<R>* v[2];
+};
+
+template <typename R, int NB>
+__global__ void __launch_bounds__(kFieldThreads) dots_kernel(Basis2<R> basis, const cpx<R>* __restrict__ w,
+                                                             long long n_sites, double* partials) {
+  __shared__ double red_s[32 * kNumSums];
+  double s[kNumSums] = {0, 0, 0, 0, 0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_sites; i += stride) {
+    const cpx<R> x = w[i];
+    const double wx = x.x, wy = x.y;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const cpx<R> u = basis.v[j][i];
+      const double ux = u.x, uy = u.y;
+      s[2 * j] += ux * wx + uy * wy;      // Re conj(u) w
+      s[2 * j + 1] += ux * wy - uy * wx;  // Im
+    }
+    s[4] += wx * wx + wy * wy;
+  }
+  block_sum_store<kNumSums>(s, red_s, partials + (long long)blockIdx.x * kPartialStride);
+}
+
+template <typename R>
+cudaError_t launch_dots(const cpx<R>* const* basis, int nb, const cpx<R>* w, long long n_sites, double* partials,
+                        int nblocks, cudaStream_t st) {
+  Basis2<R> b{{nb > 0 ? basis[0] : nullptr, nb > 1 ? basis[1] : nullptr}};
+  if (nb == 0) dots_kernel<R, 0><<<nblocks, kFieldThreads, 0, st>>>(b, w, n_sites, partials);
+  else if (nb == 1) dots_kernel<R, 1><<<nblocks, kFieldThreads, 0, st>>>(b, w, n_sites, partials);
+  else dots_kernel<R, 2><<<nblocks, kFieldThreads, 0, st>>>(b, w, n_sites, partials);
+  return cudaGetLastError();
+}
+
+// coef_out: [Re c0, Im c0, Re c1, Im c1, |w|^2, 1/|w|]
+__global__ void __launch_bounds__(256) finish_dots_kernel(const double* __restrict__ partials, int nblocks,
+                                                          double* coef_out) {
+  __shared__ double red_s[32 * kNumSums];
+  __shared__ double tot[kNumSums];
+  double s[kNumSums] = {0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < kNumSums; ++i) s[i] += partials[(long long)b * kPartialStride + i];
+  block_sum_store<kNumSums>(s, red_s, tot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kNumSums; ++i) coef_out[i] = tot[i];
+    coef_out[5] = tot[4] > 0 ? 1.0 / sqrt(tot[4]) : 0.0;
+  }
+}
+
+cudaError_t launch_finish_dots(const double* partials, int nblocks, int nb, double* coef_out, cudaStream_t st) {
+  (void)nb;
+  finish_dots_kernel<<<1, 256, 0, st>>>(partials, nblocks, coef_out);
+  return cudaGetLastError();
+}
+
+// w = src - sum_j c_j v_j, evaluated in FP64 per element and rounded once.
+template <typename R, int NB>
+__global__ void __launch_bounds__(kFieldThreads) axpy_kernel(cpx<R>* w, const cpx<R>* src, Basis2<R> basis,
+                                                             const double* __restrict__ coef, long long n_sites) {
+  double cr[2] = {0, 0}, ci[2] = {0, 0};
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    cr[j] = coef[2 * j];
+    ci[j] = coef[2 * j + 1];
+  }
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_sites; i += stride) {
+    const cpx<R> x = src[i];
+    double ox = x.x, oy = x.y;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const cpx<R> u = basis.v[j][i];
+      ox -= cr[j] * double(u.x) - ci[j] * double(u.y);
+      oy -= cr[j] * double(u.y) + ci[j] * double(u.x);
+    }
+    w[i] = mk<R>(R(ox), R(oy));
+  }
+}
+
+template <typename R>
+cudaError_t launch_axpy_basis(cpx<R>* w, const cpx<R>* src, const cpx<R>* const* basis, int nb, const double* coef,
+                              long long n_sites, cudaStream_t st) {
+  Basis2<R> b{{nb > 0 ? basis[0] : nullptr, nb > 1 ? basis[1] : nullptr}};
+  const int nblk = field_blocks();
+  if (nb == 0) axpy_kernel<R, 0><<<nblk, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites);
+  else if (nb == 1) axpy_kernel<R, 1><<<nblk, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites);
+  else axpy_kernel<R, 2><<<nblk, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites);
+  return cudaGetLastError();
+}
+
+// dst = src * s (s a device FP64 scalar), product in FP64.
+template <typename R>
+__global__ void __launch_bounds__(kFieldThreads) scale_copy_kernel(cpx<R>* dst, const cpx<R>* src,
+                                                                   const double* __restrict__ s, long long n) {
+  const double f = *s;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const cpx<R> x = src[i];
+    dst[i] = mk<R>(R(double(x.x) * f), R(double(x.y) * f));
+  }
+}
+
+template <typename R>
+cudaError_t launch_scale_copy(cpx<R>* dst, const cpx<R>* src, const double* s, long long n, cudaStream_t st) {
+  scale_copy_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(dst, src, s, n);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Parity projectors (Sec. 3).  Mirror of index i on an axis: (N - i) mod N, the site at
+// coordinate -x_i.  P+- = (psi(r) +- psi(-r))/2;  P-_{p_k} = ((psi(r) + psi(r with the
+// other two axes flipped)) - (psi(r with axis k flipped) + psi(-r)))/4.  The grouping
+// makes mirror-image outputs bitwise equal (or exactly negated).
+// ------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restrict__ dst, const cpx<R>* __restrict__ src,
+                                                               int n, int which, int axis, double* partials) {
+  __shared__ double red_s[32 * kNumSums];
+  double s[kNumSums] = {0, 0, 0, 0, 0};
+  const long long total = (long long)n * n * n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+    const int mx = ix == 0 ? 0 : n - ix, my = iy == 0 ? 0 : n - iy, mz = iz == 0 ? 0 : n - iz;
+    auto at = [&](int x, int y, int z) { return src[((long long)z * n + y) * n + x]; };
+    const cpx<R> p = src[i];
+    cpx<R> o;
+    if (which == 0 || which == 1) {
+      const cpx<R> q = at(mx, my, mz);
+      o = which == 0 ? p + q : p - q;
+      o = cscale<R>(o, R(0.5));
+    } else {
+      // axis k in {1, 2, 3} = x, y, z; the other two axes flip together
+      const int fx = axis == 1 ? ix : mx, fy = axis == 2 ? iy : my, fz = axis == 3 ? iz : mz;  // others flipped
+      const int gx = axis == 1 ? mx : ix, gy = axis == 2 ? my : iy, gz = axis == 3 ? mz : iz;  // axis k flipped
+      o = (p + at(fx, fy, fz)) - (at(gx, gy, gz) + at(mx, my, mz));
+      o = cscale<R>(o, R(0.25));
+    }
+    dst[i] = o;
+    s[0] += double(o.x) * double(o.x) + double(o.y) * double(o.y);
+  }
+  block_sum_store<kNumSums>(s, red_s, partials + (long long)blockIdx.x * kPartialStride);
+}
+
+template <typename R>
+cudaError_t launch_parity(cpx<R>* dst, const cpx<R>* src, int n, int which, int axis, double* partials, int nblocks,
+                          cudaStream_t st) {
+  parity_kernel<R><<<nblocks, kFieldThreads, 0, st>>>(dst, src, n, which, axis, partials);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
+// Precision conversion at the host boundary
+// ------------------------------------------------------------------------------------
+template <typename R>
+__global__ void from_f64_kernel(cpx<R>* dst, const double* __restrict__ src, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    dst[i] = mk<R>(R(src[2 * i]), R(src[2 * i + 1]));
+}
+template <typename R>
+cudaError_t launch_from_f64(cpx<R>* dst, const double* src, long long n, cudaStream_t st) {
+  from_f64_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void to_f64_kernel(double* dst, const cpx<R>* __restrict__ src, const double* s, long long n) {
+  const double f = s ? *s : 1.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const cpx<R> x = src[i];
+    dst[2 * i] = double(x.x) * f;
+    dst[2 * i + 1] = double(x.y) * f;
+  }
+}
+template <typename R>
+cudaError_t launch_to_f64(double* dst, const cpx<R>* src, const double* s, long long n, cudaStream_t st) {
+  to_f64_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(dst, src, s, n);
+  return cudaGetLastError();
+}
+
+template <typename R>
+__global__ void real_from_f64_kernel(R* dst, const double* __restrict__ src, long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = R(src[i]);
+}
+template <typename R>
+cudaError_t launch_real_from_f64(R* dst, const double* src, long long n, cudaStream_t st) {
+  real_from_f64_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+// complex potential from separate real / imaginary FP64 arrays
+template <typename R>
+__global__ void pack_f64_kernel(cpx<R>* dst, const double* __restrict__ re, const double* __restrict__ im,
+                                long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    dst[i] = mk<R>(R(re[i]), R(im[i]));
+}
+template <typename R>
+cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, long long n, cudaStream_t st) {
+  pack_f64_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(dst, re, im, n);
+  return cudaGetLastError();
+}
+
+#define QF_INST(R)                                                                                          \
+  template cudaError_t launch_dots<R>(const cpx<R>* const*, int, const cpx<R>*, long long, double*, int,   \
+                                      cudaStream_t);                                                        \
+  template cudaError_t launch_axpy_basis<R>(cpx<R>*, const cpx<R>*, const cpx<R>* const*, int, const double*, \
+                                            long long, cudaStream_t);                                      \
+  template cudaError_t launch_scale_copy<R>(cpx<R>*, const cpx<R>*, const double*, long long, cudaStream_t); \
+  template cudaError_t launch_parity<R>(cpx<R>*, const cpx<R>*, int, int, int, double*, int, cudaStream_t); \
+  template cudaError_t launch_from_f64<R>(cpx<R>*, const double*, long long, cudaStream_t);                 \
+  template cudaError_t launch_to_f64<R>(double*, const cpx<R>*, const double*, long long, cudaStream_t);    \
+  template cudaError_t launch_real_from_f64<R>(R*, const double*, long long, cudaStream_t);                 \
+  template cudaError_t launch_pack_f64<R>(cpx<R>*, const double*, const double*, long long, cudaStream_t);
+QF_INST(float)
+QF_INST(double)
+#undef QF_INST
+
+}  // namespace qf
