@@ -1,0 +1,448 @@
+"""Benchmark of the imaginary-time step on one GB300 (or N replicas under torchrun).
+
+One bench step = one check interval of a solve: 64 imaginary-time steps of the fused
+FFT kinetic step (forward FFT, T(k) multiply, inverse FFT, coef_A/coef_B update), the
+FP64 norm/energy reduction and renormalisation of the check, the snapshot, then the
+Gram-Schmidt extraction of the ground and two excited states from the three latest
+snapshots (with their FP64 energies) and a parity projection of the first excited
+state.  Metric: site-updates/s = N^3 * 64 per bench step / time.
+
+Default workload: N = 256^3, a = 0.05, relativistic kinetic term (Eq. HK3) with m = 0.3,
+Coulomb + linear potential (kappa 0.4, sigma 0.2), dtau = a/4, complex FP32 fields with
+FP64 reductions.  Each field is 134 MB (> 126 MB L2) and a step streams three of them,
+so no L2 flush is needed between timed steps.
+
+``--impl reference`` times the FP64 CPU oracle (oracle/) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2211_10185_gb300 import inputs as I  # noqa: E402
+
+CHUNK = 64
+METRIC = "site-updates/s (fused FFT step, N=256)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic_fft_step_n256.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cornell_rel_n256")
+    ap.add_argument("--n", type=int, default=None, help="override the lattice size")
+    ap.add_argument("--precision", default=None, choices=[None, "c64", "c128"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample budget")
+    return ap.parse_args()
+
+
+def workload_config(w, prec):
+    kin = I.KINETIC_NAMES[w["kinetic"]]
+    return {
+        "workload": (f"N={w['n']}^3 a={w['a']} kinetic={kin} m={w['m']} "
+                     f"dtau={'a/4' if w['dtau'] else 'default'} seed={w['seed']} {prec}"),
+        "n": w["n"], "a": w["a"], "kinetic": kin, "mass": w["m"], "precision": prec,
+        "chunk_steps": CHUNK, "check_every": CHUNK, "snap_every": CHUNK,
+        "per_step": "64 steps + check + snapshot + 3-state Gram-Schmidt + energies + parity",
+        "l2": "no flush: inputs larger than L2 (3 fields of 8 N^3 bytes per step)",
+    }
+
+
+def make_inputs(w):
+    n = w["n"]
+    v = w["potential"](n, w["a"])
+    psi0 = I.gaussian_field(n, w["seed"])
+    if w["kinetic"] == I.FDTD:
+        psi0 = I.zero_dirichlet_planes(psi0)
+    return v, psi0
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------------------
+def oracle_rate(w, v, psi0, seconds, min_steps=2):
+    """Times the FP64 oracle (as it stands) on imaginary-time steps of the same workload
+    for about ``seconds``; returns (site-updates/s, steps timed, seconds)."""
+    from oracle import qfdtd_oracle as O
+
+    n = w["n"]
+    lat = O.Lattice(n, w["a"])
+    if np.iscomplexobj(v):
+        lat.set_potential(v.real, v.imag)
+    else:
+        lat.set_potential(v)
+    lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+    lat.set_wavefunction(psi0)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        lat.step_n(1, check_every=CHUNK)
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= min_steps and el >= seconds:
+            break
+    return n ** 3 * steps / el, steps, el
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores; one bench step = one oracle
+    imaginary-time step of the same workload (a check step every 64)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import qfdtd_oracle as O
+
+    w = I.workload(args.workload, args.n)
+    v, psi0 = make_inputs(w)
+    lat = O.Lattice(w["n"], w["a"])
+    if np.iscomplexobj(v):
+        lat.set_potential(v.real, v.imag)
+    else:
+        lat.set_potential(v)
+    lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+    lat.set_wavefunction(psi0)
+    for _ in range(args.warmup):
+        lat.step_n(1, check_every=CHUNK)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lat.step_n(1, check_every=CHUNK)
+    el = time.perf_counter() - t0
+    rate = w["n"] ** 3 * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "site-updates/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded SplitMix64/Box-Muller psi0, analytic potential)",
+        "config": workload_config(w, "c128 (FP64 oracle)"),
+        "cpu_baseline": {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} oracle imaginary-time steps of the N={w['n']} workload "
+                                   f"({el:.1f} s; numpy FFT, one thread)"},
+        "e2e": {"value": rate, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in out.strip().splitlines():
+            parts = [p.strip() for p in row.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# Roofline bookkeeping
+# ---------------------------------------------------------------------------------------
+def bytes_per_site(kernel, prec, v_real):
+    c = 8 if prec == "c64" else 16
+    r = c // 2
+    vb = r if v_real else c
+    table = {
+        "fft_x_fwd": 2 * c, "fft_y_fwd": 2 * c, "fft_z_mid_T": 2 * c, "fft_y_inv": 2 * c,
+        "fft_x_inv_update": 3 * c + vb, "stencil_step": 2 * c + vb,
+    }
+    return table.get(kernel)
+
+
+def source_digest():
+    h = hashlib.sha256()
+    for f in ("qf_fft.cu", "qf_common.cuh", "qf_stencil.cu"):
+        with open(os.path.join(ROOT, "paper_2211_10185_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel, n, prec):
+    try:
+        rec = json.load(open(TRAFFIC_FILE))
+    except (OSError, ValueError):
+        return None, "no committed ncu traffic summary"
+    if rec.get("source_digest") != source_digest():
+        return None, "kernels changed since the ncu capture"
+    k = rec.get("kernels", {}).get(kernel)
+    if not k or rec.get("n") != n or rec.get("precision") != prec:
+        return None, "no capture for this kernel/workload"
+    return k["dram_bytes_per_launch"], rec.get("command")
+
+
+def hbm_peak():
+    try:
+        p = json.load(open(PEAKS_FILE))
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------------------
+# cuFFT comparator (context only): torch.fft on the same step, c64
+# ---------------------------------------------------------------------------------------
+def cufft_comparator(w, v, psi0, steps=10):
+    import torch
+
+    n, a, m = w["n"], w["a"], w["m"]
+    dt = w["dtau"] or 0.0
+    k = 2 * np.pi * np.where(np.arange(n) <= n // 2, np.arange(n), np.arange(n) - n) / n
+    kh = 4 * np.sin(k / 2) ** 2
+    if w["kinetic"] == I.FFT_NAIVE:
+        s = k * k
+    else:
+        s = kh
+    S = s[:, None, None] + s[None, :, None] + s[None, None, :]
+    if w["kinetic"] == I.FFT_REL:
+        T = np.sqrt(S + (a * m) ** 2) / a
+    else:
+        T = S / (2 * a * a * m)
+    dev = torch.device("cuda")
+    Tt = torch.tensor(T, dtype=torch.float32, device=dev)
+    vt = torch.tensor(np.asarray(v), dtype=torch.complex64, device=dev)
+    d = 1 + 0.5 * dt * vt
+    B = 1 / d
+    A = (2 - d) * B
+    psi = torch.tensor(psi0, dtype=torch.complex64, device=dev)
+
+    def one():
+        nonlocal psi
+        h = torch.fft.ifftn(Tt * torch.fft.fftn(psi))
+        psi = A * psi - (B * dt) * h
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        one()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"impl": "torch.fft (cuFFT) + torch elementwise, c64, precomputed A/B and T",
+            "ms_per_step": ms, "site_updates_per_s": n ** 3 / (ms * 1e-3)}
+
+
+# ---------------------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from oracle import qfdtd_oracle as O  # noqa: F401  (cpu_baseline only, rank 0)
+    from paper_2211_10185_gb300 import build as B
+    from paper_2211_10185_gb300 import qfdtd as Q
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    w = I.workload(args.workload, args.n)
+    prec = args.precision or w["precision"]
+    n = w["n"]
+    v, psi0 = make_inputs(w)
+    v_real = not np.iscomplexobj(v)
+
+    lat = Lattice(n, w["a"], precision=prec)
+    lat.set_potential(v)
+    lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+    lat.set_wavefunction(psi0)
+
+    def bench_step():
+        lat.step_n(CHUNK, tol=0.0, check_every=CHUNK, snap_every=CHUNK)
+        ex = lat.project_excited(3)
+        lat.parity_project(Q.QF_P_MINUS_PK, 3, 1)
+        return ex
+
+    # fill the snapshot ring (3 snapshots) before the warm-up
+    lat.step_n(3 * CHUNK, tol=0.0, check_every=CHUNK, snap_every=CHUNK)
+    for _ in range(max(3, args.warmup)):
+        bench_step()
+    torch.cuda.synchronize()
+
+    stream = lat.stream
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    launches0 = lat.info()["launches"]
+    lat.profile(True)
+    lat.profile_read(reset=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ex = bench_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    prof = lat.profile_read(reset=True)
+    lat.profile(False)
+    launches = lat.info()["launches"] - launches0
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+
+    units_per_rank = n ** 3 * CHUNK * args.steps
+    value = world * units_per_rank / (ms_total * 1e-3)
+    ms_per_step = ms_total / args.steps
+
+    # roofline of the dominant kernel (largest share of the timed device time)
+    peak, peak_src = hbm_peak()
+    dom = max(((k, v_) for k, v_ in prof.items() if bytes_per_site(k, prec, v_real)),
+              key=lambda kv: kv[1][1], default=None)
+    roof = None
+    kernels = {}
+    for k, (cnt, tot) in prof.items():
+        kernels[k] = {"launches": cnt, "avg_us": 1e3 * tot / cnt, "share": tot / ms_total}
+    if dom:
+        k, (cnt, tot) = dom
+        avg_s = tot / cnt * 1e-3
+        alg = bytes_per_site(k, prec, v_real) * n ** 3
+        achieved = alg / avg_s / 1e9
+        traffic, tsrc = load_traffic(k, n, prec)
+        roof = {"bound": "hbm", "kernel": k, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
+                "traffic_source": tsrc}
+    step_bytes = (3 * (8 if prec == "c64" else 16) + ((4 if prec == "c64" else 8) if v_real else (8 if prec == "c64" else 16)))
+    step_frac = step_bytes * units_per_rank / (ms_total * 1e-3) / 1e9 / peak
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "site-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == "c64" else "f64",
+            "data": "synthetic (seeded SplitMix64/Box-Muller psi0, analytic Cornell potential); replicas per GPU",
+            "config": dict(workload_config(w, prec), parallelism=f"replicas x{world}"),
+            "roofline": roof,
+            "kernels": kernels,
+            "step_algorithmic_hbm": {"bytes_per_site_update": step_bytes,
+                                     "frac_of_peak": step_frac,
+                                     "note": "minimum bytes of one step (read psi, V; write psi') / step time"},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "energies_last_step": [e["e"].real for e in ex],
+        }
+    # end-to-end through the public API with host buffers: upload psi0 (pinned FP64) each
+    # step, run the step, read the energies back
+    if not args.no_e2e:
+        host = torch.empty(2 * n ** 3, dtype=torch.float64, pin_memory=True)
+        host.numpy()[:] = psi0.reshape(-1).view(np.float64)
+        hv = host.numpy()
+        e_steps = max(3, min(args.steps, 10))
+
+        def e2e_step():
+            lat.set_wavefunction_raw(hv)
+            return bench_step()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        if out is not None:
+            out["e2e"] = {"value": world * n ** 3 * CHUNK * e_steps / el, "unit": "site-updates/s",
+                          "h2d_bytes_per_step": 16 * n ** 3, "d2h_bytes_per_step": 4 * 24,
+                          "steps": e_steps,
+                          "note": "host wall clock; FP64 psi0 uploaded from pinned memory each step, "
+                                  "4 energy records (check + 3 states) read back"}
+    if out is not None and not args.no_comparator and world == 1 and w["kinetic"] != I.FDTD:
+        try:
+            out["comparator_cufft"] = cufft_comparator(w, v, psi0)
+        except Exception as exc:  # context only
+            out["comparator_cufft"] = {"error": str(exc)[:200]}
+    if out is not None and world == 1 and not args.no_cpu_baseline:
+        rate, steps, el = oracle_rate(w, v, psi0, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                               "sample": f"{steps} FP64 oracle imaginary-time steps of the same N={n} workload "
+                                         f"({el:.1f} s, numpy FFT, one thread)"}
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    lat.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

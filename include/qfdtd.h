@@ -95,7 +95,14 @@ typedef struct {
   int kinetic;        /* qf_kinetic, -1 before qf_set_kinetic                         */
   int n_snapshots;    /* snapshots currently held (<= n_snap)                        */
   size_t workspace_bytes;
+  int64_t launches;   /* kernels this handle has launched so far                     */
 } qf_info;
+
+typedef struct {
+  char name[24];      /* kernel kind, e.g. "fft_z_mid_T", "fft_x_inv_update"          */
+  int64_t launches;   /* launches timed                                               */
+  double total_ms;    /* summed CUDA-event duration of those launches                 */
+} qf_kernel_stat;
 
 /* Device workspace a lattice with this description needs (bytes, 256-byte aligned
  * start expected).  QF_EINVAL for an unsupported description. */
@@ -158,6 +165,17 @@ qf_status qf_get_info(qf_lattice* lat, qf_info* out);
 /* Device pointer to a field (slot as in qf_get_wavefunction), for zero-copy access by
  * the caller on the handle's stream.  Elements are complex FP32 or FP64 pairs. */
 qf_status qf_field_pointer(qf_lattice* lat, int slot, void** dev_ptr);
+
+/* Per-kernel timing (no counterpart in the paper; measurement support).  enable != 0
+ * brackets every kernel launch of this handle with CUDA events recorded on its stream
+ * (event pool created on first use); enable == 0 stops and harvests.  Timing adds two
+ * event records per launch and no device work. */
+qf_status qf_profile(qf_lattice* lat, int enable);
+
+/* Synchronises the handle's stream, folds finished timings into per-kind totals and
+ * copies up to max of them to out; *count receives the number of kinds with launches.
+ * reset != 0 clears the totals afterwards. */
+qf_status qf_profile_read(qf_lattice* lat, qf_kernel_stat* out, int max, int* count, int reset);
 
 /* Message of the last failure of this handle ("" if none); static text for NULL. */
 const char* qf_last_error(const qf_lattice* lat);

@@ -8,6 +8,7 @@
 
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/qfdtd.h"
 #include "qf_common.cuh"
@@ -26,6 +27,16 @@ static const size_t kAlign = 256;
 static const size_t kStageBytes = size_t(32) << 20;  // host<->device staging, FP64 pairs
 
 static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Kernel kinds for the per-kernel timing of qf_profile.
+enum KernelKind {
+  K_FFT_X_FWD = 0, K_FFT_Y_FWD, K_FFT_Z_MID, K_FFT_Y_INV, K_FFT_X_INV_UPDATE, K_STENCIL, K_FINISH, K_GS_DOTS,
+  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_NUM_KINDS
+};
+static const char* kKindNames[K_NUM_KINDS] = {"fft_x_fwd", "fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
+                                               "fft_x_inv_update", "stencil_step", "finish_sums", "gs_dots",
+                                               "gs_axpy", "scale_copy", "parity", "convert"};
+static const int kEventPool = 4096;
 
 struct Layout {
   size_t field = 0, f[2] = {0, 0}, v = 0, snaps = 0, states = 0, tw = 0, sym = 0, partials = 0, scalars = 0,
@@ -95,6 +106,17 @@ struct qf_lattice {
   int snap_count = 0, snap_head = -1;  // snap_head: slot of the latest snapshot
   bool have_states[3] = {false, false, false};
   std::string err;
+  // launch accounting and optional CUDA-event timing per kernel kind
+  int64_t launches = 0;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_free;
+  struct Pend {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pend> pend;
+  int64_t prof_count[K_NUM_KINDS] = {};
+  double prof_ms[K_NUM_KINDS] = {};
 
   void* field(int i) const { return ws + L.f[i]; }
   void* psi() const { return field(live); }
@@ -119,6 +141,41 @@ static qf_status cuda_fail(qf_lattice* lat, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                                 \
     if (e_ != cudaSuccess) return cuda_fail(lat, e_, #call); \
   } while (0)
+
+// Reads back the timings of finished launches (the stream must be synchronised).
+static void prof_harvest(qf_lattice* lat) {
+  for (auto& p : lat->pend) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      lat->prof_count[p.kind] += 1;
+      lat->prof_ms[p.kind] += ms;
+    }
+    lat->ev_free.push_back(p.a);
+    lat->ev_free.push_back(p.b);
+  }
+  lat->pend.clear();
+}
+
+// Runs one kernel launch f(); counts it and, when profiling, brackets it with events.
+template <typename F>
+static cudaError_t launch(qf_lattice* lat, int kind, F&& f) {
+  lat->launches += 1;
+  if (!lat->prof) return f();
+  if (lat->ev_free.size() < 2) {
+    cudaError_t e = cudaStreamSynchronize(lat->st);
+    if (e != cudaSuccess) return e;
+    prof_harvest(lat);
+  }
+  cudaEvent_t a = lat->ev_free.back();
+  lat->ev_free.pop_back();
+  cudaEvent_t b = lat->ev_free.back();
+  lat->ev_free.pop_back();
+  cudaEventRecord(a, lat->st);
+  cudaError_t e = f();
+  cudaEventRecord(b, lat->st);
+  lat->pend.push_back({kind, a, b});
+  return e;
+}
 
 static bool desc_ok(const qf_lattice_desc* d) {
   return d && valid_n(d->n) && d->a > 0 && isfinite(d->a) && (d->prec == QF_PREC_C64 || d->prec == QF_PREC_C128) &&
@@ -182,6 +239,8 @@ extern "C" qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws
 extern "C" qf_status qf_destroy_lattice(qf_lattice* lat) {
   if (!lat) return QF_OK;
   cudaStreamSynchronize(lat->st);
+  prof_harvest(lat);
+  for (cudaEvent_t e : lat->ev_free) cudaEventDestroy(e);
   delete lat;
   return QF_OK;
 }
@@ -195,7 +254,7 @@ static qf_status staged_upload(qf_lattice* lat, const double* host, long long n,
     const long long cnt = (n - first < chunk) ? n - first : chunk;
     QF_CUDA(lat, cudaMemcpyAsync(lat->stage(), host + first * per_item, cnt * per_item * sizeof(double),
                                  cudaMemcpyHostToDevice, lat->st));
-    QF_CUDA(lat, fn(lat->stage(), first, cnt));
+    QF_CUDA(lat, launch(lat, K_CONVERT, [&] { return fn(lat->stage(), first, cnt); }));
     // the staging area is reused by the next chunk
     QF_CUDA(lat, cudaStreamSynchronize(lat->st));
   }
@@ -222,10 +281,11 @@ extern "C" qf_status qf_set_potential(qf_lattice* lat, const double* v_re, const
       double* im = lat->stage() + chunk;
       QF_CUDA(lat, cudaMemcpyAsync(re, v_re + first, cnt * sizeof(double), cudaMemcpyHostToDevice, lat->st));
       QF_CUDA(lat, cudaMemcpyAsync(im, v_im + first, cnt * sizeof(double), cudaMemcpyHostToDevice, lat->st));
-      cudaError_t e = lat->c64()
-                          ? launch_pack_f64<float>(reinterpret_cast<cpx<float>*>(vbase) + first, re, im, cnt, lat->st)
-                          : launch_pack_f64<double>(reinterpret_cast<cpx<double>*>(vbase) + first, re, im, cnt,
-                                                    lat->st);
+      cudaError_t e = launch(lat, K_CONVERT, [&] {
+        return lat->c64()
+                   ? launch_pack_f64<float>(reinterpret_cast<cpx<float>*>(vbase) + first, re, im, cnt, lat->st)
+                   : launch_pack_f64<double>(reinterpret_cast<cpx<double>*>(vbase) + first, re, im, cnt, lat->st);
+      });
       QF_CUDA(lat, e);
       QF_CUDA(lat, cudaStreamSynchronize(lat->st));
     }
@@ -311,11 +371,12 @@ extern "C" qf_status qf_get_wavefunction(qf_lattice* lat, int slot, double* re_i
   const long long chunk = (long long)(lat->L.stage_bytes / sizeof(double)) / 2;
   for (long long first = 0; first < lat->sites; first += chunk) {
     const long long cnt = (lat->sites - first < chunk) ? lat->sites - first : chunk;
-    cudaError_t e = lat->c64()
-                        ? launch_to_f64<float>(lat->stage(), reinterpret_cast<cpx<float>*>(src) + first, nullptr, cnt,
-                                               lat->st)
+    cudaError_t e = launch(lat, K_CONVERT, [&] {
+      return lat->c64() ? launch_to_f64<float>(lat->stage(), reinterpret_cast<cpx<float>*>(src) + first, nullptr,
+                                               cnt, lat->st)
                         : launch_to_f64<double>(lat->stage(), reinterpret_cast<cpx<double>*>(src) + first, nullptr,
                                                 cnt, lat->st);
+    });
     QF_CUDA(lat, e);
     QF_CUDA(lat, cudaMemcpyAsync(re_im + 2 * first, lat->stage(), cnt * 2 * sizeof(double), cudaMemcpyDeviceToHost,
                                  lat->st));
@@ -345,11 +406,11 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
       StencilArgs<float> s{reinterpret_cast<const cpx<float>*>(in), reinterpret_cast<cpx<float>*>(out), v,
                            lat->v_real, (float)kc, (float)(0.5 * dt), (float)dt, scale, lat->partials(),
                            write ? 1 : 0, reduce ? 1 : 0};
-      return launch_stencil<float>(n, s, lat->st, nblocks);
+      return launch(lat, K_STENCIL, [&] { return launch_stencil<float>(n, s, lat->st, nblocks); });
     }
     StencilArgs<double> s{reinterpret_cast<const cpx<double>*>(in), reinterpret_cast<cpx<double>*>(out), v,
                           lat->v_real, kc, 0.5 * dt, dt, scale, lat->partials(), write ? 1 : 0, reduce ? 1 : 0};
-    return launch_stencil<double>(n, s, lat->st, nblocks);
+    return launch(lat, K_STENCIL, [&] { return launch_stencil<double>(n, s, lat->st, nblocks); });
   }
   // FFT terms: in place on `in` (out must equal in when writing); tmp is scratch
   const double n3 = (double)n * n * n;
@@ -371,7 +432,13 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
     p.partials = lat->partials();
     p.write_psi = write ? 1 : 0;
     p.reduce = reduce ? 1 : 0;
-    return launch_fft_step<float>(n, p, reinterpret_cast<cpx<float>*>(lat->tmp()), lat->st, nblocks);
+    cpx<float>* tmp = reinterpret_cast<cpx<float>*>(lat->tmp());
+    for (int ps = 0; ps < kFftPasses; ++ps) {
+      cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
+                             [&] { return launch_fft_pass<float>(n, ps, p, tmp, lat->st, nblocks); });
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   FftPassArgs<double> p{};
   p.twiddle = reinterpret_cast<const cpx<double>*>(lat->ws + lat->L.tw);
@@ -388,12 +455,19 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
   p.partials = lat->partials();
   p.write_psi = write ? 1 : 0;
   p.reduce = reduce ? 1 : 0;
-  return launch_fft_step<double>(n, p, reinterpret_cast<cpx<double>*>(lat->tmp()), lat->st, nblocks);
+  cpx<double>* tmp = reinterpret_cast<cpx<double>*>(lat->tmp());
+  for (int ps = 0; ps < kFftPasses; ++ps) {
+    cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
+                           [&] { return launch_fft_pass<double>(n, ps, p, tmp, lat->st, nblocks); });
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 static qf_status read_energy(qf_lattice* lat, double* e3) {
   QF_CUDA(lat, cudaMemcpyAsync(e3, lat->sc()->energy, 3 * sizeof(double), cudaMemcpyDeviceToHost, lat->st));
   QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  if (lat->prof) prof_harvest(lat);
   return QF_OK;
 }
 
@@ -419,7 +493,7 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
     QF_CUDA(lat, kinetic_pass(lat, in, out, true, check, scale, &nb));
     lat->pending_scale = false;
     if (check) {
-      QF_CUDA(lat, launch_finish(lat->partials(), nb, lat->sc(), 1, lat->st));
+      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 1, lat->st); }));
       lat->pending_scale = true;
     }
     if (fdtd) lat->live = 1 - lat->live;
@@ -473,7 +547,7 @@ static qf_status measure(qf_lattice* lat, void* f, qf_energy* out) {
   int nb = 0;
   // FFT terms transform through tmp and read f; FDTD reads f only
   QF_CUDA(lat, kinetic_pass(lat, f, f, false, true, &lat->sc()->scale[0], &nb));
-  QF_CUDA(lat, launch_finish(lat->partials(), nb, lat->sc(), 0, lat->st));
+  QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 0, lat->st); }));
   double e3[3];
   qf_status s = read_energy(lat, e3);
   if (s != QF_OK) return s;
@@ -499,18 +573,18 @@ static qf_status gram_schmidt(qf_lattice* lat, int n_states) {
                               reinterpret_cast<const cpx<R>*>(lat->state(1))};
     const int nb = i;
     // classical Gram-Schmidt against v_0..v_{i-1}, then one re-orthogonalisation pass
-    QF_CUDA(lat, launch_dots<R>(basis, nb, src, lat->sites, lat->partials(), nblk, lat->st));
-    QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st));
-    QF_CUDA(lat, launch_axpy_basis<R>(w, src, basis, nb, coef, lat->sites, lat->st));
+    QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(basis, nb, src, lat->sites, lat->partials(), nblk, lat->st); }));
+    QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st); }));
+    QF_CUDA(lat, launch(lat, K_GS_AXPY, [&] { return launch_axpy_basis<R>(w, src, basis, nb, coef, lat->sites, lat->st); }));
     if (nb > 0) {
-      QF_CUDA(lat, launch_dots<R>(basis, nb, w, lat->sites, lat->partials(), nblk, lat->st));
-      QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st));
-      QF_CUDA(lat, launch_axpy_basis<R>(w, w, basis, nb, coef, lat->sites, lat->st));
-      QF_CUDA(lat, launch_dots<R>(basis, 0, w, lat->sites, lat->partials(), nblk, lat->st));
-      QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st));
+      QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(basis, nb, w, lat->sites, lat->partials(), nblk, lat->st); }));
+      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st); }));
+      QF_CUDA(lat, launch(lat, K_GS_AXPY, [&] { return launch_axpy_basis<R>(w, w, basis, nb, coef, lat->sites, lat->st); }));
+      QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(basis, 0, w, lat->sites, lat->partials(), nblk, lat->st); }));
+      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st); }));
     }
     // normalise: coef[5] = 1/||w||
-    QF_CUDA(lat, launch_scale_copy<R>(w, w, coef + 5, lat->sites, lat->st));
+    QF_CUDA(lat, launch(lat, K_SCALE_COPY, [&] { return launch_scale_copy<R>(w, w, coef + 5, lat->sites, lat->st); }));
     lat->have_states[i] = true;
   }
   return QF_OK;
@@ -534,11 +608,11 @@ template <typename R>
 static qf_status parity_t(qf_lattice* lat, int which, int axis, void* target) {
   const int nblk = field_blocks();
   cpx<R>* tmp = reinterpret_cast<cpx<R>*>(lat->tmp());
-  QF_CUDA(lat, launch_parity<R>(tmp, reinterpret_cast<const cpx<R>*>(target), lat->d.n, which, axis, lat->partials(),
-                                nblk, lat->st));
+  QF_CUDA(lat, launch(lat, K_PARITY, [&] { return launch_parity<R>(tmp, reinterpret_cast<const cpx<R>*>(target), lat->d.n, which, axis, lat->partials(),
+                                nblk, lat->st); }));
   double* coef = lat->sc()->gs_coef;
-  QF_CUDA(lat, launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st));
-  QF_CUDA(lat, launch_scale_copy<R>(reinterpret_cast<cpx<R>*>(target), tmp, coef + 5, lat->sites, lat->st));
+  QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st); }));
+  QF_CUDA(lat, launch(lat, K_SCALE_COPY, [&] { return launch_scale_copy<R>(reinterpret_cast<cpx<R>*>(target), tmp, coef + 5, lat->sites, lat->st); }));
   QF_CUDA(lat, cudaStreamSynchronize(lat->st));
   return QF_OK;
 }
@@ -564,6 +638,48 @@ extern "C" qf_status qf_get_info(qf_lattice* lat, qf_info* out) {
   out->kinetic = lat->kinetic;
   out->n_snapshots = lat->snap_count;
   out->workspace_bytes = lat->L.total;
+  out->launches = lat->launches;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_profile(qf_lattice* lat, int enable) {
+  if (!lat) return QF_EINVAL;
+  if (enable && lat->ev_free.empty() && lat->pend.empty()) {
+    for (int i = 0; i < kEventPool; ++i) {
+      cudaEvent_t e;
+      QF_CUDA(lat, cudaEventCreate(&e));
+      lat->ev_free.push_back(e);
+    }
+  }
+  if (!enable) {
+    QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+    prof_harvest(lat);
+  }
+  lat->prof = enable != 0;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_profile_read(qf_lattice* lat, qf_kernel_stat* out, int max, int* count, int reset) {
+  if (!lat || (max > 0 && !out)) return QF_EINVAL;
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  prof_harvest(lat);
+  int c = 0;
+  for (int k = 0; k < K_NUM_KINDS; ++k) {
+    if (lat->prof_count[k] == 0) continue;
+    if (c < max) {
+      memset(out[c].name, 0, sizeof(out[c].name));
+      strncpy(out[c].name, kKindNames[k], sizeof(out[c].name) - 1);
+      out[c].launches = lat->prof_count[k];
+      out[c].total_ms = lat->prof_ms[k];
+    }
+    ++c;
+  }
+  if (count) *count = c;
+  if (reset)
+    for (int k = 0; k < K_NUM_KINDS; ++k) {
+      lat->prof_count[k] = 0;
+      lat->prof_ms[k] = 0;
+    }
   return QF_OK;
 }
 

@@ -130,9 +130,13 @@ __device__ __forceinline__ void block_sum_store(double (&s)[NV], double* scratch
 }
 
 // ---- launchers (return cudaError_t of the launch) ------------------------------------
-// FFT kinetic step: psi_{t+1} = s (coef_A psi_t - coef_B dtau H_K psi_t); tmp is scratch.
+// FFT kinetic step psi_{t+1} = s (coef_A psi_t - coef_B dtau H_K psi_t) is five passes
+// (0: x forward psi -> tmp, 1: y forward, 2: z forward x T(k) z inverse, 3: y inverse,
+// 4: x inverse + update/sums); tmp is scratch.  nblocks_final: grid of the reducing pass.
+constexpr int kFftPasses = 5;
 template <typename R>
-cudaError_t launch_fft_step(int n, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nblocks_final);
+cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st,
+                            int* nblocks_final);
 // Number of blocks the reducing (final) pass of the FFT step uses for lattice size n.
 template <typename R>
 int fft_final_blocks(int n);
@@ -171,6 +175,10 @@ cudaError_t launch_to_f64(double* dst, const cpx<R>* src, const double* s, long 
                           cudaStream_t st);
 template <typename R>
 cudaError_t launch_real_from_f64(R* dst, const double* src, long long n, cudaStream_t st);
+template <typename R>
+cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, long long n, cudaStream_t st);
 int field_blocks();
+int fft_twiddle_count(int n);
+void fft_twiddles(int n, double* re_im);
 
 }  // namespace qf

@@ -432,13 +432,13 @@ static size_t smem_s() {
 }
 
 template <typename R, int N>
-static cudaError_t step_n(FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
+static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
   using G = Geom<R, N>;
   const int gx = N * N / G::LC, gs = (N / G::L) * (N / G::P);
   const size_t sx = smem_x<R, N>(), ss = smem_s<R, N>();
   static bool attr_done = false;
   if (!attr_done) {
-    // tiles stay below 48 KB for every supported N except the largest; raise the limit
+    // the largest tiles need more than the default 48 KB of dynamic shared memory
     cudaFuncSetAttribute(fft_x_kernel<R, N, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
     cudaFuncSetAttribute(fft_x_kernel<R, N, OP_FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
@@ -447,16 +447,16 @@ static cudaError_t step_n(FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* n
     attr_done = true;
   }
   if (nfinal) *nfinal = gx;
-  if (a.write_psi || a.reduce) {
-    FftPassArgs<R> p = a;
-    p.src = a.psi;
-    p.data = tmp;
-    fft_x_kernel<R, N, OP_FWD><<<gx, G::THREADS_X, sx, st>>>(p);
-    fft_s_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p);
-    fft_s_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(p);
-    fft_s_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p);
-    p.src = nullptr;
-    fft_x_kernel<R, N, OP_FINAL><<<gx, G::THREADS_X, sx, st>>>(p);
+  FftPassArgs<R> p = a;
+  p.data = tmp;
+  p.src = (pass == 0) ? a.psi : nullptr;
+  switch (pass) {
+    case 0: fft_x_kernel<R, N, OP_FWD><<<gx, G::THREADS_X, sx, st>>>(p); break;
+    case 1: fft_s_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p); break;
+    case 2: fft_s_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(p); break;
+    case 3: fft_s_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p); break;
+    case 4: fft_x_kernel<R, N, OP_FINAL><<<gx, G::THREADS_X, sx, st>>>(p); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -464,11 +464,11 @@ static cudaError_t step_n(FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* n
 bool fft_supported(int n) { return plan_stages(n) > 0; }
 
 template <typename R>
-cudaError_t launch_fft_step(int n, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
+cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
   switch (n) {
 #define QF_CASE(NN) \
   case NN:          \
-    return step_n<R, NN>(args, tmp, st, nfinal);
+    return pass_n<R, NN>(pass, args, tmp, st, nfinal);
     QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
     QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
 #undef QF_CASE
@@ -525,8 +525,8 @@ void fft_twiddles(int n, double* re_im) {
   }
 }
 
-template cudaError_t launch_fft_step<float>(int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
-template cudaError_t launch_fft_step<double>(int, FftPassArgs<double>, cpx<double>*, cudaStream_t, int*);
+template cudaError_t launch_fft_pass<float>(int, int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
+template cudaError_t launch_fft_pass<double>(int, int, FftPassArgs<double>, cpx<double>*, cudaStream_t, int*);
 template int fft_final_blocks<float>(int);
 template int fft_final_blocks<double>(int);
 

@@ -105,7 +105,18 @@ class Lattice:
         i = Q.qf_info()
         _check(self.h, self.lib.qf_get_info(self.h, C.byref(i)), "qf_get_info")
         return dict(dtau=i.dtau, step=i.step, tau=i.tau, kinetic=i.kinetic, n_snapshots=i.n_snapshots,
-                    workspace_bytes=i.workspace_bytes)
+                    workspace_bytes=i.workspace_bytes, launches=i.launches)
+
+    def profile(self, enable: bool = True):
+        _check(self.h, self.lib.qf_profile(self.h, int(bool(enable))), "qf_profile")
+
+    def profile_read(self, reset: bool = False) -> dict:
+        """{kernel kind: (launches, total_ms)} of the timed launches so far."""
+        out = (Q.qf_kernel_stat * 32)()
+        cnt = C.c_int()
+        _check(self.h, self.lib.qf_profile_read(self.h, out, 32, C.byref(cnt), int(bool(reset))),
+               "qf_profile_read")
+        return {out[i].name.decode(): (out[i].launches, out[i].total_ms) for i in range(min(cnt.value, 32))}
 
     def field_pointer(self, slot: int = -1) -> int:
         p = C.c_void_p()

@@ -34,7 +34,11 @@ class qf_energy(C.Structure):
 
 class qf_info(C.Structure):
     _fields_ = [("dtau", C.c_double), ("step", C.c_int64), ("tau", C.c_double), ("kinetic", C.c_int),
-                ("n_snapshots", C.c_int), ("workspace_bytes", C.c_size_t)]
+                ("n_snapshots", C.c_int), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64)]
+
+
+class qf_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 24), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
 
 _P = C.c_void_p
@@ -54,6 +58,8 @@ SIGNATURES = {
     "qf_parity_project": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "qf_get_info": (C.c_int, [_P, C.POINTER(qf_info)]),
     "qf_field_pointer": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
+    "qf_profile": (C.c_int, [_P, C.c_int]),
+    "qf_profile_read": (C.c_int, [_P, C.POINTER(qf_kernel_stat), C.c_int, C.POINTER(C.c_int), C.c_int]),
     "qf_last_error": (C.c_char_p, [_P]),
     "qf_version": (C.c_char_p, []),
 }

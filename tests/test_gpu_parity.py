@@ -112,10 +112,14 @@ def test_harmonic_fdtd_converges_like_the_oracle(prec):
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("kind", [O.FDTD, O.FFT_SYMANZIK])
 def test_excited_states_match_oracle_at_identical_snapshots(kind, prec):
+    # The snapshots hold Psi_2 at relative weight ~exp(-2 tau) (gaps of 1).  FP32 fields
+    # resolve it only while that weight is well above the accumulated FP32 rounding noise
+    # (~1e-7 per step), so the c64 comparison uses tau ~ 2.9 and c128 tau ~ 5.8.
     n, a, m = 16, 0.3, 1.0
     ref, gpu = _pair(n, a, kind, m, prec, I.harmonic(n, a), seed=0, dtau=a * a / 8)
-    ref.step_n(8 * 64, check_every=64, snap_every=32)
-    gpu.step_n(8 * 64, check_every=64, snap_every=32)
+    steps = 8 * 64 if prec == "c128" else 4 * 64
+    ref.step_n(steps, check_every=64, snap_every=32)
+    gpu.step_n(steps, check_every=64, snap_every=32)
     st, ex_ref = ref.project_excited(3)
     ex_gpu = gpu.project_excited(3)
     tol = {"c128": [1e-10, 1e-9, 1e-8], "c64": [1e-5, 1e-4, 2e-3]}[prec]
