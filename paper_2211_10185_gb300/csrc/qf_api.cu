@@ -562,29 +562,32 @@ static qf_status measure(qf_lattice* lat, void* f, qf_energy* out) {
 
 template <typename R>
 static qf_status gram_schmidt(qf_lattice* lat, int n_states) {
-  double* coef = lat->sc()->gs_coef;
+  double* coef = lat->sc()->gs_coef;  // [Re c0, Im c0, Re c1, Im c1, |w|^2, 1/|w|]
+  double* part = lat->partials();
   const int nblk = field_blocks();
+  const long long ns = lat->sites;
   for (int i = 0; i < n_states; ++i) {
-    const int j = i;  // i-th latest snapshot
-    const int idx = ((lat->snap_head - j) % lat->d.n_snap + lat->d.n_snap) % lat->d.n_snap;
-    const cpx<R>* src = reinterpret_cast<const cpx<R>*>(lat->snap(idx));
+    const int idx = ((lat->snap_head - i) % lat->d.n_snap + lat->d.n_snap) % lat->d.n_snap;
+    const cpx<R>* src = reinterpret_cast<const cpx<R>*>(lat->snap(idx));  // i-th latest snapshot
     cpx<R>* w = reinterpret_cast<cpx<R>*>(lat->state(i));
     const cpx<R>* basis[2] = {reinterpret_cast<const cpx<R>*>(lat->state(0)),
                               reinterpret_cast<const cpx<R>*>(lat->state(1))};
     const int nb = i;
-    // classical Gram-Schmidt against v_0..v_{i-1}, then one re-orthogonalisation pass
-    QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(basis, nb, src, lat->sites, lat->partials(), nblk, lat->st); }));
-    QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st); }));
-    QF_CUDA(lat, launch(lat, K_GS_AXPY, [&] { return launch_axpy_basis<R>(w, src, basis, nb, coef, lat->sites, lat->st); }));
+    // coefficients <v_j|S_i> (classical Gram-Schmidt: all from the same vector)
+    QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(basis, nb, src, ns, part, nblk, lat->st); }));
+    QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(part, nblk, nb, coef, lat->st); }));
     if (nb > 0) {
-      QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(basis, nb, w, lat->sites, lat->partials(), nblk, lat->st); }));
-      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, nb, coef, lat->st); }));
-      QF_CUDA(lat, launch(lat, K_GS_AXPY, [&] { return launch_axpy_basis<R>(w, w, basis, nb, coef, lat->sites, lat->st); }));
-      QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(basis, 0, w, lat->sites, lat->partials(), nblk, lat->st); }));
-      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st); }));
+      // w = S_i - sum c_j v_j, with <v_j|w> of the result: the re-orthogonalisation pass
+      QF_CUDA(lat, launch(lat, K_GS_AXPY,
+                          [&] { return launch_axpy_dots<R>(w, src, basis, nb, coef, ns, part, nblk, lat->st); }));
+      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(part, nblk, nb, coef, lat->st); }));
+      QF_CUDA(lat, launch(lat, K_GS_AXPY,
+                          [&] { return launch_axpy_dots<R>(w, w, basis, nb, coef, ns, part, nblk, lat->st); }));
+      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(part, nblk, nb, coef, lat->st); }));
+      src = w;
     }
-    // normalise: coef[5] = 1/||w||
-    QF_CUDA(lat, launch(lat, K_SCALE_COPY, [&] { return launch_scale_copy<R>(w, w, coef + 5, lat->sites, lat->st); }));
+    // v_i = w / ||w||  (coef[5] = 1/||w|| of the last pass)
+    QF_CUDA(lat, launch(lat, K_SCALE_COPY, [&] { return launch_scale_copy<R>(w, src, coef + 5, ns, lat->st); }));
     lat->have_states[i] = true;
   }
   return QF_OK;

@@ -129,6 +129,65 @@ __device__ __forceinline__ void block_sum_store(double (&s)[NV], double* scratch
   }
 }
 
+// ---- per-thread sum accumulators ---------------------------------------------------
+// Acc<double>: plain FP64.  Acc<float>: an unevaluated sum hi + lo of two floats
+// ("double-float") updated with error-free transformations -- the product a*b = p + e
+// with e = fma(a, b, -p) (Dekker) and the sum s = x + y with its exact error (Knuth's
+// two-sum) -- so a thread's partial sum keeps ~48 significant bits while running on
+// the FP32 pipes (FP64 throughput on this part is a small fraction of FP32).  Partial
+// sums leave the thread as FP64 and every later stage of a reduction is FP64.
+template <typename R>
+struct Acc;
+template <>
+struct Acc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct Acc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float z = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(x, z));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    add(p);
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+// The five sums of a check: <psi|psi>, Re/Im <psi|H_K psi>, Re/Im <psi|V psi>.
+template <typename R>
+struct CheckSums {
+  Acc<R> n, kr, ki, vr, vi;
+  __device__ __forceinline__ void add(cpx<R> p, cpx<R> h, cpx<R> v) {
+    n.add_prod(p.x, p.x);
+    n.add_prod(p.y, p.y);
+    kr.add_prod(p.x, h.x);
+    kr.add_prod(p.y, h.y);
+    ki.add_prod(p.x, h.y);
+    ki.add_prod(-p.y, h.x);
+    const R w = p.x * p.x + p.y * p.y;
+    vr.add_prod(w, v.x);
+    vi.add_prod(w, v.y);
+  }
+  __device__ __forceinline__ void to(double (&s)[kNumSums]) const {
+    s[0] = n.value();
+    s[1] = kr.value();
+    s[2] = ki.value();
+    s[3] = vr.value();
+    s[4] = vi.value();
+  }
+};
+
 // ---- launchers (return cudaError_t of the launch) ------------------------------------
 // FFT kinetic step psi_{t+1} = s (coef_A psi_t - coef_B dtau H_K psi_t) is five passes
 // (0: x forward psi -> tmp, 1: y forward, 2: z forward x T(k) z inverse, 3: y inverse,
@@ -159,9 +218,12 @@ cudaError_t launch_dots(const cpx<R>* const* basis, int nb, const cpx<R>* w, lon
                         double* partials, int nblocks, cudaStream_t st);
 cudaError_t launch_finish_dots(const double* partials, int nblocks, int nb, double* coef_out,
                                cudaStream_t st);
+// w = src - sum_j c_j v_j (c from coef in device memory) and, of the stored w, the sums
+// <v_j|w> and <w|w> into per-block partials (same layout as launch_dots).
 template <typename R>
-cudaError_t launch_axpy_basis(cpx<R>* w, const cpx<R>* src, const cpx<R>* const* basis, int nb,
-                              const double* coef, long long n_sites, cudaStream_t st);
+cudaError_t launch_axpy_dots(cpx<R>* w, const cpx<R>* src, const cpx<R>* const* basis, int nb,
+                             const double* coef, long long n_sites, double* partials, int nblocks,
+                             cudaStream_t st);
 template <typename R>
 cudaError_t launch_scale_copy(cpx<R>* dst, const cpx<R>* src, const double* s, long long n_sites,
                               cudaStream_t st);

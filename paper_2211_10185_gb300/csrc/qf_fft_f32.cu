@@ -1,0 +1,47 @@
+// Complex FP32 instantiation of the fused FFT kinetic step (kernels in qf_fft_impl.cuh).
+#include <math.h>
+
+#include "qf_fft_impl.cuh"
+
+namespace qf {
+
+template cudaError_t launch_fft_pass<float>(int, int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
+template int fft_final_blocks<float>(int);
+
+bool fft_supported(int n) { return plan_stages(n) > 0; }
+
+// Host-side twiddle table in the per-stage layout the kernels read.
+int fft_twiddle_count(int n) {
+  switch (n) {
+#define QF_CASE(NN) \
+  case NN:          \
+    return plan_tw_size(NN);
+    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
+    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
+#undef QF_CASE
+    default:
+      return 0;
+  }
+}
+
+// Fills tw[off(s) + k (R_s - 1) + r - 1] = exp(-2 pi i r k / (Ns R_s)) in double.
+void fft_twiddles(int n, double* re_im) {
+  const double two_pi = 6.283185307179586476925286766559;
+  int ns = 1, off = 0;
+  for (int s = 0; s < plan_stages(n); ++s) {
+    const int rad = plan_radix(n, s);
+    for (int k = 0; k < ns; ++k)
+      for (int r = 1; r < rad; ++r) {
+        const long long num = (long long)r * k;
+        const long long den = (long long)ns * rad;
+        const double ang = -two_pi * (double)num / (double)den;
+        const int idx = off + k * (rad - 1) + (r - 1);
+        re_im[2 * idx] = cos(ang);
+        re_im[2 * idx + 1] = sin(ang);
+      }
+    off += ns * (rad - 1);
+    ns *= rad;
+  }
+}
+
+}  // namespace qf

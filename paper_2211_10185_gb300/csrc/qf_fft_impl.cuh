@@ -13,6 +13,7 @@
 // y[(j/Ns) Ns R + (j mod Ns) + r Ns], so the output is in natural order.  The first
 // stage reads global memory and the last writes it directly (both coalesced);
 // intermediate stages exchange through shared memory.
+#pragma once
 #include "qf_common.cuh"
 
 namespace qf {
@@ -282,7 +283,9 @@ __device__ __forceinline__ R kin_mult(int kinetic, R sxy, R sz, R tcoef, R am2) 
 // ------------------------------------------------------------------------------------
 // Pass kernels
 // ------------------------------------------------------------------------------------
-enum PassOp : int { OP_FWD = 0, OP_INV = 1, OP_MID = 2, OP_FINAL = 3 };
+// OP_FINAL* are the last x pass: update only, update + check sums, sums only (measure).
+enum PassOp : int { OP_FWD = 0, OP_INV = 1, OP_MID = 2, OP_FINAL = 3, OP_FINAL_SUMS = 4, OP_SUMS = 5 };
+constexpr bool is_final(int op) { return op >= OP_FINAL; }
 
 template <typename R, int N>
 __device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
@@ -290,12 +293,15 @@ __device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
 }
 
 // x pass: LC contiguous lines per block.  OP_FWD: src -> data.  OP_FINAL: data (H_K psi
-// in x-transformed space) -> inverse x -> update of psi.
-template <typename R, int N, int OP>
+// in x-transformed space) -> inverse x -> update of psi.  The final pass loads psi and V
+// of its output sites at the start, so those reads overlap the inverse transform.
+template <typename R, int N, int OP, bool VREAL>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArgs<R> a) {
   using G = Geom<R, N>;
   constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
-  constexpr bool INV = (OP == OP_FINAL);
+  constexpr bool INV = is_final(OP);
+  constexpr bool WRITE = (OP == OP_FINAL || OP == OP_FINAL_SUMS);
+  constexpr bool SUMS = (OP == OP_FINAL_SUMS || OP == OP_SUMS);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cpx<R>* tw_s = reinterpret_cast<cpx<R>*>(smem_raw);
   cpx<R>* data_s = tw_s + G::TW;
@@ -306,12 +312,37 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArg
   const long long base = gline * N;
   load_twiddles<R, N>(tw_s, a.twiddle);
 
-  const cpx<R>* in = (OP == OP_FWD && a.src) ? a.src : a.data;
+  const cpx<R>* __restrict__ in = (OP == OP_FWD && a.src) ? a.src : a.data;
   cpx<R> v[EPT];
 #pragma unroll
   for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
     for (int r = 0; r < R0; ++r) v[b * R0 + r] = in[base + e_in<N, 0>(g, b, r)];
+
+  // final pass: psi and V at the sites this thread will write (natural order)
+  cpx<R> pv[INV ? EPT : 1];
+  cpx<R> vv[INV && !VREAL ? EPT : 1];
+  R vr_[INV && VREAL ? EPT : 1];
+  if constexpr (INV) {
+    const cpx<R>* __restrict__ psi_in = a.psi;
+#pragma unroll
+    for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) pv[b * RL + r] = psi_in[base + e_out<N, S - 1>(g, b, r)];
+    if constexpr (VREAL) {
+      const R* __restrict__ vr = reinterpret_cast<const R*>(a.v);
+#pragma unroll
+      for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) vr_[b * RL + r] = vr[base + e_out<N, S - 1>(g, b, r)];
+    } else {
+      const cpx<R>* __restrict__ vc = reinterpret_cast<const cpx<R>*>(a.v);
+#pragma unroll
+      for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) vv[b * RL + r] = vc[base + e_out<N, S - 1>(g, b, r)];
+    }
+  }
   __syncthreads();  // twiddles visible
 
   Tile<R, N, false> t{data_s, line};
@@ -324,36 +355,30 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArg
       for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r)] = v[b * RL + r];
   } else {
     // v = H_K psi at the sites of this line (the 1/N^3 is inside T).
-    double acc[kNumSums] = {0, 0, 0, 0, 0};
-    const R sc = R(*a.scale);
+    auto vat = [&](int i) { return VREAL ? mk<R>(vr_[VREAL ? i : 0], R(0)) : vv[VREAL ? 0 : i]; };
+    if constexpr (SUMS) {
+      CheckSums<R> cs;
 #pragma unroll
-    for (int b = 0; b < EPT / RL; ++b)
+      for (int i = 0; i < EPT; ++i) cs.add(pv[i], v[i], vat(i));
+      double acc[kNumSums];
+      cs.to(acc);
+      block_sum_store<kNumSums>(acc, red_s, a.partials + (long long)blockIdx.x * kPartialStride);
+    }
+    if constexpr (WRITE) {
+      const R sc = R(*a.scale);
 #pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        const long long site = base + e_out<N, S - 1>(g, b, r);
-        const cpx<R> h = v[b * RL + r];
-        const cpx<R> p = a.psi[site];
-        cpx<R> vv;
-        if (a.v_real) vv = mk<R>(reinterpret_cast<const R*>(a.v)[site], R(0));
-        else vv = reinterpret_cast<const cpx<R>*>(a.v)[site];
-        if (a.reduce) {
-          const double px = p.x, py = p.y, hx = h.x, hy = h.y;
-          const double w = px * px + py * py;
-          acc[0] += w;
-          acc[1] += px * hx + py * hy;   // Re conj(psi) H psi
-          acc[2] += px * hy - py * hx;   // Im
-          acc[3] += w * double(vv.x);
-          acc[4] += w * double(vv.y);
-        }
-        if (a.write_psi) {
+      for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int i = b * RL + r;
           // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d
-          const cpx<R> d = mk<R>(R(1) + a.half_dtau * vv.x, a.half_dtau * vv.y);
-          const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), p) - cscale<R>(h, a.dtau);
+          const cpx<R> vi = vat(i);
+          const cpx<R> d = mk<R>(R(1) + a.half_dtau * vi.x, a.half_dtau * vi.y);
+          const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), pv[i]) - cscale<R>(v[i], a.dtau);
           const R inv = sc / (d.x * d.x + d.y * d.y);
-          a.psi[site] = cscale<R>(cmulc<R>(num, d), inv);
+          a.psi[base + e_out<N, S - 1>(g, b, r)] = cscale<R>(cmulc<R>(num, d), inv);
         }
-      }
-    if (a.reduce) block_sum_store<kNumSums>(acc, red_s, a.partials + (long long)blockIdx.x * kPartialStride);
+    }
   }
 }
 
@@ -431,6 +456,23 @@ static size_t smem_s() {
   return G::TW * sizeof(cpx<R>) + ((N * sizeof(R) + 15) / 16) * 16 + (size_t)G::C * N * sizeof(cpx<R>);
 }
 
+template <typename R, int N, int OP, bool VREAL>
+static void set_smem_attr(size_t bytes) {
+  cudaFuncSetAttribute(fft_x_kernel<R, N, OP, VREAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R, int N, bool VREAL>
+static cudaError_t final_pass(FftPassArgs<R> p, int gx, size_t sx, cudaStream_t st) {
+  using G = Geom<R, N>;
+  if (p.write_psi && p.reduce)
+    fft_x_kernel<R, N, OP_FINAL_SUMS, VREAL><<<gx, G::THREADS_X, sx, st>>>(p);
+  else if (p.write_psi)
+    fft_x_kernel<R, N, OP_FINAL, VREAL><<<gx, G::THREADS_X, sx, st>>>(p);
+  else
+    fft_x_kernel<R, N, OP_SUMS, VREAL><<<gx, G::THREADS_X, sx, st>>>(p);
+  return cudaGetLastError();
+}
+
 template <typename R, int N>
 static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
   using G = Geom<R, N>;
@@ -439,8 +481,13 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
   static bool attr_done = false;
   if (!attr_done) {
     // the largest tiles need more than the default 48 KB of dynamic shared memory
-    cudaFuncSetAttribute(fft_x_kernel<R, N, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
-    cudaFuncSetAttribute(fft_x_kernel<R, N, OP_FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
+    set_smem_attr<R, N, OP_FWD, false>(sx);
+    set_smem_attr<R, N, OP_FINAL, false>(sx);
+    set_smem_attr<R, N, OP_FINAL, true>(sx);
+    set_smem_attr<R, N, OP_FINAL_SUMS, false>(sx);
+    set_smem_attr<R, N, OP_FINAL_SUMS, true>(sx);
+    set_smem_attr<R, N, OP_SUMS, false>(sx);
+    set_smem_attr<R, N, OP_SUMS, true>(sx);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
@@ -451,17 +498,15 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
   p.data = tmp;
   p.src = (pass == 0) ? a.psi : nullptr;
   switch (pass) {
-    case 0: fft_x_kernel<R, N, OP_FWD><<<gx, G::THREADS_X, sx, st>>>(p); break;
+    case 0: fft_x_kernel<R, N, OP_FWD, false><<<gx, G::THREADS_X, sx, st>>>(p); break;
     case 1: fft_s_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 2: fft_s_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 3: fft_s_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p); break;
-    case 4: fft_x_kernel<R, N, OP_FINAL><<<gx, G::THREADS_X, sx, st>>>(p); break;
+    case 4: return a.v_real ? final_pass<R, N, true>(p, gx, sx, st) : final_pass<R, N, false>(p, gx, sx, st);
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
-
-bool fft_supported(int n) { return plan_stages(n) > 0; }
 
 template <typename R>
 cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
@@ -490,44 +535,5 @@ int fft_final_blocks(int n) {
       return 0;
   }
 }
-
-// Host-side twiddle table in the per-stage layout the kernels read.
-int fft_twiddle_count(int n) {
-  switch (n) {
-#define QF_CASE(NN) \
-  case NN:          \
-    return plan_tw_size(NN);
-    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
-    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
-#undef QF_CASE
-    default:
-      return 0;
-  }
-}
-
-// Fills tw[off(s) + k (R_s - 1) + r - 1] = exp(-2 pi i r k / (Ns R_s)) in double.
-void fft_twiddles(int n, double* re_im) {
-  const double two_pi = 6.283185307179586476925286766559;
-  int ns = 1, off = 0;
-  for (int s = 0; s < plan_stages(n); ++s) {
-    const int rad = plan_radix(n, s);
-    for (int k = 0; k < ns; ++k)
-      for (int r = 1; r < rad; ++r) {
-        const long long num = (long long)r * k;
-        const long long den = (long long)ns * rad;
-        const double ang = -two_pi * (double)num / (double)den;
-        const int idx = off + k * (rad - 1) + (r - 1);
-        re_im[2 * idx] = cos(ang);
-        re_im[2 * idx + 1] = sin(ang);
-      }
-    off += ns * (rad - 1);
-    ns *= rad;
-  }
-}
-
-template cudaError_t launch_fft_pass<float>(int, int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
-template cudaError_t launch_fft_pass<double>(int, int, FftPassArgs<double>, cpx<double>*, cudaStream_t, int*);
-template int fft_final_blocks<float>(int);
-template int fft_final_blocks<double>(int);
 
 }  // namespace qf

@@ -52,20 +52,24 @@ template <typename R, int NB>
 __global__ void __launch_bounds__(kFieldThreads) dots_kernel(Basis2<R> basis, const cpx<R>* __restrict__ w,
                                                              long long n_sites, double* partials) {
   __shared__ double red_s[32 * kNumSums];
-  double s[kNumSums] = {0, 0, 0, 0, 0};
+  Acc<R> acc[kNumSums];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_sites; i += stride) {
     const cpx<R> x = w[i];
-    const double wx = x.x, wy = x.y;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       const cpx<R> u = basis.v[j][i];
-      const double ux = u.x, uy = u.y;
-      s[2 * j] += ux * wx + uy * wy;      // Re conj(u) w
-      s[2 * j + 1] += ux * wy - uy * wx;  // Im
+      acc[2 * j].add_prod(u.x, x.x);  // Re conj(u) w
+      acc[2 * j].add_prod(u.y, x.y);
+      acc[2 * j + 1].add_prod(u.x, x.y);  // Im conj(u) w
+      acc[2 * j + 1].add_prod(-u.y, x.x);
     }
-    s[4] += wx * wx + wy * wy;
+    acc[4].add_prod(x.x, x.x);
+    acc[4].add_prod(x.y, x.y);
   }
+  double s[kNumSums];
+#pragma unroll
+  for (int i = 0; i < kNumSums; ++i) s[i] = acc[i].value();
   block_sum_store<kNumSums>(s, red_s, partials + (long long)blockIdx.x * kPartialStride);
 }
 
@@ -102,38 +106,78 @@ cudaError_t launch_finish_dots(const double* partials, int nblocks, int nb, doub
   return cudaGetLastError();
 }
 
-// w = src - sum_j c_j v_j, evaluated in FP64 per element and rounded once.
+// w = src - sum_j c_j v_j with c_j from device memory, then the sums <v_j|w> and <w|w> of
+// the stored (rounded) w.  FP64 fields: the update is FP64.  FP32 fields: each FP64
+// coefficient is split as c = c_hi + c_lo (two floats) and applied with fused
+// multiply-adds, so the coefficient enters with ~48 bits; what rounding leaves along v_j
+// is removed by the re-orthogonalisation pass that follows.
+template <typename R>
+__device__ __forceinline__ cpx<R> sub_cmul(cpx<R> w, double cr, double ci, cpx<R> u);
+template <>
+__device__ __forceinline__ cpx<double> sub_cmul<double>(cpx<double> w, double cr, double ci, cpx<double> u) {
+  return mk<double>(w.x - (cr * u.x - ci * u.y), w.y - (cr * u.y + ci * u.x));
+}
+template <>
+__device__ __forceinline__ cpx<float> sub_cmul<float>(cpx<float> w, double cr, double ci, cpx<float> u) {
+  const float rh = float(cr), rl = float(cr - double(rh));
+  const float ih = float(ci), il = float(ci - double(ih));
+  float x = w.x, y = w.y;
+  x = __fmaf_rn(-rh, u.x, x);
+  x = __fmaf_rn(ih, u.y, x);
+  x = __fmaf_rn(-rl, u.x, x);
+  x = __fmaf_rn(il, u.y, x);
+  y = __fmaf_rn(-rh, u.y, y);
+  y = __fmaf_rn(-ih, u.x, y);
+  y = __fmaf_rn(-rl, u.y, y);
+  y = __fmaf_rn(-il, u.x, y);
+  return mk<float>(x, y);
+}
+
 template <typename R, int NB>
-__global__ void __launch_bounds__(kFieldThreads) axpy_kernel(cpx<R>* w, const cpx<R>* src, Basis2<R> basis,
-                                                             const double* __restrict__ coef, long long n_sites) {
+__global__ void __launch_bounds__(kFieldThreads) axpy_dots_kernel(cpx<R>* w, const cpx<R>* src, Basis2<R> basis,
+                                                                  const double* __restrict__ coef, long long n_sites,
+                                                                  double* partials) {
+  __shared__ double red_s[32 * kNumSums];
   double cr[2] = {0, 0}, ci[2] = {0, 0};
 #pragma unroll
   for (int j = 0; j < NB; ++j) {
     cr[j] = coef[2 * j];
     ci[j] = coef[2 * j + 1];
   }
+  Acc<R> acc[kNumSums];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_sites; i += stride) {
-    const cpx<R> x = src[i];
-    double ox = x.x, oy = x.y;
+    cpx<R> x = src[i];
+    cpx<R> u[NB > 0 ? NB : 1];
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      const cpx<R> u = basis.v[j][i];
-      ox -= cr[j] * double(u.x) - ci[j] * double(u.y);
-      oy -= cr[j] * double(u.y) + ci[j] * double(u.x);
+      u[j] = basis.v[j][i];
+      x = sub_cmul<R>(x, cr[j], ci[j], u[j]);
     }
-    w[i] = mk<R>(R(ox), R(oy));
+    w[i] = x;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      acc[2 * j].add_prod(u[j].x, x.x);
+      acc[2 * j].add_prod(u[j].y, x.y);
+      acc[2 * j + 1].add_prod(u[j].x, x.y);
+      acc[2 * j + 1].add_prod(-u[j].y, x.x);
+    }
+    acc[4].add_prod(x.x, x.x);
+    acc[4].add_prod(x.y, x.y);
   }
+  double s[kNumSums];
+#pragma unroll
+  for (int i = 0; i < kNumSums; ++i) s[i] = acc[i].value();
+  block_sum_store<kNumSums>(s, red_s, partials + (long long)blockIdx.x * kPartialStride);
 }
 
 template <typename R>
-cudaError_t launch_axpy_basis(cpx<R>* w, const cpx<R>* src, const cpx<R>* const* basis, int nb, const double* coef,
-                              long long n_sites, cudaStream_t st) {
+cudaError_t launch_axpy_dots(cpx<R>* w, const cpx<R>* src, const cpx<R>* const* basis, int nb, const double* coef,
+                             long long n_sites, double* partials, int nblocks, cudaStream_t st) {
   Basis2<R> b{{nb > 0 ? basis[0] : nullptr, nb > 1 ? basis[1] : nullptr}};
-  const int nblk = field_blocks();
-  if (nb == 0) axpy_kernel<R, 0><<<nblk, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites);
-  else if (nb == 1) axpy_kernel<R, 1><<<nblk, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites);
-  else axpy_kernel<R, 2><<<nblk, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites);
+  if (nb == 0) axpy_dots_kernel<R, 0><<<nblocks, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites, partials);
+  else if (nb == 1) axpy_dots_kernel<R, 1><<<nblocks, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites, partials);
+  else axpy_dots_kernel<R, 2><<<nblocks, kFieldThreads, 0, st>>>(w, src, b, coef, n_sites, partials);
   return cudaGetLastError();
 }
 
@@ -165,7 +209,7 @@ template <typename R>
 __global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restrict__ dst, const cpx<R>* __restrict__ src,
                                                                int n, int which, int axis, double* partials) {
   __shared__ double red_s[32 * kNumSums];
-  double s[kNumSums] = {0, 0, 0, 0, 0};
+  Acc<R> nrm;
   const long long total = (long long)n * n * n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
@@ -186,8 +230,10 @@ __global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restric
       o = cscale<R>(o, R(0.25));
     }
     dst[i] = o;
-    s[0] += double(o.x) * double(o.x) + double(o.y) * double(o.y);
+    nrm.add_prod(o.x, o.x);
+    nrm.add_prod(o.y, o.y);
   }
+  double s[kNumSums] = {0, 0, 0, 0, nrm.value()};  // slot 4 = squared norm (as the dots)
   block_sum_store<kNumSums>(s, red_s, partials + (long long)blockIdx.x * kPartialStride);
 }
 
@@ -257,8 +303,8 @@ cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, lon
 #define QF_INST(R)                                                                                          \
   template cudaError_t launch_dots<R>(const cpx<R>* const*, int, const cpx<R>*, long long, double*, int,   \
                                       cudaStream_t);                                                        \
-  template cudaError_t launch_axpy_basis<R>(cpx<R>*, const cpx<R>*, const cpx<R>* const*, int, const double*, \
-                                            long long, cudaStream_t);                                      \
+  template cudaError_t launch_axpy_dots<R>(cpx<R>*, const cpx<R>*, const cpx<R>* const*, int, const double*,  \
+                                           long long, double*, int, cudaStream_t);                          \
   template cudaError_t launch_scale_copy<R>(cpx<R>*, const cpx<R>*, const double*, long long, cudaStream_t); \
   template cudaError_t launch_parity<R>(cpx<R>*, const cpx<R>*, int, int, int, double*, int, cudaStream_t); \
   template cudaError_t launch_from_f64<R>(cpx<R>*, const double*, long long, cudaStream_t);                 \

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a,
   const int z0 = blockIdx.z * ST_ZC;
   const int z1 = min(n, z0 + ST_ZC);
   const bool active = ix < n && iy < n;
-  double acc[kNumSums] = {0, 0, 0, 0, 0};
+  CheckSums<R> cs;
   if (active) {
     const R sc = R(*a.scale);
     cpx<R> zm = ld_masked<R>(a.in, n, ix, iy, z0 - 1 < 0 ? 0 : z0 - 1);
@@ -48,15 +48,7 @@ __global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a,
         cpx<R> vv;
         if (a.v_real) vv = mk<R>(reinterpret_cast<const R*>(a.v)[site], R(0));
         else vv = reinterpret_cast<const cpx<R>*>(a.v)[site];
-        if (a.reduce) {
-          const double px = c.x, py = c.y, hx = h.x, hy = h.y;
-          const double w = px * px + py * py;
-          acc[0] += w;
-          acc[1] += px * hx + py * hy;
-          acc[2] += px * hy - py * hx;
-          acc[3] += w * double(vv.x);
-          acc[4] += w * double(vv.y);
-        }
+        if (a.reduce) cs.add(c, h, vv);
         if (a.write_psi) {
           const cpx<R> d = mk<R>(R(1) + a.half_dtau * vv.x, a.half_dtau * vv.y);
           const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), c) - cscale<R>(h, a.dtau);
@@ -71,6 +63,8 @@ __global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a,
     }
   }
   if (a.reduce) {
+    double acc[kNumSums];
+    cs.to(acc);
     const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     // flatten the 2D thread index for the block reduction
     double* out = a.partials + (long long)bid * kPartialStride;
