@@ -181,15 +181,17 @@ cudaError_t launch_axpy_dots(cpx<R>* w, const cpx<R>* src, const cpx<R>* const* 
   return cudaGetLastError();
 }
 
-// dst = src * s (s a device FP64 scalar), product in FP64.
+// dst = src * s (s a device FP64 scalar).  FP64 fields multiply in FP64; FP32 fields by
+// the scale rounded to FP32 (a uniform relative change of at most 2^-24: these scales
+// are normalisations).
 template <typename R>
 __global__ void __launch_bounds__(kFieldThreads) scale_copy_kernel(cpx<R>* dst, const cpx<R>* src,
                                                                    const double* __restrict__ s, long long n) {
-  const double f = *s;
+  const R f = R(*s);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const cpx<R> x = src[i];
-    dst[i] = mk<R>(R(double(x.x) * f), R(double(x.y) * f));
+    dst[i] = mk<R>(x.x * f, x.y * f);
   }
 }
 
