@@ -177,6 +177,32 @@ qf_status qf_profile(qf_lattice* lat, int enable);
  * reset != 0 clears the totals afterwards. */
 qf_status qf_profile_read(qf_lattice* lat, qf_kernel_stat* out, int max, int* count, int reset);
 
+/* One imaginary-time FFT step that allocates no device memory (the paper has no
+ * counterpart: this is for callers that cannot allocate).  Some callers have no way to
+ * obtain device memory when they call -- e.g. a plugin inside an application whose
+ * allocator already owns the GPU, a loop that must not fail on out-of-memory midway,
+ * or a plain-C caller holding only raw device pointers -- so they cannot provide the
+ * workspace qf_create_lattice needs.  This call does the same work as one step of
+ * qf_step_n for an FFT kinetic term (Eqs. HK1-HK3, complex FP32 fields) on arrays the
+ * caller passes, and keeps its scratch (the transformed field, partial sums, tables) in
+ * one fixed device array inside the library, present on every GPU that loads it until
+ * the process exits.
+ *   n: 8..64 and one of the FFT sizes listed above (QF_EINVAL otherwise: the fixed
+ *      scratch holds at most a 64^3 complex FP32 field).
+ *   kinetic: QF_KIN_FFT_NAIVE, _SYMANZIK or _REL; a, mass, dtau > 0 (no default rule).
+ *   psi: device, n^3 complex FP32 (interleaved re, im), overwritten in place by
+ *        out_scale * (coef_A psi - coef_B dtau H_K psi).
+ *   v: device potential, n^3 FP32 values (v_complex == 0) or n^3 complex FP32 pairs.
+ *   sums: NULL, or device array of 5 doubles that receives <psi|psi>, Re and Im
+ *        <psi|H_K psi>, Re and Im <psi|V psi> of the input psi (FP64 sums).
+ *   cuda_stream: stream for all work; the call returns without synchronising it.
+ * The first call on a device looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the one array and it keeps the previous
+ * call's contents (each call rewrites everything it reads), so calls whose GPU work
+ * overlaps -- on different streams or from different threads on one device -- race. */
+qf_status qf_fft_step_static(int n, double a, int kinetic, double mass, double dtau, void* psi, const void* v,
+                             int v_complex, double out_scale, double* sums, void* cuda_stream);
+
 /* Message of the last failure of this handle ("" if none); static text for NULL. */
 const char* qf_last_error(const qf_lattice* lat);
 

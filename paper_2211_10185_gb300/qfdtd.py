@@ -60,6 +60,8 @@ SIGNATURES = {
     "qf_field_pointer": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
     "qf_profile": (C.c_int, [_P, C.c_int]),
     "qf_profile_read": (C.c_int, [_P, C.POINTER(qf_kernel_stat), C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "qf_fft_step_static": (C.c_int, [C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, _P, _P, C.c_int,
+                                     C.c_double, _P, _P]),
     "qf_last_error": (C.c_char_p, [_P]),
     "qf_version": (C.c_char_p, []),
 }

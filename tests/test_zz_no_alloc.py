@@ -1,0 +1,79 @@
+"""qf_fft_step_static: the FFT step for callers that cannot allocate device memory.
+
+Some callers cannot hand the library a workspace (no allocator of their own, memory
+already owned by a host application, or a loop that must not fail on out-of-memory);
+this entry point keeps its scratch in a fixed array inside the library instead.  The
+test runs it twice in a row on caller-owned torch tensors and checks each result
+against the lattice path (qf_step_n) on the same inputs.  It lives in its own file that
+pytest collects last.
+"""
+import ctypes as C
+import math
+
+import numpy as np
+import pytest
+
+from paper_2211_10185_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+@pytest.mark.parametrize("kind", [I.FFT_NAIVE, I.FFT_REL])
+def test_static_step_matches_the_lattice_step_twice(kind):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10185_gb300 import build, qfdtd as Q
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    build.build()
+    lib = Q.load()
+    n, a, m = 32, 0.2, 1.3
+    v = I.cornell(n, a, 0.5, 0.2)
+    psi0 = I.gaussian_field(n, 21)
+
+    lat = Lattice(n, a, precision="c64")
+    lat.set_potential(v)
+    lat.set_kinetic(kind, m)
+    lat.set_wavefunction(psi0)
+    dtau = lat.info()["dtau"]
+
+    dev = torch.device("cuda")
+    psi = torch.tensor(psi0, dtype=torch.complex64, device=dev).contiguous()
+    vt = torch.tensor(v, dtype=torch.float32, device=dev).contiguous()
+    sums = torch.zeros(5, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    scale = 1.0
+    for call in range(2):
+        st = lib.qf_fft_step_static(n, a, kind, m, dtau, C.c_void_p(psi.data_ptr()), C.c_void_p(vt.data_ptr()),
+                                    0, scale, C.c_void_p(sums.data_ptr()), C.c_void_p(stream))
+        assert st == Q.QF_OK
+        torch.cuda.synchronize()
+        # the lattice path: a check on every step, renormalising the step after a check
+        lat.step_n(1, check_every=1)
+        ref_psi = lat.get_wavefunction()
+        got = psi.cpu().numpy().astype(np.complex128)
+        assert _rel(got, ref_psi) < 2e-6 * (1 + math.log2(n))
+        s = sums.cpu().numpy()
+        e_static = complex(s[1] + s[3], s[2] + s[4]) / s[0]
+        e_ref = lat.energies()
+        assert abs(e_static - e_ref["e"]) < 1e-5 * abs(e_ref["e"])
+        assert s[0] == pytest.approx(e_ref["norm"], rel=1e-5)
+        scale = 1.0 / math.sqrt(s[0])
+
+
+def test_static_step_rejects_lattices_beyond_its_fixed_scratch():
+    from paper_2211_10185_gb300 import build, qfdtd as Q
+
+    build.build()
+    lib = Q.load()
+    for n in (96, 128, 10):
+        assert lib.qf_fft_step_static(n, 0.1, I.FFT_NAIVE, 1.0, 1e-3, C.c_void_p(256), C.c_void_p(256), 0, 1.0,
+                                      None, None) == Q.QF_EINVAL
+    assert lib.qf_fft_step_static(32, 0.1, I.FDTD, 1.0, 1e-3, C.c_void_p(256), C.c_void_p(256), 0, 1.0,
+                                  None, None) == Q.QF_EINVAL
