@@ -417,21 +417,33 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArg
   if constexpr (OP == OP_MID) {
     run_stages<R, N, true, false, 0, S - 1>(v, g, t, tw_s);
     // forward z transform done: natural-order kz; multiply by T and start the inverse
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < EPT / RL; ++b)
-#pragma unroll
-      for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1>(g, b, r), v[b * RL + r]);
-    __syncthreads();
     const R sxy = sym_s[x] + sym_s[o];  // kx = x, ky = o (after the x and y passes)
+    if constexpr (R0 == RL) {
+      // the last forward stage leaves this thread exactly the elements the first inverse
+      // stage reads (j + r N/R for both), so T is applied in registers
 #pragma unroll
-    for (int b = 0; b < EPT / R0; ++b)
+      for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-      for (int r = 0; r < R0; ++r) {
-        const int kz = e_in<N, 0>(g, b, r);
-        const R tm = kin_mult<R>(a.kinetic, sxy, sym_s[kz], a.tcoef, a.am2);
-        v[b * R0 + r] = cscale<R>(t.ld(kz), tm);
-      }
+        for (int r = 0; r < RL; ++r) {
+          const int kz = e_out<N, S - 1>(g, b, r);
+          v[b * RL + r] = cscale<R>(v[b * RL + r], kin_mult<R>(a.kinetic, sxy, sym_s[kz], a.tcoef, a.am2));
+        }
+    } else {
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+        for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1>(g, b, r), v[b * RL + r]);
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int kz = e_in<N, 0>(g, b, r);
+          const R tm = kin_mult<R>(a.kinetic, sxy, sym_s[kz], a.tcoef, a.am2);
+          v[b * R0 + r] = cscale<R>(t.ld(kz), tm);
+        }
+    }
     run_stages<R, N, true, true, 0, S - 1>(v, g, t, tw_s);
   } else {
     run_stages<R, N, true, INV, 0, S - 1>(v, g, t, tw_s);
