@@ -53,7 +53,30 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU baseline sample budget")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=96)
+    ap.add_argument("--served-cap", type=int, default=3000)
     return ap.parse_args()
+
+
+def max_over_ranks(value: float) -> float:
+    """Maximum of a per-rank float over all ranks (NCCL on GPUs, gloo on CPU); the
+    value itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job rate: every rank processed units_per_rank; the job took the slowest
+    rank's time (replicas, weak scaling)."""
+    return world * units_per_rank / seconds_max
 
 
 def workload_config(w, prec):
@@ -278,6 +301,54 @@ def cufft_comparator(w, v, psi0, steps=10):
 
 
 # ---------------------------------------------------------------------------------------
+# Served mix: Poisson arrivals of Cornell solves, continuous batching
+# ---------------------------------------------------------------------------------------
+def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget=170e9, n_cmp=8):
+    """Serves a seeded sample of the mixed workload in real time; then, on a subsample of
+    small requests, compares the batched FP32 form with serial per-lattice FP64 solves."""
+    import torch
+
+    from paper_2211_10185_gb300 import qfdtd as Q
+    from paper_2211_10185_gb300.serve import Server, served_mix
+
+    reqs = served_mix(n_req, rate=rate, sizes=sizes, seed=4, max_steps=cap)
+    srv = Server(int(budget), chunk=CHUNK)
+    srv.run(reqs, realtime=True)
+    torch.cuda.synchronize()
+    out = dict(srv.metrics())
+    out.update({"requests": n_req, "arrival_rate_per_s": rate, "sizes": list(sizes), "step_cap": cap,
+                "tolerance": "|dE| < 1e-7 (1 + |E|)", "hbm_budget_bytes": int(budget), "realtime": True})
+    # comparator: the same small requests, all arriving at once, FP32 batched vs FP64 alone
+    sub = [r for r in reqs if r.n <= 64][:n_cmp]
+    t0 = time.perf_counter()
+    srv32 = Server(int(budget), chunk=CHUNK)
+    r32 = {r.rid: r for r in srv32.run(sub, realtime=False)}
+    torch.cuda.synchronize()
+    t32 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r64 = {}
+    for req in sub:
+        one = Server(int(budget), chunk=CHUNK)
+        req64 = dataclasses_replace(req, precision="c128")
+        (res,) = one.run([req64], realtime=False)
+        r64[req.rid] = res
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    errs = [abs(r32[i].energy - r64[i].energy) / max(1e-300, abs(r64[i].energy)) for i in r64]
+    out["fp32_batched_vs_fp64_alone"] = {
+        "requests": len(sub), "fp32_batched_solves_per_s": len(sub) / t32, "fp64_alone_solves_per_s": len(sub) / t64,
+        "max_rel_energy_err_fp32_vs_fp64": max(errs) if errs else None,
+        "same_status": all(r32[i].status == r64[i].status for i in r64)}
+    return out
+
+
+def dataclasses_replace(obj, **kw):
+    import dataclasses
+
+    return dataclasses.replace(obj, **kw)
+
+
+# ---------------------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------------------
 def run_ours(args):
@@ -344,9 +415,7 @@ def run_ours(args):
             prof = lat.profile_read(reset=True)
             lat.profile(False)
         if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms = max_over_ranks(ms)
             dist.barrier()
         return ms, prof, ex
 
@@ -360,7 +429,7 @@ def run_ours(args):
     ms_prof, prof, _ = timed_region(True)
 
     units_per_rank = n ** 3 * CHUNK * args.steps
-    value = world * units_per_rank / (ms_total * 1e-3)
+    value = aggregate_rate(units_per_rank, world, ms_total * 1e-3)
     ms_per_step = ms_total / args.steps
 
     # roofline of the dominant kernel (largest share of the timed device time)
@@ -424,11 +493,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         if world > 1:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+            el = max_over_ranks(el)
         if out is not None:
-            out["e2e"] = {"value": world * n ** 3 * CHUNK * e_steps / el, "unit": "site-updates/s",
+            out["e2e"] = {"value": aggregate_rate(n ** 3 * CHUNK * e_steps, world, el), "unit": "site-updates/s",
                           "h2d_bytes_per_step": 16 * n ** 3, "d2h_bytes_per_step": 4 * 24,
                           "steps": e_steps,
                           "note": "host wall clock; FP64 psi0 uploaded from pinned memory each step, "
@@ -438,6 +505,13 @@ def run_ours(args):
             out["comparator_cufft"] = cufft_comparator(w, v, psi0)
         except Exception as exc:  # context only
             out["comparator_cufft"] = {"error": str(exc)[:200]}
+    if out is not None and not args.no_served:
+        lat.close()
+        torch.cuda.synchronize()
+        try:
+            out["served"] = served_benchmark(args.served_requests, args.served_cap)
+        except Exception as exc:
+            out["served"] = {"error": str(exc)[:300]}
     if out is not None and world == 1 and not args.no_cpu_baseline:
         rate, steps, el = oracle_rate(w, v, psi0, args.cpu_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",

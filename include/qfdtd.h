@@ -203,6 +203,42 @@ qf_status qf_profile_read(qf_lattice* lat, qf_kernel_stat* out, int max, int* co
 qf_status qf_fft_step_static(int n, double a, int kinetic, double mass, double dtau, void* psi, const void* v,
                              int v_complex, double out_scale, double* sums, void* cuda_stream);
 
+/* ---- Batches (no counterpart in the paper: serving many independent solves) ------
+ * A batch advances many resident lattices together.  Each step, complex-FP32 lattices
+ * of equal N -- and, for FFT terms, equal real/complex V and check status -- form a
+ * group, and each pass of a group is a single kernel launch over all its members (up
+ * to 48 per launch); FP64 lattices run their own launches.  Every member computes
+ * exactly what qf_step_n computes for it alone (same kernels, same blocks, same
+ * reduction order), so its results do not depend on the other members.  A batch holds
+ * no device memory; members keep their own workspaces.  During qf_batch_step all
+ * members' work is issued on the batch's stream. */
+typedef struct qf_batch qf_batch;
+#define QF_BATCH_RUNNING (-1)
+
+qf_status qf_batch_create(void* cuda_stream, qf_batch** out);
+qf_status qf_batch_destroy(qf_batch* b); /* never destroys the members */
+
+/* Adds a ready lattice (potential, kinetic term and psi set) with its own stopping rule:
+ * it converges at a check with |E_t - E_prev| < tol_abs + tol_rel |E_t| and stops after
+ * max_steps steps taken inside the batch.  The lattice must not be used on its own
+ * while it is a member. */
+qf_status qf_batch_add(qf_batch* b, qf_lattice* lat, int64_t max_steps, double tol_abs, double tol_rel);
+qf_status qf_batch_remove(qf_batch* b, qf_lattice* lat);
+
+/* Advances every running member by up to `steps` steps (check_every and snap_every as
+ * in qf_step_n).  Members stop at convergence (status QF_OK) or at their step cap
+ * (QF_ENOTCONV) and stay in the batch until removed; *n_running (may be NULL) receives
+ * the number still running. */
+qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, int snap_every, int* n_running);
+
+/* Members in insertion order: count, and per member (arrays of at least `max` entries,
+ * may be NULL) its status (QF_BATCH_RUNNING, QF_OK, QF_ENOTCONV) and steps taken. */
+qf_status qf_batch_members(qf_batch* b, int* count, int* status, int64_t* steps_done, int max);
+
+/* Kernel launches the batch has issued. */
+qf_status qf_batch_info(qf_batch* b, int64_t* launches);
+const char* qf_batch_last_error(const qf_batch* b);
+
 /* Message of the last failure of this handle ("" if none); static text for NULL. */
 const char* qf_last_error(const qf_lattice* lat);
 

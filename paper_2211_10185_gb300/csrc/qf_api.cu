@@ -8,6 +8,7 @@
 
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/qfdtd.h"
@@ -395,44 +396,58 @@ extern "C" qf_status qf_field_pointer(qf_lattice* lat, int slot, void** dev_ptr)
 
 // One kinetic application on `in` (psi' written to `out` when write), with FP64 sums
 // when reduce; returns the number of partial rows written through nblocks.
+// Arguments of the FFT passes / the stencil for one lattice (kernels in qf_fft_impl.cuh and
+// qf_stencil.cu); `in` is the field the kinetic term acts on.
+template <typename R>
+static FftPassArgs<R> fft_args(qf_lattice* lat, void* in, bool write, bool reduce, const double* scale) {
+  const int n = lat->d.n;
+  const double a = lat->d.a, m = lat->mass, dt = lat->dtau;
+  const double n3 = (double)n * n * n;
+  FftPassArgs<R> p{};
+  p.twiddle = reinterpret_cast<const cpx<R>*>(lat->ws + lat->L.tw);
+  p.symbol = reinterpret_cast<const R*>(lat->ws + lat->L.sym);
+  p.kinetic = lat->kinetic;
+  p.tcoef = (R)(lat->kinetic == QF_KIN_FFT_REL ? 1.0 / (a * n3) : 1.0 / (2.0 * a * a * m * n3));
+  p.am2 = (R)((a * m) * (a * m));
+  p.psi = reinterpret_cast<cpx<R>*>(in);
+  p.v = lat->ws + lat->L.v;
+  p.v_real = lat->v_real;
+  p.half_dtau = (R)(0.5 * dt);
+  p.dtau = (R)dt;
+  p.scale = scale;
+  p.partials = lat->partials();
+  p.write_psi = write ? 1 : 0;
+  p.reduce = reduce ? 1 : 0;
+  p.data = reinterpret_cast<cpx<R>*>(lat->tmp());
+  return p;
+}
+
+template <typename R>
+static StencilArgs<R> stencil_args(qf_lattice* lat, void* in, void* out, bool write, bool reduce,
+                                   const double* scale) {
+  const double a = lat->d.a, m = lat->mass, dt = lat->dtau;
+  return StencilArgs<R>{reinterpret_cast<const cpx<R>*>(in), reinterpret_cast<cpx<R>*>(out), lat->ws + lat->L.v,
+                        lat->v_real, (R)(1.0 / (2.0 * m * a * a)), (R)(0.5 * dt), (R)dt, scale, lat->partials(),
+                        write ? 1 : 0, reduce ? 1 : 0};
+}
+
+// One kinetic application on `in` (psi' written to `out` when write), with FP64 sums
+// when reduce; returns the number of partial rows written through nblocks.
 static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write, bool reduce, const double* scale,
                                 int* nblocks) {
   const int n = lat->d.n;
-  const double a = lat->d.a, m = lat->mass, dt = lat->dtau;
-  const void* v = lat->ws + lat->L.v;
   if (lat->kinetic == QF_KIN_FDTD) {
-    const double kc = 1.0 / (2.0 * m * a * a);
     if (lat->c64()) {
-      StencilArgs<float> s{reinterpret_cast<const cpx<float>*>(in), reinterpret_cast<cpx<float>*>(out), v,
-                           lat->v_real, (float)kc, (float)(0.5 * dt), (float)dt, scale, lat->partials(),
-                           write ? 1 : 0, reduce ? 1 : 0};
+      StencilArgs<float> s = stencil_args<float>(lat, in, out, write, reduce, scale);
       return launch(lat, K_STENCIL, [&] { return launch_stencil<float>(n, s, lat->st, nblocks); });
     }
-    StencilArgs<double> s{reinterpret_cast<const cpx<double>*>(in), reinterpret_cast<cpx<double>*>(out), v,
-                          lat->v_real, kc, 0.5 * dt, dt, scale, lat->partials(), write ? 1 : 0, reduce ? 1 : 0};
+    StencilArgs<double> s = stencil_args<double>(lat, in, out, write, reduce, scale);
     return launch(lat, K_STENCIL, [&] { return launch_stencil<double>(n, s, lat->st, nblocks); });
   }
-  // FFT terms: in place on `in` (out must equal in when writing); tmp is scratch
-  const double n3 = (double)n * n * n;
-  const double tcoef = lat->kinetic == QF_KIN_FFT_REL ? 1.0 / (a * n3) : 1.0 / (2.0 * a * a * m * n3);
-  const double am2 = (a * m) * (a * m);
+  // FFT terms: in place on `in` (out must equal in when writing); the scratch field is tmp
   if (lat->c64()) {
-    FftPassArgs<float> p{};
-    p.twiddle = reinterpret_cast<const cpx<float>*>(lat->ws + lat->L.tw);
-    p.symbol = reinterpret_cast<const float*>(lat->ws + lat->L.sym);
-    p.kinetic = lat->kinetic;
-    p.tcoef = (float)tcoef;
-    p.am2 = (float)am2;
-    p.psi = reinterpret_cast<cpx<float>*>(in);
-    p.v = v;
-    p.v_real = lat->v_real;
-    p.half_dtau = (float)(0.5 * dt);
-    p.dtau = (float)dt;
-    p.scale = scale;
-    p.partials = lat->partials();
-    p.write_psi = write ? 1 : 0;
-    p.reduce = reduce ? 1 : 0;
-    cpx<float>* tmp = reinterpret_cast<cpx<float>*>(lat->tmp());
+    FftPassArgs<float> p = fft_args<float>(lat, in, write, reduce, scale);
+    cpx<float>* tmp = p.data;
     for (int ps = 0; ps < kFftPasses; ++ps) {
       cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
                              [&] { return launch_fft_pass<float>(n, ps, p, tmp, lat->st, nblocks); });
@@ -440,28 +455,57 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
     }
     return cudaSuccess;
   }
-  FftPassArgs<double> p{};
-  p.twiddle = reinterpret_cast<const cpx<double>*>(lat->ws + lat->L.tw);
-  p.symbol = reinterpret_cast<const double*>(lat->ws + lat->L.sym);
-  p.kinetic = lat->kinetic;
-  p.tcoef = tcoef;
-  p.am2 = am2;
-  p.psi = reinterpret_cast<cpx<double>*>(in);
-  p.v = v;
-  p.v_real = lat->v_real;
-  p.half_dtau = 0.5 * dt;
-  p.dtau = dt;
-  p.scale = scale;
-  p.partials = lat->partials();
-  p.write_psi = write ? 1 : 0;
-  p.reduce = reduce ? 1 : 0;
-  cpx<double>* tmp = reinterpret_cast<cpx<double>*>(lat->tmp());
+  FftPassArgs<double> p = fft_args<double>(lat, in, write, reduce, scale);
+  cpx<double>* tmp = p.data;
   for (int ps = 0; ps < kFftPasses; ++ps) {
     cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
                            [&] { return launch_fft_pass<double>(n, ps, p, tmp, lat->st, nblocks); });
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Bookkeeping after the kinetic pass of step t has been issued on `st` (shared by
+// qf_step_n and qf_batch_step so both advance a lattice identically): finishing sums and
+// the pending renormalisation on a check step, buffer swap (FDTD), counters, snapshot.
+static cudaError_t after_step(qf_lattice* lat, bool check, int nb, int snap_every, cudaStream_t st) {
+  lat->pending_scale = false;
+  if (check) {
+    cudaError_t e = launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 1, st); });
+    if (e != cudaSuccess) return e;
+    lat->pending_scale = true;
+  }
+  if (lat->kinetic == QF_KIN_FDTD) lat->live = 1 - lat->live;
+  lat->step += 1;
+  lat->tau += lat->dtau;
+  if (snap_every > 0 && lat->step % snap_every == 0) {
+    lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
+    cudaError_t e = cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(), (size_t)lat->sites * (lat->c64() ? 8 : 16),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (lat->snap_count < lat->d.n_snap) lat->snap_count++;
+  }
+  return cudaSuccess;
+}
+
+// Records the energy of the check at step t; returns whether |E_t - E_prev| < tol where
+// tol = tol_abs + tol_rel |E_t|.
+static bool record_check(qf_lattice* lat, const double* e3, int64_t t, double tau_t, double tol_abs,
+                         double tol_rel) {
+  qf_energy r{};
+  r.e_re = e3[0];
+  r.e_im = e3[1];
+  r.norm = e3[2];
+  r.de = lat->have_prev ? hypot(e3[0] - lat->prev_re, e3[1] - lat->prev_im) : INFINITY;
+  r.step = t;
+  r.tau = tau_t;
+  lat->last = r;
+  lat->have_last = true;
+  const bool conv = lat->have_prev && r.de < tol_abs + tol_rel * hypot(e3[0], e3[1]);
+  lat->have_prev = true;
+  lat->prev_re = e3[0];
+  lat->prev_im = e3[1];
+  return conv;
 }
 
 static qf_status read_energy(qf_lattice* lat, double* e3) {
@@ -491,39 +535,13 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
     void* in = lat->psi();
     void* out = fdtd ? lat->tmp() : in;
     QF_CUDA(lat, kinetic_pass(lat, in, out, true, check, scale, &nb));
-    lat->pending_scale = false;
-    if (check) {
-      QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 1, lat->st); }));
-      lat->pending_scale = true;
-    }
-    if (fdtd) lat->live = 1 - lat->live;
-    lat->step += 1;
-    lat->tau += lat->dtau;
+    QF_CUDA(lat, after_step(lat, check, nb, snap_every, lat->st));
     ++done;
-    if (snap_every > 0 && lat->step % snap_every == 0) {
-      lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
-      QF_CUDA(lat, cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(),
-                                   (size_t)lat->sites * (lat->c64() ? 8 : 16), cudaMemcpyDeviceToDevice, lat->st));
-      if (lat->snap_count < lat->d.n_snap) lat->snap_count++;
-    }
     if (check) {
       double e3[3];
       qf_status s = read_energy(lat, e3);
       if (s != QF_OK) return s;
-      qf_energy r{};
-      r.e_re = e3[0];
-      r.e_im = e3[1];
-      r.norm = e3[2];
-      r.de = lat->have_prev ? hypot(e3[0] - lat->prev_re, e3[1] - lat->prev_im) : INFINITY;
-      r.step = t;
-      r.tau = tau_t;
-      lat->last = r;
-      lat->have_last = true;
-      const bool conv = lat->have_prev && r.de < tol_abs;
-      lat->have_prev = true;
-      lat->prev_re = e3[0];
-      lat->prev_im = e3[1];
-      if (conv) {
+      if (record_check(lat, e3, t, tau_t, tol_abs, 0.0)) {
         status = QF_OK;
         break;
       }
@@ -692,3 +710,222 @@ extern "C" const char* qf_last_error(const qf_lattice* lat) {
 }
 
 extern "C" const char* qf_version(void) { return kVersion; }
+
+// ------------------------------------------------------------------------------------
+// Batches: many resident lattices advanced together.  Each step, FP32 lattices with the
+// same N (and, for FFT terms, the same real/complex V and check status) form groups, and
+// each pass of a group is one launch over all its members; FP64 lattices run their own
+// launches.  A member computes exactly what qf_step_n computes for it alone.
+// ------------------------------------------------------------------------------------
+struct qf_batch {
+  struct Member {
+    qf_lattice* lat;
+    int64_t max_steps, steps_done;
+    double tol_abs, tol_rel;
+    int status;  // QF_BATCH_RUNNING, QF_OK (converged), QF_ENOTCONV (step cap reached)
+  };
+  cudaStream_t st = nullptr;
+  std::vector<Member> m;
+  std::string err;
+  int64_t launches = 0;
+};
+
+static qf_status bfail(qf_batch* b, qf_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+#define QF_BCUDA(b, call)                                                                     \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return bfail(b, QF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" qf_status qf_batch_create(void* cuda_stream, qf_batch** out) {
+  if (!out) return QF_EINVAL;
+  qf_batch* b = new (std::nothrow) qf_batch();
+  if (!b) return QF_ENOMEM;
+  b->st = static_cast<cudaStream_t>(cuda_stream);
+  *out = b;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_destroy(qf_batch* b) {
+  if (!b) return QF_OK;
+  cudaStreamSynchronize(b->st);
+  delete b;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_add(qf_batch* b, qf_lattice* lat, int64_t max_steps, double tol_abs, double tol_rel) {
+  if (!b || !lat) return QF_EINVAL;
+  if (max_steps < 0 || !(tol_abs >= 0) || !(tol_rel >= 0)) return bfail(b, QF_EINVAL, "bad step cap or tolerance");
+  if (!lat->have_v || lat->kinetic < 0 || !lat->have_psi)
+    return bfail(b, QF_ESTATE, "set the potential, kinetic term and wavefunction first");
+  for (auto& x : b->m)
+    if (x.lat == lat) return bfail(b, QF_EINVAL, "lattice already in the batch");
+  // work of the lattice's own stream must be visible to the batch stream
+  QF_BCUDA(b, cudaStreamSynchronize(lat->st));
+  b->m.push_back({lat, max_steps, 0, tol_abs, tol_rel, QF_BATCH_RUNNING});
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_remove(qf_batch* b, qf_lattice* lat) {
+  if (!b || !lat) return QF_EINVAL;
+  for (size_t i = 0; i < b->m.size(); ++i)
+    if (b->m[i].lat == lat) {
+      QF_BCUDA(b, cudaStreamSynchronize(b->st));
+      b->m.erase(b->m.begin() + i);
+      return QF_OK;
+    }
+  return bfail(b, QF_EINVAL, "lattice not in the batch");
+}
+
+extern "C" qf_status qf_batch_members(qf_batch* b, int* count, int* status, int64_t* steps_done, int max) {
+  if (!b) return QF_EINVAL;
+  if (count) *count = (int)b->m.size();
+  for (int i = 0; i < (int)b->m.size() && i < max; ++i) {
+    if (status) status[i] = b->m[i].status;
+    if (steps_done) steps_done[i] = b->m[i].steps_done;
+  }
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, int snap_every, int* n_running) {
+  if (!b) return QF_EINVAL;
+  if (steps < 0 || check_every < 0 || snap_every < 0) return bfail(b, QF_EINVAL, "negative step counts");
+  cudaStream_t st = b->st;
+  // during the call every member issues its work on the batch stream
+  struct StreamSwap {
+    qf_batch* b;
+    std::vector<cudaStream_t> saved;
+    explicit StreamSwap(qf_batch* bb) : b(bb) {
+      for (auto& x : b->m) {
+        saved.push_back(x.lat->st);
+        x.lat->st = b->st;
+      }
+    }
+    ~StreamSwap() {
+      for (size_t i = 0; i < saved.size(); ++i) b->m[i].lat->st = saved[i];
+    }
+  } swap_guard(b);
+  std::vector<int> run;
+  std::vector<char> chk;
+  std::vector<int> nblk;
+  std::vector<double> tau_t;
+  std::vector<int64_t> t_of;
+  std::vector<double> e3;
+  for (int64_t s = 0; s < steps; ++s) {
+    run.clear();
+    for (int i = 0; i < (int)b->m.size(); ++i)
+      if (b->m[i].status == QF_BATCH_RUNNING) {
+        if (b->m[i].steps_done >= b->m[i].max_steps) b->m[i].status = QF_ENOTCONV;
+        else run.push_back(i);
+      }
+    if (run.empty()) break;
+    const int R = (int)run.size();
+    chk.assign(R, 0);
+    nblk.assign(R, 0);
+    tau_t.assign(R, 0);
+    t_of.assign(R, 0);
+    for (int k = 0; k < R; ++k) {
+      qf_lattice* L = b->m[run[k]].lat;
+      t_of[k] = L->step;
+      tau_t[k] = L->tau;
+      chk[k] = check_every > 0 && L->step % check_every == 0;
+    }
+    // group FP32 members by (N, kinetic family, real V, check); FP64 members run alone
+    std::vector<char> done(R, 0);
+    for (int k = 0; k < R; ++k) {
+      if (done[k]) continue;
+      qf_lattice* L = b->m[run[k]].lat;
+      const double* sk = L->pending_scale ? &L->sc()->scale[1] : &L->sc()->scale[0];
+      const bool fdtd = L->kinetic == QF_KIN_FDTD;
+      if (!L->c64()) {
+        void* in = L->psi();
+        QF_BCUDA(b, kinetic_pass(L, in, fdtd ? L->tmp() : in, true, chk[k], sk, &nblk[k]));
+        b->launches += fdtd ? 1 : kFftPasses;
+        done[k] = 1;
+        continue;
+      }
+      std::vector<int> g;
+      for (int q = k; q < R; ++q) {
+        if (done[q]) continue;
+        qf_lattice* M = b->m[run[q]].lat;
+        if (!M->c64() || M->d.n != L->d.n || (M->kinetic == QF_KIN_FDTD) != fdtd) continue;
+        if (!fdtd && (M->v_real != L->v_real || chk[q] != chk[k])) continue;
+        g.push_back(q);
+        done[q] = 1;
+      }
+      const int n = L->d.n;
+      for (size_t off = 0; off < g.size(); off += kGroupMax) {
+        const int cnt = (int)std::min<size_t>(kGroupMax, g.size() - off);
+        if (fdtd) {
+          StencilGroup<float> sg;
+          sg.count = cnt;
+          for (int j = 0; j < cnt; ++j) {
+            const int q = g[off + j];
+            qf_lattice* M = b->m[run[q]].lat;
+            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
+            sg.a[j] = stencil_args<float>(M, M->psi(), M->tmp(), true, chk[q], sq);
+            nblk[q] = stencil_blocks<float>(n);
+          }
+          QF_BCUDA(b, launch_stencil_group<float>(n, sg, st));
+          b->launches += 1;
+        } else {
+          FftGroup<float> fg;
+          fg.count = cnt;
+          for (int j = 0; j < cnt; ++j) {
+            const int q = g[off + j];
+            qf_lattice* M = b->m[run[q]].lat;
+            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
+            fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
+            nblk[q] = fft_final_blocks<float>(n);
+          }
+          for (int ps = 0; ps < kFftPasses; ++ps) {
+            for (int j = 0; j < cnt; ++j) fg.a[j].src = ps == 0 ? fg.a[j].psi : nullptr;
+            QF_BCUDA(b, launch_fft_group_pass<float>(n, ps, fg, st));
+            b->launches += 1;
+          }
+        }
+      }
+    }
+    // per-member bookkeeping, identical to qf_step_n
+    bool any_check = false;
+    for (int k = 0; k < R; ++k) {
+      qf_lattice* L = b->m[run[k]].lat;
+      QF_BCUDA(b, after_step(L, chk[k], nblk[k], snap_every, st));
+      if (chk[k]) b->launches += 1;
+      b->m[run[k]].steps_done += 1;
+      any_check = any_check || chk[k];
+    }
+    if (any_check) {
+      e3.assign(3 * R, 0.0);
+      for (int k = 0; k < R; ++k)
+        if (chk[k])
+          QF_BCUDA(b, cudaMemcpyAsync(&e3[3 * k], b->m[run[k]].lat->sc()->energy, 3 * sizeof(double),
+                                      cudaMemcpyDeviceToHost, st));
+      QF_BCUDA(b, cudaStreamSynchronize(st));
+      for (int k = 0; k < R; ++k) {
+        if (!chk[k]) continue;
+        auto& mb = b->m[run[k]];
+        if (record_check(mb.lat, &e3[3 * k], t_of[k], tau_t[k], mb.tol_abs, mb.tol_rel)) mb.status = QF_OK;
+      }
+    }
+  }
+  QF_BCUDA(b, cudaStreamSynchronize(st));
+  int nr = 0;
+  for (auto& x : b->m) {
+    if (x.status == QF_BATCH_RUNNING && x.steps_done >= x.max_steps) x.status = QF_ENOTCONV;
+    nr += x.status == QF_BATCH_RUNNING;
+  }
+  if (n_running) *n_running = nr;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_info(qf_batch* b, int64_t* launches) {
+  if (!b) return QF_EINVAL;
+  if (launches) *launches = b->launches;
+  return QF_OK;
+}
+
+extern "C" const char* qf_batch_last_error(const qf_batch* b) { return b ? b->err.c_str() : "null batch"; }

@@ -78,6 +78,14 @@ struct FftPassArgs {
   int reduce;             // accumulate the kNumSums sums
 };
 
+// Up to kGroupMax lattices of one size advanced by a single launch per pass.
+constexpr int kGroupMax = 48;
+template <typename R>
+struct FftGroup {
+  int count;
+  FftPassArgs<R> a[kGroupMax];
+};
+
 // FDTD stencil step arguments (Eq. HK0 with Dirichlet planes).
 template <typename R>
 struct StencilArgs {
@@ -92,6 +100,12 @@ struct StencilArgs {
   double* partials;
   int write_psi;
   int reduce;
+};
+
+template <typename R>
+struct StencilGroup {
+  int count;
+  StencilArgs<R> a[kGroupMax];
 };
 
 // ---- block-level FP64 reduction of kNumSums values (deterministic order) ----------
@@ -196,6 +210,10 @@ constexpr int kFftPasses = 5;
 template <typename R>
 cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st,
                             int* nblocks_final);
+// One pass for a group of lattices of size n sharing real/complex V and check status
+// (c64 only); each member's arguments are as launch_fft_pass would use them.
+template <typename R>
+cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st);
 // Number of blocks the reducing (final) pass of the FFT step uses for lattice size n.
 template <typename R>
 int fft_final_blocks(int n);
@@ -206,6 +224,8 @@ template <typename R>
 cudaError_t launch_stencil(int n, StencilArgs<R> args, cudaStream_t st, int* nblocks);
 template <typename R>
 int stencil_blocks(int n);
+template <typename R>
+cudaError_t launch_stencil_group(int n, const StencilGroup<R>& g, cudaStream_t st);
 
 // Finishing reduction: sums nblocks partial rows in index order into sc->sums, then
 // energy and (when set_scale) sc->scale[1] = 1/sqrt(norm).

@@ -296,7 +296,7 @@ __device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
 // in x-transformed space) -> inverse x -> update of psi.  The final pass loads psi and V
 // of its output sites at the start, so those reads overlap the inverse transform.
 template <typename R, int N, int OP, bool VREAL>
-__global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArgs<R> a) {
+__device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bid) {
   using G = Geom<R, N>;
   constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
   constexpr bool INV = is_final(OP);
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArg
   double* red_s = reinterpret_cast<double*>(data_s + G::LC * G::PL);
 
   const int line = threadIdx.x / G::TL, g = threadIdx.x % G::TL;
-  const long long gline = (long long)blockIdx.x * G::LC + line;
+  const long long gline = (long long)bid * G::LC + line;
   const long long base = gline * N;
   load_twiddles<R, N>(tw_s, a.twiddle);
 
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArg
       for (int i = 0; i < EPT; ++i) cs.add(pv[i], v[i], vat(i));
       double acc[kNumSums];
       cs.to(acc);
-      block_sum_store<kNumSums>(acc, red_s, a.partials + (long long)blockIdx.x * kPartialStride);
+      block_sum_store<kNumSums>(acc, red_s, a.partials + (long long)bid * kPartialStride);
     }
     if constexpr (WRITE) {
       const R sc = R(*a.scale);
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArg
 // y / z passes: C = L x P columns per block.  AXIS 1: points stride N, outer = z (stride
 // N^2).  AXIS 2: points stride N^2, outer = y (stride N).
 template <typename R, int N, int AXIS, int OP>
-__global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArgs<R> a) {
+__device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bid) {
   using G = Geom<R, N>;
   constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
   constexpr long long PSTRIDE = AXIS == 1 ? N : (long long)N * N;
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArg
   const int c = threadIdx.x % G::C, g = threadIdx.x / G::C;
   const int l = c % G::L, p = c / G::L;
   constexpr int XB = N / G::L;
-  const int xb = blockIdx.x % XB, ob = blockIdx.x / XB;
+  const int xb = bid % XB, ob = bid / XB;
   const int x = xb * G::L + l, o = ob * G::P + p;
   const long long base = (long long)o * OSTRIDE + x;
   load_twiddles<R, N>(tw_s, a.twiddle);
@@ -452,6 +452,27 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArg
   for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
     for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r) * PSTRIDE] = v[b * RL + r];
+}
+
+// Entry points: one lattice (arguments by value), or a group of up to kGroupMax lattices
+// of the same N advanced by one launch (blockIdx.y selects the lattice; the arguments of
+// all members travel in the kernel's parameter space).  Every lattice runs exactly the
+// blocks it would run alone.
+template <typename R, int N, int OP, bool VREAL>
+__global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArgs<R> a) {
+  fft_x_body<R, N, OP, VREAL>(a, blockIdx.x);
+}
+template <typename R, int N, int AXIS, int OP>
+__global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArgs<R> a) {
+  fft_s_body<R, N, AXIS, OP>(a, blockIdx.x);
+}
+template <typename R, int N, int OP, bool VREAL>
+__global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_group_kernel(const __grid_constant__ FftGroup<R> g) {
+  fft_x_body<R, N, OP, VREAL>(g.a[blockIdx.y], blockIdx.x);
+}
+template <typename R, int N, int AXIS, int OP>
+__global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_group_kernel(const __grid_constant__ FftGroup<R> g) {
+  fft_s_body<R, N, AXIS, OP>(g.a[blockIdx.y], blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
@@ -520,12 +541,71 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
   return cudaGetLastError();
 }
 
+
+template <typename R, int N, int OP, bool VREAL>
+static void set_smem_attr_group(size_t bytes) {
+  cudaFuncSetAttribute(fft_x_group_kernel<R, N, OP, VREAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// One pass for a group of lattices of size N: g.a[i] holds lattice i's arguments as
+// launch_fft_pass would build them (data = its scratch field, src = psi on pass 0).
+template <typename R, int N>
+static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st) {
+  using G = Geom<R, N>;
+  const size_t sx = smem_x<R, N>(), ss = smem_s<R, N>();
+  static bool attr_done = false;
+  if (!attr_done) {
+    set_smem_attr_group<R, N, OP_FWD, false>(sx);
+    set_smem_attr_group<R, N, OP_FINAL, false>(sx);
+    set_smem_attr_group<R, N, OP_FINAL, true>(sx);
+    set_smem_attr_group<R, N, OP_FINAL_SUMS, false>(sx);
+    set_smem_attr_group<R, N, OP_FINAL_SUMS, true>(sx);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    attr_done = true;
+  }
+  const dim3 gx(N * N / G::LC, g.count), gs((N / G::L) * (N / G::P), g.count);
+  const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0;
+  switch (pass) {
+    case 0: fft_x_group_kernel<R, N, OP_FWD, false><<<gx, G::THREADS_X, sx, st>>>(g); break;
+    case 1: fft_s_group_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 2: fft_s_group_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 3: fft_s_group_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 4:
+      if (vreal) {
+        if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, true><<<gx, G::THREADS_X, sx, st>>>(g);
+        else fft_x_group_kernel<R, N, OP_FINAL, true><<<gx, G::THREADS_X, sx, st>>>(g);
+      } else {
+        if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, false><<<gx, G::THREADS_X, sx, st>>>(g);
+        else fft_x_group_kernel<R, N, OP_FINAL, false><<<gx, G::THREADS_X, sx, st>>>(g);
+      }
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
   switch (n) {
 #define QF_CASE(NN) \
   case NN:          \
     return pass_n<R, NN>(pass, args, tmp, st, nfinal);
+    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
+    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
+#undef QF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st) {
+  switch (n) {
+#define QF_CASE(NN) \
+  case NN:          \
+    return group_pass_n<R, NN>(pass, g, st);
     QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
     QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
 #undef QF_CASE

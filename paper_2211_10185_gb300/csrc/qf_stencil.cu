@@ -23,11 +23,11 @@ __device__ __forceinline__ cpx<R> ld_masked(const cpx<R>* __restrict__ p, int n,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a, int n) {
+__device__ __forceinline__ void stencil_body(const StencilArgs<R>& a, const int n, const int bzi) {
   __shared__ double red_s[32 * kNumSums];
   const int ix = blockIdx.x * ST_BX + threadIdx.x;
   const int iy = blockIdx.y * ST_BY + threadIdx.y;
-  const int z0 = blockIdx.z * ST_ZC;
+  const int z0 = bzi * ST_ZC;
   const int z1 = min(n, z0 + ST_ZC);
   const bool active = ix < n && iy < n;
   CheckSums<R> cs;
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a,
   if (a.reduce) {
     double acc[kNumSums];
     cs.to(acc);
-    const int bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int bid = (bzi * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     // flatten the 2D thread index for the block reduction
     double* out = a.partials + (long long)bid * kPartialStride;
     // block_sum_store uses threadIdx.x as the linear id: remap through a local copy
@@ -85,6 +85,26 @@ __global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a,
     }
   }
 }
+
+template <typename R>
+__global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a, int n) {
+  stencil_body<R>(a, n, blockIdx.z);
+}
+
+// A group of lattices of the same n: blockIdx.z = member * z-chunks + z-chunk.
+template <typename R>
+__global__ void __launch_bounds__(ST_BX* ST_BY) stencil_group_kernel(const __grid_constant__ StencilGroup<R> g, int n) {
+  const int nzb = (n + ST_ZC - 1) / ST_ZC;
+  stencil_body<R>(g.a[blockIdx.z / nzb], n, blockIdx.z % nzb);
+}
+
+template <typename R>
+cudaError_t launch_stencil_group(int n, const StencilGroup<R>& g, cudaStream_t st) {
+  dim3 grid((n + ST_BX - 1) / ST_BX, (n + ST_BY - 1) / ST_BY, ((n + ST_ZC - 1) / ST_ZC) * g.count);
+  stencil_group_kernel<R><<<grid, dim3(ST_BX, ST_BY), 0, st>>>(g, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_stencil_group<float>(int, const StencilGroup<float>&, cudaStream_t);
 
 template <typename R>
 int stencil_blocks(int n) {

