@@ -1,11 +1,11 @@
-// Complex FP32 instantiation of the fused FFT kinetic step (kernels in qf_fft_impl.cuh).
+// Host helpers of the fused FFT kinetic step: plan sizes and twiddle tables (kernels in
+// qf_fft_impl.cuh; the complex-FP32 entry points are instantiated in qf_fft_group.cu).
 #include <math.h>
 
 #include "qf_fft_impl.cuh"
 
 namespace qf {
 
-template cudaError_t launch_fft_pass<float>(int, int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
 template int fft_final_blocks<float>(int);
 
 bool fft_supported(int n) { return plan_stages(n) > 0; }

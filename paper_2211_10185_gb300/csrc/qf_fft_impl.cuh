@@ -560,13 +560,15 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
     set_smem_attr_group<R, N, OP_FINAL, true>(sx);
     set_smem_attr_group<R, N, OP_FINAL_SUMS, false>(sx);
     set_smem_attr_group<R, N, OP_FINAL_SUMS, true>(sx);
+    set_smem_attr_group<R, N, OP_SUMS, false>(sx);
+    set_smem_attr_group<R, N, OP_SUMS, true>(sx);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     attr_done = true;
   }
   const dim3 gx(N * N / G::LC, g.count), gs((N / G::L) * (N / G::P), g.count);
-  const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0;
+  const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0, write = g.a[0].write_psi != 0;
   switch (pass) {
     case 0: fft_x_group_kernel<R, N, OP_FWD, false><<<gx, G::THREADS_X, sx, st>>>(g); break;
     case 1: fft_s_group_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
@@ -574,10 +576,12 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
     case 3: fft_s_group_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 4:
       if (vreal) {
-        if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, true><<<gx, G::THREADS_X, sx, st>>>(g);
+        if (!write) fft_x_group_kernel<R, N, OP_SUMS, true><<<gx, G::THREADS_X, sx, st>>>(g);
+        else if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, true><<<gx, G::THREADS_X, sx, st>>>(g);
         else fft_x_group_kernel<R, N, OP_FINAL, true><<<gx, G::THREADS_X, sx, st>>>(g);
       } else {
-        if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, false><<<gx, G::THREADS_X, sx, st>>>(g);
+        if (!write) fft_x_group_kernel<R, N, OP_SUMS, false><<<gx, G::THREADS_X, sx, st>>>(g);
+        else if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, false><<<gx, G::THREADS_X, sx, st>>>(g);
         else fft_x_group_kernel<R, N, OP_FINAL, false><<<gx, G::THREADS_X, sx, st>>>(g);
       }
       break;
@@ -586,12 +590,30 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// Complex-FP32 lattices always run the grouped kernels (a lone lattice is a group of one),
+// so a lattice executes the same machine code alone and inside a batch.
+template <typename R, int N>
+static cudaError_t single_pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
+  if constexpr (sizeof(R) == 4) {
+    using G = Geom<R, N>;
+    if (nfinal) *nfinal = N * N / G::LC;
+    FftGroup<R> g;
+    g.count = 1;
+    g.a[0] = a;
+    g.a[0].data = tmp;
+    g.a[0].src = (pass == 0) ? a.psi : nullptr;
+    return group_pass_n<R, N>(pass, g, st);
+  } else {
+    return pass_n<R, N>(pass, a, tmp, st, nfinal);
+  }
+}
+
 template <typename R>
 cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
   switch (n) {
 #define QF_CASE(NN) \
   case NN:          \
-    return pass_n<R, NN>(pass, args, tmp, st, nfinal);
+    return single_pass_n<R, NN>(pass, args, tmp, st, nfinal);
     QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
     QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
 #undef QF_CASE

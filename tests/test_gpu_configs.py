@@ -1,0 +1,94 @@
+"""The paper-shaped workloads at their full sizes, through the C ABI, against the oracle.
+
+* N=256 relativistic workload (the bench configuration): two steps with checks,
+  every site compared with the FP64 oracle.
+* N=512 Gaussian-mix workload (complex V, HK2): one step with a check, every site.
+* N=32 harmonic oscillator with the FDTD term in FP64: converged ground state and the
+  first excited state from snapshots, against the oracle and near 3/2 and 5/2.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qfdtd_oracle as O
+from paper_2211_10185_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10185_gb300 import build
+
+    build.build()
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def _pair_from_workload(name, precision=None):
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    w = I.workload(name)
+    n, a = w["n"], w["a"]
+    v = w["potential"](n, a)
+    psi0 = I.gaussian_field(n, w["seed"])
+    if w["kinetic"] == I.FDTD:
+        psi0 = I.zero_dirichlet_planes(psi0)
+    ref = O.Lattice(n, a)
+    if np.iscomplexobj(v):
+        ref.set_potential(v.real, v.imag)
+    else:
+        ref.set_potential(v)
+    ref.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+    ref.set_wavefunction(psi0)
+    gpu = Lattice(n, a, precision=precision or w["precision"])
+    gpu.set_potential(v)
+    gpu.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+    gpu.set_wavefunction(psi0)
+    return w, ref, gpu
+
+
+def test_bench_workload_n256_two_steps_every_site():
+    w, ref, gpu = _pair_from_workload("cornell_rel_n256")
+    for _ in range(2):
+        ref.step_n(1, check_every=1)
+        gpu.step_n(1, check_every=1)
+        e_ref, e_gpu = ref.energies(), gpu.energies()
+        assert abs(e_gpu["e"] - e_ref["e"]) < 1e-5 * abs(e_ref["e"])
+    out = gpu.get_wavefunction()
+    assert _rel(out, ref.psi) < 2e-6 * (1 + math.log2(w["n"]))
+    # worst site relative to the field's rms
+    rms = np.sqrt(np.mean(np.abs(ref.psi) ** 2))
+    assert np.max(np.abs(out - ref.psi)) < 1e-4 * rms
+
+
+def test_gaussmix_workload_n512_one_step_every_site():
+    w, ref, gpu = _pair_from_workload("gaussmix_symanzik_n512")
+    ref.step_n(1, check_every=1)
+    gpu.step_n(1, check_every=1)
+    e_ref, e_gpu = ref.energies(), gpu.energies()
+    assert abs(e_gpu["e"] - e_ref["e"]) < 1e-5 * abs(e_ref["e"])
+    assert _rel(gpu.get_wavefunction(), ref.psi) < 2e-6 * (1 + math.log2(w["n"]))
+
+
+def test_harmonic_fdtd_n32_ground_and_first_excited():
+    # the plain-method configuration: N=32, a=0.15, FDTD, m=1, V=r^2/2, dtau=a^2/8, FP64,
+    # until |dE| < 1e-8, then ground and first excited states
+    w, ref, gpu = _pair_from_workload("ho_fdtd_n32")
+    s_ref, d_ref = ref.step_n(100000, tol=w["tol"], check_every=64, snap_every=32)
+    s_gpu, d_gpu = gpu.step_n(100000, tol=w["tol"], check_every=64, snap_every=32)
+    assert s_ref == O.OK and s_gpu == 0 and d_ref == d_gpu
+    e_ref, e_gpu = ref.energies()["e"], gpu.energies()["e"]
+    assert abs(e_gpu - e_ref) < 1e-10 * abs(e_ref)
+    assert abs(e_gpu.real - 1.5) < 5e-3                      # lattice + finite-volume error
+    st, ex_ref = ref.project_excited(2)
+    ex_gpu = gpu.project_excited(2)
+    assert abs(ex_gpu[0]["e"] - ex_ref[0]["e"]) < 1e-10 * abs(ex_ref[0]["e"])
+    assert abs(ex_gpu[1]["e"] - ex_ref[1]["e"]) < 1e-8 * abs(ex_ref[1]["e"])
+    assert abs(ex_gpu[1]["e"].real - 2.5) < 2e-2
