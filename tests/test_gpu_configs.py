@@ -101,3 +101,44 @@ def test_harmonic_fdtd_n32_ground_and_first_excited():
     assert abs(ex_gpu[0]["e"] - ex_ref[0]["e"]) < 1e-10 * abs(ex_ref[0]["e"])
     assert abs(ex_gpu[1]["e"] - ex_ref[1]["e"]) < 1e-8 * abs(ex_ref[1]["e"])
     assert abs(ex_gpu[1]["e"].real - e1) < (dt * e1) ** 2 + 1e-6
+
+
+@pytest.mark.parametrize("kind,cplx", [(I.FFT_NAIVE, False), (I.FFT_SYMANZIK, True), (I.FFT_REL, True)])
+def test_n256_cluster_plane_path_every_kinetic(kind, cplx):
+    # 256^3 complex-FP32 lattices take the three-pass path (xy planes in 8-CTA clusters)
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    n, a, m = 256, 0.05, 0.7
+    v = I.cornell(n, a, 0.4, 0.2)
+    if cplx:
+        v = v - 0.05j * np.abs(v)
+    psi0 = I.gaussian_field(n, 31)
+    ref = O.Lattice(n, a)
+    if cplx:
+        ref.set_potential(v.real, v.imag)
+    else:
+        ref.set_potential(v)
+    ref.set_kinetic(kind, m)
+    ref.set_wavefunction(psi0)
+    gpu = Lattice(n, a, precision="c64")
+    gpu.set_potential(v)
+    gpu.set_kinetic(kind, m)
+    gpu.set_wavefunction(psi0)
+    ref.step_n(2, check_every=1)
+    gpu.step_n(2, check_every=1)
+    assert abs(gpu.energies()["e"] - ref.energies()["e"]) < 1e-5 * abs(ref.energies()["e"])
+    assert _rel(gpu.get_wavefunction(), ref.psi) < 2e-6 * (1 + math.log2(n))
+
+
+def test_n256_excited_states_and_parity_on_the_plane_path():
+    w, ref, gpu = _pair_from_workload("cornell_rel_n256")
+    for lat in (ref, gpu):
+        lat.step_n(3 * 16, check_every=16, snap_every=16)
+    st, ex_ref = ref.project_excited(3)
+    ex_gpu = gpu.project_excited(3)
+    for i in range(3):
+        assert abs(ex_gpu[i]["e"] - ex_ref[i]["e"]) < 1e-4 * abs(ex_ref[i]["e"]), i
+    ref.parity_project(O.P_MINUS_PK, 3, 1)
+    gpu.parity_project(O.P_MINUS_PK, 3, 1)
+    s_gpu, s_ref = gpu.get_wavefunction(1), ref.states[1]
+    assert abs(abs(np.vdot(s_gpu, s_ref)) - 1) < 1e-3
