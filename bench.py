@@ -221,7 +221,6 @@ def bytes_per_site(kernel, prec, v_real):
     table = {
         "fft_x_fwd": 2 * c, "fft_y_fwd": 2 * c, "fft_z_mid_T": 2 * c, "fft_y_inv": 2 * c,
         "fft_x_inv_update": 3 * c + vb, "stencil_step": 2 * c + vb,
-        "fft_xy_fwd": 2 * c, "fft_yx_inv_update": 3 * c + vb,
     }
     return table.get(kernel)
 

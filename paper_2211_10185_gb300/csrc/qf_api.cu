@@ -32,18 +32,11 @@ static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Kernel kinds for the per-kernel timing of qf_profile.
 enum KernelKind {
   K_FFT_X_FWD = 0, K_FFT_Y_FWD, K_FFT_Z_MID, K_FFT_Y_INV, K_FFT_X_INV_UPDATE, K_STENCIL, K_FINISH, K_GS_DOTS,
-  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_FFT_XY_FWD, K_FFT_YX_INV_UPDATE, K_NUM_KINDS
+  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_NUM_KINDS
 };
 static const char* kKindNames[K_NUM_KINDS] = {"fft_x_fwd", "fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
                                                "fft_x_inv_update", "stencil_step", "finish_sums", "gs_dots",
-                                               "gs_axpy", "scale_copy", "parity", "convert", "fft_xy_fwd",
-                                               "fft_yx_inv_update"};
-
-// Profile kind of pass ps of a step made of np passes.
-static int fft_pass_kind(int ps, int np) {
-  if (np == 3) return ps == 0 ? K_FFT_XY_FWD : ps == 1 ? K_FFT_Z_MID : K_FFT_YX_INV_UPDATE;
-  return K_FFT_X_FWD + ps;
-}
+                                               "gs_axpy", "scale_copy", "parity", "convert"};
 static const int kEventPool = 4096;
 
 struct Layout {
@@ -220,12 +213,9 @@ extern "C" qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws
   }
   if (e == cudaSuccess && fft_supported(desc->n)) {
     // per-stage twiddle table exp(-2 pi i r k/(Ns R)) in the lattice precision
-    const int cnt0 = fft_twiddle_count(desc->n);
-    const bool plane = desc->prec == QF_PREC_C64 && fft_passes<float>(desc->n) == 3;
-    const int cnt = cnt0 + (plane ? desc->n : 0);
+    const int cnt = fft_twiddle_count(desc->n);
     double* tw = new double[2 * (size_t)cnt + 2];
     fft_twiddles(desc->n, tw);
-    if (plane) fft_plane_twiddles(desc->n, tw + 2 * cnt0);
     if (desc->prec == QF_PREC_C64) {
       float* f = new float[2 * (size_t)cnt + 2];
       for (int i = 0; i < 2 * cnt; ++i) f[i] = (float)tw[i];
@@ -458,9 +448,8 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
   if (lat->c64()) {
     FftPassArgs<float> p = fft_args<float>(lat, in, write, reduce, scale);
     cpx<float>* tmp = p.data;
-    const int np = fft_passes<float>(n);
-    for (int ps = 0; ps < np; ++ps) {
-      cudaError_t e = launch(lat, fft_pass_kind(ps, np),
+    for (int ps = 0; ps < kFftPasses; ++ps) {
+      cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
                              [&] { return launch_fft_pass<float>(n, ps, p, tmp, lat->st, nblocks); });
       if (e != cudaSuccess) return e;
     }
@@ -854,7 +843,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
       if (!L->c64()) {
         void* in = L->psi();
         QF_BCUDA(b, kinetic_pass(L, in, fdtd ? L->tmp() : in, true, chk[k], sk, &nblk[k]));
-        b->launches += fdtd ? 1 : fft_passes<double>(L->d.n);
+        b->launches += fdtd ? 1 : kFftPasses;
         done[k] = 1;
         continue;
       }
@@ -890,9 +879,9 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
             qf_lattice* M = b->m[run[q]].lat;
             const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
             fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
-            nblk[q] = n == 256 ? 256 * 8 : fft_final_blocks<float>(n);
+            nblk[q] = fft_final_blocks<float>(n);
           }
-          for (int ps = 0; ps < fft_passes<float>(n); ++ps) {
+          for (int ps = 0; ps < kFftPasses; ++ps) {
             for (int j = 0; j < cnt; ++j) fg.a[j].src = ps == 0 ? fg.a[j].psi : nullptr;
             QF_BCUDA(b, launch_fft_group_pass<float>(n, ps, fg, st));
             b->launches += 1;

@@ -217,11 +217,7 @@ cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStr
 // Number of blocks the reducing (final) pass of the FFT step uses for lattice size n.
 template <typename R>
 int fft_final_blocks(int n);
-// Passes of one FFT step (3 for complex-FP32 256^3 lattices, else 5) and the W_N^j table
-// those plane passes read after the per-stage twiddles.
-template <typename R>
-int fft_passes(int n);
-void fft_plane_twiddles(int n, double* re_im);
+
 // Whether the FFT path has kernels for this n.
 bool fft_supported(int n);
 

@@ -24,15 +24,6 @@ int fft_twiddle_count(int n) {
   }
 }
 
-// W_N^j = exp(-2 pi i j / N), j < N (the cross-CTA stages of the plane transforms).
-void fft_plane_twiddles(int n, double* re_im) {
-  const double two_pi = 6.283185307179586476925286766559;
-  for (int j = 0; j < n; ++j) {
-    re_im[2 * j] = cos(-two_pi * (double)j / (double)n);
-    re_im[2 * j + 1] = sin(-two_pi * (double)j / (double)n);
-  }
-}
-
 // Fills tw[off(s) + k (R_s - 1) + r - 1] = exp(-2 pi i r k / (Ns R_s)) in double.
 void fft_twiddles(int n, double* re_im) {
   const double two_pi = 6.283185307179586476925286766559;

@@ -7,6 +7,5 @@ namespace qf {
 
 template cudaError_t launch_fft_pass<double>(int, int, FftPassArgs<double>, cpx<double>*, cudaStream_t, int*);
 template int fft_final_blocks<double>(int);
-template int fft_passes<double>(int);
 
 }  // namespace qf

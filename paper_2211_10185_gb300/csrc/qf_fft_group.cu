@@ -6,6 +6,5 @@ namespace qf {
 
 template cudaError_t launch_fft_group_pass<float>(int, int, const FftGroup<float>&, cudaStream_t);
 template cudaError_t launch_fft_pass<float>(int, int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
-template int fft_passes<float>(int);
 
 }  // namespace qf

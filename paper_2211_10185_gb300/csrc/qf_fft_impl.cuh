@@ -14,8 +14,6 @@
 // stage reads global memory and the last writes it directly (both coalesced);
 // intermediate stages exchange through shared memory.
 #pragma once
-#include <cooperative_groups.h>
-
 #include "qf_common.cuh"
 
 namespace qf {
@@ -478,305 +476,6 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_group_kernel(cons
 }
 
 // ------------------------------------------------------------------------------------
-// N = 256, complex FP32: three passes per step.  The x and y transforms of one z-plane
-// (256 x 256 values, 512 KB) are done by a cluster of 8 CTAs sharing their shared memory:
-// CTA c holds the 32 rows y = 8m + c.  Forward: x transforms of its rows, a 32-point DFT
-// over m (the decimated y-subsequence), then -- after a cluster barrier -- each CTA reads
-// over distributed shared memory the 8 partial spectra of its 4 output indices k' and
-// finishes with a radix-8 stage across the CTAs:
-//   X[k' + 32 q] = sum_c W8^{c q} W256^{c k'} Y_c[k'],  Y_c[k'] = sum_m x[8m + c] W32^{m k'}.
-// Inverse: the same stages in reverse order, the radix-8 stage writing into the owning
-// CTA's shared memory.  Pass 2 is the z pass of the five-pass step.
-// ------------------------------------------------------------------------------------
-constexpr int kPlN = 256, kPlCl = 8, kPlRows = kPlN / kPlCl, kPlThreads = 512;
-constexpr int kPlPL = kPlN + (kPlN >> 4) + 1;     // padded row (float2 elements)
-constexpr int kPlTwX = plan_tw_size(kPlN);         // per-stage x table (255)
-constexpr int kPlTw = kPlTwX + kPlN;               // + W256^j, j < 256
-// shared memory: tables | two row buffers (forward: landing + work alternate) ...
-constexpr size_t kPlBuf = (size_t)kPlRows * kPlPL * sizeof(cpx<float>);
-constexpr size_t kPlSmemFwd = kPlTw * sizeof(cpx<float>) + 2 * kPlBuf;
-// ... inverse: two landing buffers for the next plane's spectra, one work buffer, sums
-constexpr size_t kPlSmemInv = kPlTw * sizeof(cpx<float>) + 3 * kPlBuf + 32 * kNumSums * sizeof(double);
-
-// 8-byte asynchronous global->shared copies (sm_80+ cp.async), grouped per plane
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-// waits until at most one (the most recent) group of this thread is still in flight
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-__device__ __forceinline__ int pl_pad(int e) { return e + (e >> 4); }
-
-// 32-point DFT over the rows of this CTA's tile for every column (Stockham, radix 16 then
-// radix 2), in place; 2 threads per column.  INV: inverse direction.
-template <bool INV>
-__device__ __forceinline__ void plane_rows_dft32(cpx<float>* d, const cpx<float>* w256) {
-  const int col = threadIdx.x % kPlN, gy = threadIdx.x / kPlN;  // gy in {0, 1}
-  const int pc = pl_pad(col);
-  cpx<float> u[16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) u[r] = d[(gy + 2 * r) * kPlPL + pc];
-  dft16<float, INV>(u);
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < 16; ++r) d[(16 * gy + r) * kPlPL + pc] = u[r];
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int j = gy + 2 * b;
-    const cpx<float> w = w256[8 * j];  // W32^j
-    cpx<float> a0 = d[j * kPlPL + pc], a1 = d[(j + 16) * kPlPL + pc];
-    a1 = INV ? cmulc<float>(a1, w) : cmul<float>(a1, w);
-    u[2 * b] = a0 + a1;      // row j
-    u[2 * b + 1] = a0 - a1;  // row j + 16
-  }
-  __syncthreads();
-#pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const int j = gy + 2 * b;
-    d[j * kPlPL + pc] = u[2 * b];
-    d[(j + 16) * kPlPL + pc] = u[2 * b + 1];
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void plane_load_tables(cpx<float>* tw_s, const cpx<float>* tw) {
-  for (int i = threadIdx.x; i < kPlTw; i += blockDim.x) tw_s[i] = tw[i];
-}
-
-// Persistent forward xy pass.  Cluster `cid` handles planes item = cid, cid + ncl, ...
-// (item = member * 256 + z); each CTA copies its 32 rows of the next plane into the idle
-// buffer while it transforms and exchanges the current one.
-__device__ __forceinline__ void plane_fwd_issue(cpx<float>* buf, const FftGroup<float>& grp, int item, int rank) {
-  const FftPassArgs<float>& a = grp.a[item / kPlN];
-  const int z = item % kPlN;
-  const int line = threadIdx.x / 16, g = threadIdx.x % 16;
-  const cpx<float>* in = a.src ? a.src : a.data;
-  const cpx<float>* row = in + ((long long)z * kPlN + kPlCl * line + rank) * kPlN;
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    const int e = g + 16 * r;
-    cp_async8(buf + line * kPlPL + pl_pad(e), row + e);
-  }
-}
-
-__device__ __forceinline__ void plane_fwd_persistent(const FftGroup<float>& grp) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
-  const int cid = blockIdx.x / kPlCl, ncl = gridDim.x / kPlCl;
-  const int total = grp.count * kPlN;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(smem_raw);
-  cpx<float>* w_s = tw_s + kPlTwX;
-  cpx<float>* bufs = tw_s + kPlTw;
-  plane_load_tables(tw_s, grp.a[0].twiddle);
-  const int line = threadIdx.x / 16, g = threadIdx.x % 16;
-  if (cid < total) plane_fwd_issue(bufs, grp, cid, rank);
-  cp_async_commit();
-  __syncthreads();  // tables
-  int i = 0;
-  for (int item = cid; item < total; item += ncl, ++i) {
-    cpx<float>* cur = bufs + (i & 1) * (kPlRows * kPlPL);
-    cpx<float>* nxt = bufs + ((i + 1) & 1) * (kPlRows * kPlPL);
-    if (item + ncl < total) plane_fwd_issue(nxt, grp, item + ncl, rank);
-    cp_async_commit();
-    cp_async_wait_prev();  // this thread's copies of the current plane have landed
-    const FftPassArgs<float>& a = grp.a[item / kPlN];
-    const int z = item % kPlN;
-    // x transforms of rows y = 8 line + rank (stage 0 reads this thread's own copies)
-    Tile<float, kPlN, false> t{cur, line};
-    cpx<float> v[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = t.ld(e_in<kPlN, 0>(g, 0, r));
-    run_stages<float, kPlN, false, false, 0, 1>(v, g, t, tw_s);
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 16; ++r) t.st(e_out<kPlN, 1>(g, 0, r), v[r]);
-    __syncthreads();
-    // 32-point DFT over the decimated rows, then the W256^{c k'} twiddle of the last stage
-    plane_rows_dft32<false>(cur, w_s);
-    {
-      const int col = threadIdx.x % kPlN, gy = threadIdx.x / kPlN, pc = pl_pad(col);
-#pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        const int kp = gy + 2 * b;
-        cur[kp * kPlPL + pc] = cmul<float>(cur[kp * kPlPL + pc], w_s[rank * kp]);
-      }
-    }
-    cl.sync();
-    // radix-8 across the cluster for k' = 4 rank + {0..3}
-    {
-      const int kx = threadIdx.x % kPlN, kk = threadIdx.x / kPlN, pc = pl_pad(kx);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kp = kPlCl / 2 * rank + kk + 2 * h;
-        cpx<float> q[8];
-#pragma unroll
-        for (int c = 0; c < kPlCl; ++c) {
-          const cpx<float>* rem = cl.map_shared_rank(cur, c);
-          q[c] = rem[kp * kPlPL + pc];
-        }
-        dft8<float, false>(q);
-#pragma unroll
-        for (int qq = 0; qq < kPlCl; ++qq) a.data[((long long)z * kPlN + kp + kPlRows * qq) * kPlN + kx] = q[qq];
-      }
-    }
-    cl.sync();  // the cluster has finished reading `cur`; it is refilled two planes later
-  }
-}
-
-// Persistent inverse yx pass + update.  The spectra of the next plane are copied into a
-// landing buffer while the current plane is exchanged and transformed.
-__device__ __forceinline__ void plane_inv_issue(cpx<float>* land, const FftGroup<float>& grp, int item, int rank) {
-  const FftPassArgs<float>& a = grp.a[item / kPlN];
-  const int z = item % kPlN;
-  const int kx = threadIdx.x % kPlN, kk = threadIdx.x / kPlN;
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int kp = kPlCl / 2 * rank + kk + 2 * h;
-#pragma unroll
-    for (int qq = 0; qq < kPlCl; ++qq)
-      cp_async8(land + ((kk + 2 * h) * kPlCl + qq) * kPlN + kx,
-                a.data + ((long long)z * kPlN + kp + kPlRows * qq) * kPlN + kx);
-  }
-}
-
-template <int OP, bool VREAL>
-__device__ __forceinline__ void plane_inv_persistent(const FftGroup<float>& grp) {
-  namespace cg = cooperative_groups;
-  constexpr bool WRITE = (OP == OP_FINAL || OP == OP_FINAL_SUMS);
-  constexpr bool SUMS = (OP == OP_FINAL_SUMS || OP == OP_SUMS);
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
-  const int cid = blockIdx.x / kPlCl, ncl = gridDim.x / kPlCl;
-  const int total = grp.count * kPlN;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(smem_raw);
-  cpx<float>* w_s = tw_s + kPlTwX;
-  cpx<float>* lands = tw_s + kPlTw;
-  cpx<float>* work = lands + 2 * (kPlRows * kPlPL);
-  double* red_s = reinterpret_cast<double*>(work + kPlRows * kPlPL);
-  plane_load_tables(tw_s, grp.a[0].twiddle);
-  const int line = threadIdx.x / 16, g = threadIdx.x % 16;
-  if (cid < total) plane_inv_issue(lands, grp, cid, rank);
-  cp_async_commit();
-  __syncthreads();
-  cl.sync();  // every CTA of the cluster runs before shared memory is written remotely
-  int i = 0;
-  for (int item = cid; item < total; item += ncl, ++i) {
-    cpx<float>* cur = lands + (i & 1) * (kPlRows * kPlPL);
-    cpx<float>* nxt = lands + ((i + 1) & 1) * (kPlRows * kPlPL);
-    if (item + ncl < total) plane_inv_issue(nxt, grp, item + ncl, rank);
-    cp_async_commit();
-    cp_async_wait_prev();
-    const FftPassArgs<float>& a = grp.a[item / kPlN];
-    const int z = item % kPlN;
-    // inverse radix-8 over q for k' = 4 rank + {0..3}; Z_c goes to CTA c's work row k'
-    {
-      const int kx = threadIdx.x % kPlN, kk = threadIdx.x / kPlN, pc = pl_pad(kx);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int kp = kPlCl / 2 * rank + kk + 2 * h;
-        cpx<float> q[8];
-#pragma unroll
-        for (int qq = 0; qq < kPlCl; ++qq) q[qq] = cur[((kk + 2 * h) * kPlCl + qq) * kPlN + kx];
-        dft8<float, true>(q);
-#pragma unroll
-        for (int c = 0; c < kPlCl; ++c) {
-          cpx<float>* rem = cl.map_shared_rank(work, c);
-          rem[kp * kPlPL + pc] = cmulc<float>(q[c], w_s[c * kp]);
-        }
-      }
-    }
-    cl.sync();
-    // psi and V of the sites this thread updates (row y = 8 line + rank, x = g + 16 r):
-    // issued now, consumed after the transforms
-    const long long base = ((long long)z * kPlN + kPlCl * line + rank) * kPlN;
-    cpx<float> pv[16];
-    cpx<float> vv[VREAL ? 1 : 16];
-    float vr_[VREAL ? 16 : 1];
-    {
-      const cpx<float>* __restrict__ psi_in = a.psi;
-#pragma unroll
-      for (int r = 0; r < 16; ++r) pv[r] = psi_in[base + e_out<kPlN, 1>(g, 0, r)];
-      if constexpr (VREAL) {
-        const float* __restrict__ vp = reinterpret_cast<const float*>(a.v);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) vr_[r] = vp[base + e_out<kPlN, 1>(g, 0, r)];
-      } else {
-        const cpx<float>* __restrict__ vp = reinterpret_cast<const cpx<float>*>(a.v);
-#pragma unroll
-        for (int r = 0; r < 16; ++r) vv[r] = vp[base + e_out<kPlN, 1>(g, 0, r)];
-      }
-    }
-    plane_rows_dft32<true>(work, w_s);
-    Tile<float, kPlN, false> t{work, line};
-    cpx<float> v[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = t.ld(e_in<kPlN, 0>(g, 0, r));
-    run_stages<float, kPlN, false, true, 0, 1>(v, g, t, tw_s);
-    auto vat = [&](int k) { return VREAL ? mk<float>(vr_[VREAL ? k : 0], 0.f) : vv[VREAL ? 0 : k]; };
-    if constexpr (SUMS) {
-      CheckSums<float> cs;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) cs.add(pv[k], v[k], vat(k));
-      double acc[kNumSums];
-      cs.to(acc);
-      block_sum_store<kNumSums>(acc, red_s, a.partials + ((long long)z * kPlCl + rank) * kPartialStride);
-    }
-    if constexpr (WRITE) {
-      const float sc = float(*a.scale);
-#pragma unroll
-      for (int r = 0; r < 16; ++r) {
-        const cpx<float> vi = vat(r);
-        const cpx<float> d = mk<float>(1.f + a.half_dtau * vi.x, a.half_dtau * vi.y);
-        const cpx<float> num = cmul<float>(mk<float>(2.f - d.x, -d.y), pv[r]) - cscale<float>(v[r], a.dtau);
-        const float inv = sc / (d.x * d.x + d.y * d.y);
-        a.psi[base + e_out<kPlN, 1>(g, 0, r)] = cscale<float>(cmulc<float>(num, d), inv);
-      }
-    }
-    cl.sync();  // every CTA is done with its work buffer before the next remote writes
-  }
-}
-
-template <int CL = kPlCl>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kPlThreads, 1)
-    plane_fwd_kernel(const __grid_constant__ FftGroup<float> g) {
-  plane_fwd_persistent(g);
-}
-
-template <int OP, bool VREAL>
-__global__ void __cluster_dims__(kPlCl, 1, 1) __launch_bounds__(kPlThreads, 1)
-    plane_inv_kernel(const __grid_constant__ FftGroup<float> g) {
-  plane_inv_persistent<OP, VREAL>(g);
-}
-
-// Clusters of the persistent plane kernels that can be resident at once (queried once).
-template <typename K>
-static int plane_max_clusters(K kernel, size_t smem) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kPlCl * 64, 1, 1);
-  cfg.blockDim = dim3(kPlThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = kPlCl;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
-  int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess || n < 1) {
-    cudaGetLastError();
-    n = 152 / kPlCl;
-  }
-  return n;
-}
-
-// ------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------
 template <typename R, int N>
@@ -870,43 +569,6 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
   }
   const dim3 gx(N * N / G::LC, g.count), gs((N / G::L) * (N / G::P), g.count);
   const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0, write = g.a[0].write_psi != 0;
-  if constexpr (sizeof(R) == 4 && N == kPlN) {
-    // three passes: xy forward (8-CTA clusters per plane), z, yx inverse + update
-    static bool plane_attr = false;
-    static int ncl_fwd = 0, ncl_inv = 0;
-    if (!plane_attr) {
-      const int sf = (int)kPlSmemFwd, si = (int)kPlSmemInv;
-      cudaFuncSetAttribute(plane_fwd_kernel<kPlCl>, cudaFuncAttributeMaxDynamicSharedMemorySize, sf);
-      cudaFuncSetAttribute(plane_inv_kernel<OP_FINAL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, si);
-      cudaFuncSetAttribute(plane_inv_kernel<OP_FINAL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, si);
-      cudaFuncSetAttribute(plane_inv_kernel<OP_FINAL_SUMS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, si);
-      cudaFuncSetAttribute(plane_inv_kernel<OP_FINAL_SUMS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, si);
-      cudaFuncSetAttribute(plane_inv_kernel<OP_SUMS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, si);
-      cudaFuncSetAttribute(plane_inv_kernel<OP_SUMS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, si);
-      ncl_fwd = plane_max_clusters(plane_fwd_kernel<kPlCl>, kPlSmemFwd);
-      ncl_inv = plane_max_clusters(plane_inv_kernel<OP_FINAL_SUMS, false>, kPlSmemInv);
-      plane_attr = true;
-    }
-    const int items = g.count * kPlN;
-    const dim3 gpf(kPlCl * (ncl_fwd < items ? ncl_fwd : items)), gpi(kPlCl * (ncl_inv < items ? ncl_inv : items));
-    switch (pass) {
-      case 0: plane_fwd_kernel<kPlCl><<<gpf, kPlThreads, kPlSmemFwd, st>>>(g); break;
-      case 1: fft_s_group_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(g); break;
-      case 2:
-        if (vreal) {
-          if (!write) plane_inv_kernel<OP_SUMS, true><<<gpi, kPlThreads, kPlSmemInv, st>>>(g);
-          else if (sums) plane_inv_kernel<OP_FINAL_SUMS, true><<<gpi, kPlThreads, kPlSmemInv, st>>>(g);
-          else plane_inv_kernel<OP_FINAL, true><<<gpi, kPlThreads, kPlSmemInv, st>>>(g);
-        } else {
-          if (!write) plane_inv_kernel<OP_SUMS, false><<<gpi, kPlThreads, kPlSmemInv, st>>>(g);
-          else if (sums) plane_inv_kernel<OP_FINAL_SUMS, false><<<gpi, kPlThreads, kPlSmemInv, st>>>(g);
-          else plane_inv_kernel<OP_FINAL, false><<<gpi, kPlThreads, kPlSmemInv, st>>>(g);
-        }
-        break;
-      default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-  }
   switch (pass) {
     case 0: fft_x_group_kernel<R, N, OP_FWD, false><<<gx, G::THREADS_X, sx, st>>>(g); break;
     case 1: fft_s_group_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
@@ -934,7 +596,7 @@ template <typename R, int N>
 static cudaError_t single_pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
   if constexpr (sizeof(R) == 4) {
     using G = Geom<R, N>;
-    if (nfinal) *nfinal = (N == kPlN) ? kPlN * kPlCl : N * N / G::LC;
+    if (nfinal) *nfinal = N * N / G::LC;
     FftGroup<R> g;
     g.count = 1;
     g.a[0] = a;
@@ -972,12 +634,6 @@ cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStr
     default:
       return cudaErrorInvalidValue;
   }
-}
-
-// Passes per step: 3 for complex-FP32 256^3 lattices (cluster plane transforms), else 5.
-template <typename R>
-int fft_passes(int n) {
-  return (sizeof(R) == 4 && n == kPlN) ? 3 : kFftPasses;
 }
 
 template <typename R>

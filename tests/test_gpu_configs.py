@@ -104,8 +104,7 @@ def test_harmonic_fdtd_n32_ground_and_first_excited():
 
 
 @pytest.mark.parametrize("kind,cplx", [(I.FFT_NAIVE, False), (I.FFT_SYMANZIK, True), (I.FFT_REL, True)])
-def test_n256_cluster_plane_path_every_kinetic(kind, cplx):
-    # 256^3 complex-FP32 lattices take the three-pass path (xy planes in 8-CTA clusters)
+def test_n256_every_fft_kinetic_and_complex_potential(kind, cplx):
     from paper_2211_10185_gb300.lattice import Lattice
 
     n, a, m = 256, 0.05, 0.7
@@ -130,7 +129,7 @@ def test_n256_cluster_plane_path_every_kinetic(kind, cplx):
     assert _rel(gpu.get_wavefunction(), ref.psi) < 2e-6 * (1 + math.log2(n))
 
 
-def test_n256_excited_states_and_parity_on_the_plane_path():
+def test_n256_excited_states_and_parity():
     w, ref, gpu = _pair_from_workload("cornell_rel_n256")
     for lat in (ref, gpu):
         lat.step_n(3 * 16, check_every=16, snap_every=16)
