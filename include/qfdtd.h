@@ -242,6 +242,13 @@ const char* qf_batch_last_error(const qf_batch* b);
 /* Message of the last failure of this handle ("" if none); static text for NULL. */
 const char* qf_last_error(const qf_lattice* lat);
 
+/* Self-test of the bounded device waits (no counterpart in the paper; failure
+ * detection).  Launches, on the handle's stream, a kernel whose wait on a
+ * shared-memory barrier can never complete; the wait gives up after its iteration limit
+ * (about a second), the kernel records the failure and returns, and this call returns
+ * QF_ETIMEOUT with the context still usable.  QF_OK would mean the limit did not work. */
+qf_status qf_selftest_bounded_wait(qf_lattice* lat);
+
 /* Library version string. */
 const char* qf_version(void);
 

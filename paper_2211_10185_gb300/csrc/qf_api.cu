@@ -13,8 +13,13 @@
 
 #include "../../include/qfdtd.h"
 #include "qf_common.cuh"
+#include "qf_stencil_tma.cuh"
 
 namespace qf {
+bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64);
+cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st);
+template <typename R>
+cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st);
 int fft_twiddle_count(int n);
 void fft_twiddles(int n, double* re_im);
 template <typename R>
@@ -106,6 +111,12 @@ struct qf_lattice {
   qf_energy last{};
   int snap_count = 0, snap_head = -1;  // snap_head: slot of the latest snapshot
   bool have_states[3] = {false, false, false};
+  // the scratch field holds the forward x transform of the live psi (written by the
+  // previous step's final pass), so the next FFT step starts at its second pass
+  bool xfwd_valid = false;
+  // tensor maps of the two field buffers for the TMA-staged stencil
+  CUtensorMap fmap[2];
+  bool fmap_ok = false;
   std::string err;
   // launch accounting and optional CUDA-event timing per kernel kind
   int64_t launches = 0;
@@ -233,6 +244,8 @@ extern "C" qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws
     delete lat;
     return QF_ECUDA;
   }
+  lat->fmap_ok = encode_stencil_map(&lat->fmap[0], lat->field(0), desc->n, desc->prec == QF_PREC_C64) &&
+                 encode_stencil_map(&lat->fmap[1], lat->field(1), desc->n, desc->prec == QF_PREC_C64);
   *out = lat;
   return QF_OK;
 }
@@ -350,6 +363,7 @@ extern "C" qf_status qf_set_wavefunction(qf_lattice* lat, const double* re_im) {
   if (s != QF_OK) return s;
   lat->have_psi = true;
   lat->pending_scale = false;
+  lat->xfwd_valid = false;
   return QF_OK;
 }
 
@@ -394,8 +408,6 @@ extern "C" qf_status qf_field_pointer(qf_lattice* lat, int slot, void** dev_ptr)
   return QF_OK;
 }
 
-// One kinetic application on `in` (psi' written to `out` when write), with FP64 sums
-// when reduce; returns the number of partial rows written through nblocks.
 // Arguments of the FFT passes / the stencil for one lattice (kernels in qf_fft_impl.cuh and
 // qf_stencil.cu); `in` is the field the kinetic term acts on.
 template <typename R>
@@ -431,37 +443,80 @@ static StencilArgs<R> stencil_args(qf_lattice* lat, void* in, void* out, bool wr
                         write ? 1 : 0, reduce ? 1 : 0};
 }
 
+// Appends lattice `lat` (input field `in`) to a TMA stencil group; the tensor map of a
+// field buffer is cached, others (state slots) are encoded on the spot.
+template <typename R>
+static bool stencil_group_member(qf_lattice* lat, void* in, void* out, bool write, bool reduce, const double* scale,
+                                 StencilTmaGroup<R>& g, bool first = true) {
+  if (first) {
+    g.count = 0;
+    g.n = lat->d.n;
+    g.err = &lat->sc()->err[0];
+  }
+  const int i = g.count;
+  if (i >= kGroupMax) return false;
+  if (in == lat->field(0) && lat->fmap_ok) g.map[i] = lat->fmap[0];
+  else if (in == lat->field(1) && lat->fmap_ok) g.map[i] = lat->fmap[1];
+  else if (!encode_stencil_map(&g.map[i], in, lat->d.n, lat->c64())) return false;
+  g.a[i] = stencil_args<R>(lat, in, out, write, reduce, scale);
+  g.count = i + 1;
+  return true;
+}
+
+// Reads and clears the bounded-wait failure flag of a lattice.
+static qf_status check_device_error(qf_lattice* lat) {
+  int err = 0;
+  QF_CUDA(lat, cudaMemcpyAsync(&err, &lat->sc()->err[0], sizeof(int), cudaMemcpyDeviceToHost, lat->st));
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  if (err) {
+    QF_CUDA(lat, cudaMemsetAsync(&lat->sc()->err[0], 0, sizeof(int), lat->st));
+    return fail(lat, QF_ETIMEOUT, "a bounded device wait ran out (copy engine did not complete)");
+  }
+  return QF_OK;
+}
+
 // One kinetic application on `in` (psi' written to `out` when write), with FP64 sums
 // when reduce; returns the number of partial rows written through nblocks.
 static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write, bool reduce, const double* scale,
                                 int* nblocks) {
   const int n = lat->d.n;
   if (lat->kinetic == QF_KIN_FDTD) {
+    if (nblocks) *nblocks = stencil_blocks<float>(n);
     if (lat->c64()) {
-      StencilArgs<float> s = stencil_args<float>(lat, in, out, write, reduce, scale);
-      return launch(lat, K_STENCIL, [&] { return launch_stencil<float>(n, s, lat->st, nblocks); });
+      StencilTmaGroup<float> g;
+      if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
+      return launch(lat, K_STENCIL, [&] { return launch_stencil_tma<float>(g, lat->st); });
     }
-    StencilArgs<double> s = stencil_args<double>(lat, in, out, write, reduce, scale);
-    return launch(lat, K_STENCIL, [&] { return launch_stencil<double>(n, s, lat->st, nblocks); });
+    StencilTmaGroup<double> g;
+    if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
+    return launch(lat, K_STENCIL, [&] { return launch_stencil_tma<double>(g, lat->st); });
   }
-  // FFT terms: in place on `in` (out must equal in when writing); the scratch field is tmp
+  // FFT terms: in place on `in` (out must equal in when writing); the scratch field is tmp.
+  // A step on the live psi emits the next step's first pass and may skip its own.
+  const bool live = write && in == lat->psi();
+  const int first = (live && lat->xfwd_valid) ? 1 : 0;
+  lat->xfwd_valid = false;
   if (lat->c64()) {
     FftPassArgs<float> p = fft_args<float>(lat, in, write, reduce, scale);
+    p.emit_next = live ? 1 : 0;
     cpx<float>* tmp = p.data;
-    for (int ps = 0; ps < kFftPasses; ++ps) {
+    for (int ps = first; ps < kFftPasses; ++ps) {
       cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
                              [&] { return launch_fft_pass<float>(n, ps, p, tmp, lat->st, nblocks); });
       if (e != cudaSuccess) return e;
     }
+    lat->xfwd_valid = live;
     return cudaSuccess;
   }
   FftPassArgs<double> p = fft_args<double>(lat, in, write, reduce, scale);
+  p.emit_next = live ? 1 : 0;
   cpx<double>* tmp = p.data;
-  for (int ps = 0; ps < kFftPasses; ++ps) {
+  for (int ps = first; ps < kFftPasses; ++ps) {
     cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
                            [&] { return launch_fft_pass<double>(n, ps, p, tmp, lat->st, nblocks); });
     if (e != cudaSuccess) return e;
   }
+  lat->xfwd_valid = live;
   return cudaSuccess;
 }
 
@@ -548,8 +603,12 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
     }
   }
   if (steps_done) *steps_done = done;
-  // surface asynchronous launch failures before reporting
+  // surface asynchronous launch failures and bounded-wait timeouts before reporting
   QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  if (lat->kinetic == QF_KIN_FDTD) {
+    qf_status s = check_device_error(lat);
+    if (s != QF_OK) return s;
+  }
   return status;
 }
 
@@ -563,6 +622,8 @@ extern "C" qf_status qf_energies(qf_lattice* lat, qf_energy* out) {
 // <v|H|v>/<v|v> of a field into out (FP64 sums; the field is not modified).
 static qf_status measure(qf_lattice* lat, void* f, qf_energy* out) {
   int nb = 0;
+  if (lat->kinetic == QF_KIN_FDTD && f != lat->field(0) && f != lat->field(1) && !lat->fmap_ok)
+    return fail(lat, QF_ECUDA, "tensor map encoding unavailable");
   // FFT terms transform through tmp and read f; FDTD reads f only
   QF_CUDA(lat, kinetic_pass(lat, f, f, false, true, &lat->sc()->scale[0], &nb));
   QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 0, lat->st); }));
@@ -628,6 +689,7 @@ extern "C" qf_status qf_project_excited(qf_lattice* lat, int n_states, qf_energy
 template <typename R>
 static qf_status parity_t(qf_lattice* lat, int which, int axis, void* target) {
   const int nblk = field_blocks();
+  lat->xfwd_valid = false;  // the scratch field is overwritten
   cpx<R>* tmp = reinterpret_cast<cpx<R>*>(lat->tmp());
   QF_CUDA(lat, launch(lat, K_PARITY, [&] { return launch_parity<R>(tmp, reinterpret_cast<const cpx<R>*>(target), lat->d.n, which, axis, lat->partials(),
                                 nblk, lat->st); }));
@@ -710,6 +772,17 @@ extern "C" const char* qf_last_error(const qf_lattice* lat) {
 }
 
 extern "C" const char* qf_version(void) { return kVersion; }
+
+extern "C" qf_status qf_selftest_bounded_wait(qf_lattice* lat) {
+  if (!lat) return QF_EINVAL;
+  int* flag = &lat->sc()->err[1];
+  QF_CUDA(lat, cudaMemsetAsync(flag, 0, sizeof(int), lat->st));
+  QF_CUDA(lat, launch_bounded_wait_probe(flag, lat->st));
+  int err = 0;
+  QF_CUDA(lat, cudaMemcpyAsync(&err, flag, sizeof(int), cudaMemcpyDeviceToHost, lat->st));
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  return err ? QF_ETIMEOUT : QF_OK;
+}
 
 // ------------------------------------------------------------------------------------
 // Batches: many resident lattices advanced together.  Each step, FP32 lattices with the
@@ -860,29 +933,42 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
       for (size_t off = 0; off < g.size(); off += kGroupMax) {
         const int cnt = (int)std::min<size_t>(kGroupMax, g.size() - off);
         if (fdtd) {
-          StencilGroup<float> sg;
-          sg.count = cnt;
+          StencilTmaGroup<float> sg;
           for (int j = 0; j < cnt; ++j) {
             const int q = g[off + j];
             qf_lattice* M = b->m[run[q]].lat;
             const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
-            sg.a[j] = stencil_args<float>(M, M->psi(), M->tmp(), true, chk[q], sq);
+            if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0))
+              return bfail(b, QF_ECUDA, "tensor map encoding failed");
+            // one error flag per launch: the first member's
             nblk[q] = stencil_blocks<float>(n);
           }
-          QF_BCUDA(b, launch_stencil_group<float>(n, sg, st));
+          QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
           b->launches += 1;
         } else {
-          FftGroup<float> fg;
+          FftGroup<float> fg, f0;
           fg.count = cnt;
+          f0.count = 0;
           for (int j = 0; j < cnt; ++j) {
             const int q = g[off + j];
             qf_lattice* M = b->m[run[q]].lat;
             const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
             fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
+            fg.a[j].emit_next = 1;
             nblk[q] = fft_final_blocks<float>(n);
+            if (!M->xfwd_valid) {
+              f0.a[f0.count] = fg.a[j];
+              f0.a[f0.count].src = fg.a[j].psi;
+              f0.count++;
+            }
+            M->xfwd_valid = true;
           }
-          for (int ps = 0; ps < kFftPasses; ++ps) {
-            for (int j = 0; j < cnt; ++j) fg.a[j].src = ps == 0 ? fg.a[j].psi : nullptr;
+          if (f0.count > 0) {
+            QF_BCUDA(b, launch_fft_group_pass<float>(n, 0, f0, st));
+            b->launches += 1;
+          }
+          for (int ps = 1; ps < kFftPasses; ++ps) {
+            for (int j = 0; j < cnt; ++j) fg.a[j].src = nullptr;
             QF_BCUDA(b, launch_fft_group_pass<float>(n, ps, fg, st));
             b->launches += 1;
           }
@@ -913,6 +999,11 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
     }
   }
   QF_BCUDA(b, cudaStreamSynchronize(st));
+  for (auto& x : b->m)
+    if (x.lat->kinetic == QF_KIN_FDTD) {
+      qf_status es = check_device_error(x.lat);
+      if (es != QF_OK) return bfail(b, es, x.lat->err);
+    }
   int nr = 0;
   for (auto& x : b->m) {
     if (x.status == QF_BATCH_RUNNING && x.steps_done >= x.max_steps) x.status = QF_ENOTCONV;

@@ -53,7 +53,8 @@ struct DevScalars {
   double gs_coef[8];   // Gram-Schmidt coefficients <v_i|w> (complex, up to 3) + spare
   double gs_scale[2];  // 1/||w|| of the current Gram-Schmidt vector
   double parity_scale[2];
-  double spare[6];
+  int err[2];          // [0]: a bounded device wait ran out (QF_ETIMEOUT)
+  double spare[5];
 };
 
 // Arguments of one pass of the FFT kinetic step.
@@ -76,6 +77,8 @@ struct FftPassArgs {
   double* partials;       // per-block FP64 sums when reducing
   int write_psi;          // 0: measure only (no write)
   int reduce;             // accumulate the kNumSums sums
+  int emit_next;          // final pass that writes psi': also write its forward x transform
+                          // into data, so the next step can skip its first pass
 };
 
 // Up to kGroupMax lattices of one size advanced by a single launch per pass.
@@ -100,12 +103,6 @@ struct StencilArgs {
   double* partials;
   int write_psi;
   int reduce;
-};
-
-template <typename R>
-struct StencilGroup {
-  int count;
-  StencilArgs<R> a[kGroupMax];
 };
 
 // ---- block-level FP64 reduction of kNumSums values (deterministic order) ----------
@@ -222,11 +219,7 @@ int fft_final_blocks(int n);
 bool fft_supported(int n);
 
 template <typename R>
-cudaError_t launch_stencil(int n, StencilArgs<R> args, cudaStream_t st, int* nblocks);
-template <typename R>
 int stencil_blocks(int n);
-template <typename R>
-cudaError_t launch_stencil_group(int n, const StencilGroup<R>& g, cudaStream_t st);
 
 // Finishing reduction: sums nblocks partial rows in index order into sc->sums, then
 // energy and (when set_scale) sc->scale[1] = 1/sqrt(norm).

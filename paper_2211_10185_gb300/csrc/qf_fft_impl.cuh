@@ -295,7 +295,7 @@ __device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
 // x pass: LC contiguous lines per block.  OP_FWD: src -> data.  OP_FINAL: data (H_K psi
 // in x-transformed space) -> inverse x -> update of psi.  The final pass loads psi and V
 // of its output sites at the start, so those reads overlap the inverse transform.
-template <typename R, int N, int OP, bool VREAL>
+template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
 __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bid) {
   using G = Geom<R, N>;
   constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
@@ -376,8 +376,30 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
           const cpx<R> d = mk<R>(R(1) + a.half_dtau * vi.x, a.half_dtau * vi.y);
           const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), pv[i]) - cscale<R>(v[i], a.dtau);
           const R inv = sc / (d.x * d.x + d.y * d.y);
-          a.psi[base + e_out<N, S - 1>(g, b, r)] = cscale<R>(cmulc<R>(num, d), inv);
+          v[i] = cscale<R>(cmulc<R>(num, d), inv);  // psi_{t+1}
+          a.psi[base + e_out<N, S - 1>(g, b, r)] = v[i];
         }
+      if constexpr (NEXT) {
+        // forward x transform of psi_{t+1} for the next step (its first pass)
+        if constexpr (R0 != RL) {
+          __syncthreads();
+#pragma unroll
+          for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+            for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1>(g, b, r), v[b * RL + r]);
+          __syncthreads();
+#pragma unroll
+          for (int b = 0; b < EPT / R0; ++b)
+#pragma unroll
+            for (int r = 0; r < R0; ++r) v[b * R0 + r] = t.ld(e_in<N, 0>(g, b, r));
+        }
+        // (equal first and last radix: the thread already holds the first stage's inputs)
+        run_stages<R, N, false, false, 0, S - 1>(v, g, t, tw_s);
+#pragma unroll
+        for (int b = 0; b < EPT / RL; ++b)
+#pragma unroll
+          for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r)] = v[b * RL + r];
+      }
     }
   }
 }
@@ -458,17 +480,17 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
 // of the same N advanced by one launch (blockIdx.y selects the lattice; the arguments of
 // all members travel in the kernel's parameter space).  Every lattice runs exactly the
 // blocks it would run alone.
-template <typename R, int N, int OP, bool VREAL>
+template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArgs<R> a) {
-  fft_x_body<R, N, OP, VREAL>(a, blockIdx.x);
+  fft_x_body<R, N, OP, VREAL, NEXT>(a, blockIdx.x);
 }
 template <typename R, int N, int AXIS, int OP>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArgs<R> a) {
   fft_s_body<R, N, AXIS, OP>(a, blockIdx.x);
 }
-template <typename R, int N, int OP, bool VREAL>
+template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_group_kernel(const __grid_constant__ FftGroup<R> g) {
-  fft_x_body<R, N, OP, VREAL>(g.a[blockIdx.y], blockIdx.x);
+  fft_x_body<R, N, OP, VREAL, NEXT>(g.a[blockIdx.y], blockIdx.x);
 }
 template <typename R, int N, int AXIS, int OP>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_group_kernel(const __grid_constant__ FftGroup<R> g) {
@@ -489,21 +511,39 @@ static size_t smem_s() {
   return G::TW * sizeof(cpx<R>) + ((N * sizeof(R) + 15) / 16) * 16 + (size_t)G::C * N * sizeof(cpx<R>);
 }
 
-template <typename R, int N, int OP, bool VREAL>
-static void set_smem_attr(size_t bytes) {
-  cudaFuncSetAttribute(fft_x_kernel<R, N, OP, VREAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+// Variant of the final x pass for (real V, writes psi', check sums, emits the next x transform).
+template <typename R, int N, bool GROUP, bool VREAL>
+static auto final_kernel(bool write, bool sums, bool next) {
+  if constexpr (GROUP) {
+    if (!write) return fft_x_group_kernel<R, N, OP_SUMS, VREAL, false>;
+    if (sums) return next ? fft_x_group_kernel<R, N, OP_FINAL_SUMS, VREAL, true>
+                          : fft_x_group_kernel<R, N, OP_FINAL_SUMS, VREAL, false>;
+    return next ? fft_x_group_kernel<R, N, OP_FINAL, VREAL, true> : fft_x_group_kernel<R, N, OP_FINAL, VREAL, false>;
+  } else {
+    if (!write) return fft_x_kernel<R, N, OP_SUMS, VREAL, false>;
+    if (sums) return next ? fft_x_kernel<R, N, OP_FINAL_SUMS, VREAL, true> : fft_x_kernel<R, N, OP_FINAL_SUMS, VREAL, false>;
+    return next ? fft_x_kernel<R, N, OP_FINAL, VREAL, true> : fft_x_kernel<R, N, OP_FINAL, VREAL, false>;
+  }
 }
 
-template <typename R, int N, bool VREAL>
-static cudaError_t final_pass(FftPassArgs<R> p, int gx, size_t sx, cudaStream_t st) {
-  using G = Geom<R, N>;
-  if (p.write_psi && p.reduce)
-    fft_x_kernel<R, N, OP_FINAL_SUMS, VREAL><<<gx, G::THREADS_X, sx, st>>>(p);
-  else if (p.write_psi)
-    fft_x_kernel<R, N, OP_FINAL, VREAL><<<gx, G::THREADS_X, sx, st>>>(p);
+// Raises the dynamic shared-memory limit of every x-pass variant (the largest tiles need
+// more than the default 48 KB).
+template <typename R, int N, bool GROUP>
+static void set_x_attrs(size_t sx) {
+  for (int vr = 0; vr < 2; ++vr)
+    for (int w = 0; w < 2; ++w)
+      for (int su = 0; su < 2; ++su)
+        for (int nx = 0; nx < 2; ++nx) {
+          const void* f = vr ? (const void*)final_kernel<R, N, GROUP, true>(w, su, nx)
+                             : (const void*)final_kernel<R, N, GROUP, false>(w, su, nx);
+          cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
+        }
+  if constexpr (GROUP)
+    cudaFuncSetAttribute((const void*)fft_x_group_kernel<R, N, OP_FWD, false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
   else
-    fft_x_kernel<R, N, OP_SUMS, VREAL><<<gx, G::THREADS_X, sx, st>>>(p);
-  return cudaGetLastError();
+    cudaFuncSetAttribute((const void*)fft_x_kernel<R, N, OP_FWD, false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
 }
 
 template <typename R, int N>
@@ -513,14 +553,7 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
   const size_t sx = smem_x<R, N>(), ss = smem_s<R, N>();
   static bool attr_done = false;
   if (!attr_done) {
-    // the largest tiles need more than the default 48 KB of dynamic shared memory
-    set_smem_attr<R, N, OP_FWD, false>(sx);
-    set_smem_attr<R, N, OP_FINAL, false>(sx);
-    set_smem_attr<R, N, OP_FINAL, true>(sx);
-    set_smem_attr<R, N, OP_FINAL_SUMS, false>(sx);
-    set_smem_attr<R, N, OP_FINAL_SUMS, true>(sx);
-    set_smem_attr<R, N, OP_SUMS, false>(sx);
-    set_smem_attr<R, N, OP_SUMS, true>(sx);
+    set_x_attrs<R, N, false>(sx);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
@@ -530,38 +563,31 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
   FftPassArgs<R> p = a;
   p.data = tmp;
   p.src = (pass == 0) ? a.psi : nullptr;
+  const bool write = p.write_psi != 0, sums = p.reduce != 0, next = write && p.emit_next != 0;
   switch (pass) {
     case 0: fft_x_kernel<R, N, OP_FWD, false><<<gx, G::THREADS_X, sx, st>>>(p); break;
     case 1: fft_s_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 2: fft_s_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 3: fft_s_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p); break;
-    case 4: return a.v_real ? final_pass<R, N, true>(p, gx, sx, st) : final_pass<R, N, false>(p, gx, sx, st);
+    case 4:
+      if (p.v_real) final_kernel<R, N, false, true>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(p);
+      else final_kernel<R, N, false, false>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(p);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-
-template <typename R, int N, int OP, bool VREAL>
-static void set_smem_attr_group(size_t bytes) {
-  cudaFuncSetAttribute(fft_x_group_kernel<R, N, OP, VREAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 // One pass for a group of lattices of size N: g.a[i] holds lattice i's arguments as
-// launch_fft_pass would build them (data = its scratch field, src = psi on pass 0).
+// launch_fft_pass would build them (data = its scratch field, src = psi on pass 0).  The
+// final pass variant follows member 0 (members of a group agree on it).
 template <typename R, int N>
 static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st) {
   using G = Geom<R, N>;
   const size_t sx = smem_x<R, N>(), ss = smem_s<R, N>();
   static bool attr_done = false;
   if (!attr_done) {
-    set_smem_attr_group<R, N, OP_FWD, false>(sx);
-    set_smem_attr_group<R, N, OP_FINAL, false>(sx);
-    set_smem_attr_group<R, N, OP_FINAL, true>(sx);
-    set_smem_attr_group<R, N, OP_FINAL_SUMS, false>(sx);
-    set_smem_attr_group<R, N, OP_FINAL_SUMS, true>(sx);
-    set_smem_attr_group<R, N, OP_SUMS, false>(sx);
-    set_smem_attr_group<R, N, OP_SUMS, true>(sx);
+    set_x_attrs<R, N, true>(sx);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
@@ -569,21 +595,15 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
   }
   const dim3 gx(N * N / G::LC, g.count), gs((N / G::L) * (N / G::P), g.count);
   const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0, write = g.a[0].write_psi != 0;
+  const bool next = write && g.a[0].emit_next != 0;
   switch (pass) {
     case 0: fft_x_group_kernel<R, N, OP_FWD, false><<<gx, G::THREADS_X, sx, st>>>(g); break;
     case 1: fft_s_group_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 2: fft_s_group_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 3: fft_s_group_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 4:
-      if (vreal) {
-        if (!write) fft_x_group_kernel<R, N, OP_SUMS, true><<<gx, G::THREADS_X, sx, st>>>(g);
-        else if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, true><<<gx, G::THREADS_X, sx, st>>>(g);
-        else fft_x_group_kernel<R, N, OP_FINAL, true><<<gx, G::THREADS_X, sx, st>>>(g);
-      } else {
-        if (!write) fft_x_group_kernel<R, N, OP_SUMS, false><<<gx, G::THREADS_X, sx, st>>>(g);
-        else if (sums) fft_x_group_kernel<R, N, OP_FINAL_SUMS, false><<<gx, G::THREADS_X, sx, st>>>(g);
-        else fft_x_group_kernel<R, N, OP_FINAL, false><<<gx, G::THREADS_X, sx, st>>>(g);
-      }
+      if (vreal) final_kernel<R, N, true, true>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
+      else final_kernel<R, N, true, false>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
       break;
     default: return cudaErrorInvalidValue;
   }

@@ -1,137 +1,80 @@
-// FDTD kinetic step (Eq. HK0) fused with the imaginary-time update, sm_103a.
+// FDTD kinetic step (Eq. HK0) fused with the imaginary-time update: launchers of the
+// TMA-staged kernel in qf_stencil_tma.cuh.
 //
 // (H_K^(0) psi)(r) = -1/(2 m a^2) sum over the six neighbours of (psi(nbr) - psi(r)), with
 // psi pinned to 0 on the Dirichlet planes (any index 0; a neighbour index N wraps onto
 // the plane 0).  One pass: read psi and V, write psi' = s (coef_A psi - coef_B dtau H psi)
 // into the other buffer, plus the FP64 partial sums of <psi|psi>, <psi|H_K psi>,
-// <psi|V psi> on check steps.
-//
-// Each block owns a BX x BY column tile and marches in z, keeping psi(z-1), psi(z),
-// psi(z+1) of its column in registers; the x/y neighbours come from the cache
-// hierarchy (they are read by the neighbouring threads of the same block).
-#include "qf_common.cuh"
+// <psi|V psi> on check steps.  A lone lattice is a group of one, so it runs the same
+// code alone and inside a batch.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "qf_stencil_tma.cuh"
 
 namespace qf {
 
-constexpr int ST_BX = 32, ST_BY = 4, ST_ZC = 16;
-
-template <typename R>
-__device__ __forceinline__ cpx<R> ld_masked(const cpx<R>* __restrict__ p, int n, int ix, int iy, int iz) {
-  // sites on the Dirichlet planes (index 0, or N = the plane 0 seen across the wrap) are 0
-  if (ix == 0 || iy == 0 || iz == 0 || ix == n || iy == n || iz == n) return mk<R>(R(0), R(0));
-  return p[((long long)iz * n + iy) * n + ix];
-}
-
-template <typename R>
-__device__ __forceinline__ void stencil_body(const StencilArgs<R>& a, const int n, const int bzi) {
-  __shared__ double red_s[32 * kNumSums];
-  const int ix = blockIdx.x * ST_BX + threadIdx.x;
-  const int iy = blockIdx.y * ST_BY + threadIdx.y;
-  const int z0 = bzi * ST_ZC;
-  const int z1 = min(n, z0 + ST_ZC);
-  const bool active = ix < n && iy < n;
-  CheckSums<R> cs;
-  if (active) {
-    const R sc = R(*a.scale);
-    cpx<R> zm = ld_masked<R>(a.in, n, ix, iy, z0 - 1 < 0 ? 0 : z0 - 1);
-    cpx<R> c = ld_masked<R>(a.in, n, ix, iy, z0);
-    for (int iz = z0; iz < z1; ++iz) {
-      const cpx<R> zp = ld_masked<R>(a.in, n, ix, iy, iz + 1);
-      const long long site = ((long long)iz * n + iy) * n + ix;
-      const bool interior = ix != 0 && iy != 0 && iz != 0;
-      if (interior) {
-        const cpx<R> xm = ld_masked<R>(a.in, n, ix - 1, iy, iz), xp = ld_masked<R>(a.in, n, ix + 1, iy, iz);
-        const cpx<R> ym = ld_masked<R>(a.in, n, ix, iy - 1, iz), yp = ld_masked<R>(a.in, n, ix, iy + 1, iz);
-        const cpx<R> nb = ((xm + xp) + (ym + yp)) + (zm + zp);
-        // H psi = -kcoef (sum nbr - 6 psi)
-        const cpx<R> h = mk<R>(-a.kcoef * (nb.x - R(6) * c.x), -a.kcoef * (nb.y - R(6) * c.y));
-        cpx<R> vv;
-        if (a.v_real) vv = mk<R>(reinterpret_cast<const R*>(a.v)[site], R(0));
-        else vv = reinterpret_cast<const cpx<R>*>(a.v)[site];
-        if (a.reduce) cs.add(c, h, vv);
-        if (a.write_psi) {
-          const cpx<R> d = mk<R>(R(1) + a.half_dtau * vv.x, a.half_dtau * vv.y);
-          const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), c) - cscale<R>(h, a.dtau);
-          const R inv = sc / (d.x * d.x + d.y * d.y);
-          a.out[site] = cscale<R>(cmulc<R>(num, d), inv);
-        }
-      } else if (a.write_psi) {
-        a.out[site] = mk<R>(R(0), R(0));
-      }
-      zm = c;
-      c = zp;
-    }
-  }
-  if (a.reduce) {
-    double acc[kNumSums];
-    cs.to(acc);
-    const int bid = (bzi * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    // flatten the 2D thread index for the block reduction
-    double* out = a.partials + (long long)bid * kPartialStride;
-    // block_sum_store uses threadIdx.x as the linear id: remap through a local copy
-    const int tid = threadIdx.y * ST_BX + threadIdx.x;
-    // warp-level: threads of one warp share threadIdx.y (BX = 32)
-    warp_sum<kNumSums>(acc);
-    const int lane = tid & 31, warp = tid >> 5;
-    if (lane == 0)
-      for (int i = 0; i < kNumSums; ++i) red_s[warp * kNumSums + i] = acc[i];
-    __syncthreads();
-    if (warp == 0) {
-      double t[kNumSums];
-      for (int i = 0; i < kNumSums; ++i) t[i] = lane < ST_BY ? red_s[lane * kNumSums + i] : 0.0;
-      warp_sum<kNumSums>(t);
-      if (lane == 0)
-        for (int i = 0; i < kNumSums; ++i) out[i] = t[i];
-    }
-  }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(ST_BX* ST_BY) stencil_kernel(StencilArgs<R> a, int n) {
-  stencil_body<R>(a, n, blockIdx.z);
-}
-
-// A group of lattices of the same n: blockIdx.z = member * z-chunks + z-chunk.
-template <typename R>
-__global__ void __launch_bounds__(ST_BX* ST_BY) stencil_group_kernel(const __grid_constant__ StencilGroup<R> g, int n) {
-  const int nzb = (n + ST_ZC - 1) / ST_ZC;
-  stencil_body<R>(g.a[blockIdx.z / nzb], n, blockIdx.z % nzb);
-}
-
-template cudaError_t launch_stencil_group<float>(int, const StencilGroup<float>&, cudaStream_t);
-
 template <typename R>
 int stencil_blocks(int n) {
-  return ((n + ST_BX - 1) / ST_BX) * ((n + ST_BY - 1) / ST_BY) * ((n + ST_ZC - 1) / ST_ZC);
+  return ((n + TS_X - 1) / TS_X) * ((n + TS_Y - 1) / TS_Y) * ((n + TS_Z - 1) / TS_Z);
 }
 
 template <typename R>
-cudaError_t launch_stencil_group(int n, const StencilGroup<R>& g, cudaStream_t st) {
-  dim3 grid((n + ST_BX - 1) / ST_BX, (n + ST_BY - 1) / ST_BY, ((n + ST_ZC - 1) / ST_ZC) * g.count);
-  stencil_group_kernel<R><<<grid, dim3(ST_BX, ST_BY), 0, st>>>(g, n);
+cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st) {
+  const int n = g.n;
+  dim3 grid((n + TS_X - 1) / TS_X, (n + TS_Y - 1) / TS_Y, ((n + TS_Z - 1) / TS_Z) * g.count);
+  stencil_tma_kernel<R><<<grid, dim3(TS_X, TS_Y), 0, st>>>(g);
   return cudaGetLastError();
 }
-// Complex-FP32 lattices run the grouped kernel (a lone lattice is a group of one) so a
-// lattice executes the same machine code alone and inside a batch.
-template <typename R>
-cudaError_t launch_stencil(int n, StencilArgs<R> a, cudaStream_t st, int* nblocks) {
-  dim3 grid((n + ST_BX - 1) / ST_BX, (n + ST_BY - 1) / ST_BY, (n + ST_ZC - 1) / ST_ZC);
-  dim3 block(ST_BX, ST_BY);
-  if (nblocks) *nblocks = grid.x * grid.y * grid.z;
-  if constexpr (sizeof(R) == 4) {
-    StencilGroup<R> g;
-    g.count = 1;
-    g.a[0] = a;
-    return launch_stencil_group<R>(n, g, st);
-  } else {
-    stencil_kernel<R><<<grid, block, 0, st>>>(a, n);
-    return cudaGetLastError();
+
+// Tensor map of an N^3 complex field for the stencil's plane boxes (8-byte elements:
+// one complex FP32 or one FP64 component).
+bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!encode) return false;
+  const cuuint64_t w = c64 ? (cuuint64_t)n : 2 * (cuuint64_t)n;
+  const cuuint64_t dims[3] = {w, (cuuint64_t)n, (cuuint64_t)n};
+  const cuuint64_t strides[2] = {w * 8, w * 8 * (cuuint64_t)n};
+  const cuuint32_t box[3] = {(cuuint32_t)(c64 ? TmaTile<float>::W : TmaTile<double>::W), (cuuint32_t)(TS_Y + 2), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, c64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, field,
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// Self-test of the bounded waits: an mbarrier that expects bytes nobody sends never
+// completes, so every thread's bounded wait runs out and the block reports it.
+__global__ void bounded_wait_probe(int* err) {
+  __shared__ alignas(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    mbar_expect_tx(&bar, 16);  // no copy follows
   }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0);
+  if (__syncthreads_and(ok) == 0 && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st) {
+  bounded_wait_probe<<<1, 32, 0, st>>>(err);
+  return cudaGetLastError();
 }
 
 template int stencil_blocks<float>(int);
 template int stencil_blocks<double>(int);
-template cudaError_t launch_stencil<float>(int, StencilArgs<float>, cudaStream_t, int*);
-template cudaError_t launch_stencil<double>(int, StencilArgs<double>, cudaStream_t, int*);
+template cudaError_t launch_stencil_tma<float>(const StencilTmaGroup<float>&, cudaStream_t);
+template cudaError_t launch_stencil_tma<double>(const StencilTmaGroup<double>&, cudaStream_t);
 
 }  // namespace qf

@@ -1,0 +1,207 @@
+// TMA-staged FDTD step (Eq. HK0), sm_103a.
+//
+// A block owns a 32 x 8 column tile of the output and marches through a chunk of z.  One
+// thread streams the halo-extended z-planes of the tile (x0-2 .. x0+33 or x0-1 .. x0+32,
+// y0-1 .. y0+8) from global memory into a ring of four shared-memory buffers with
+// cp.async.bulk.tensor; each buffer has an mbarrier that completes when its bytes have
+// landed.  While plane z is computed (it needs planes z-1, z, z+1) the planes z+2 and z+3
+// are in flight.  Coordinates outside the lattice are filled with zeros by the copy
+// engine; the Dirichlet planes (index 0) are masked when read.
+//
+// Every wait is bounded.  If a buffer does not complete within the limit, the block
+// agrees on it (__syncthreads_and), records the failure in *err, waits a bounded time
+// for its own copies still in flight and returns; the host reports QF_ETIMEOUT.
+#pragma once
+#include <cuda.h>
+
+#include "qf_common.cuh"
+
+namespace qf {
+
+constexpr int TS_X = 32, TS_Y = 8, TS_Z = 32, TS_BUF = 4;
+constexpr unsigned kTmaSpinLimit = 1u << 24;
+
+// words of 8 bytes per tile row: c64 x0-2 .. x0+33 (36 complex); c128 x0-1 .. x0+32 as
+// 68 doubles
+template <typename R>
+struct TmaTile {
+  static constexpr int W = sizeof(R) == 4 ? TS_X + 4 : 2 * (TS_X + 2);
+  static constexpr int PLANE_WORDS = (TS_Y + 2) * W;            // one box
+  static constexpr int STRIDE_WORDS = (PLANE_WORDS + 15) / 16 * 16;  // buffers start on 128 B
+  static constexpr unsigned BYTES = PLANE_WORDS * 8u;
+};
+
+template <typename R>
+struct alignas(64) StencilTmaGroup {
+  CUtensorMap map[kGroupMax];  // input field of member i, 3D (x, y, z), 8-byte elements
+  StencilArgs<R> a[kGroupMax];
+  int count;
+  int n;
+  int* err;  // set to 1 when a bounded wait ran out
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for phase `parity` of a buffer's barrier
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  for (unsigned it = 0; it < kTmaSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// plane p of member tile -> buffer; coordinates in elements of the tensor map
+template <typename R>
+__device__ __forceinline__ void tma_plane(const CUtensorMap* map, unsigned long long* bar, void* dst, int x0, int y0,
+                                          int z) {
+  const int cx = sizeof(R) == 4 ? x0 - 2 : 2 * (x0 - 1);  // x start: 16-byte aligned
+  const int cy = y0 - 1;
+  mbar_expect_tx(bar, TmaTile<R>::BYTES);
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(cx), "r"(cy), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename R>
+__device__ __forceinline__ cpx<R> tile_at(const unsigned long long* buf, int ix, int iy, int x0, int y0) {
+  const int row = iy - y0 + 1;
+  if constexpr (sizeof(R) == 4) {
+    const cpx<float>* b = reinterpret_cast<const cpx<float>*>(buf);
+    const cpx<float> v = b[row * TmaTile<R>::W + (ix - x0 + 2)];
+    return mk<R>(R(v.x), R(v.y));
+  } else {
+    const cpx<double>* b = reinterpret_cast<const cpx<double>*>(buf);
+    const cpx<double> v = b[(row * TmaTile<R>::W) / 2 + (ix - x0 + 1)];
+    return mk<R>(R(v.x), R(v.y));
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TS_X* TS_Y) stencil_tma_kernel(const __grid_constant__ StencilTmaGroup<R> g) {
+  __shared__ alignas(128) unsigned long long planes[TS_BUF][TmaTile<R>::STRIDE_WORDS];
+  __shared__ alignas(8) unsigned long long bars[TS_BUF];
+  __shared__ double red_s[32 * kNumSums];
+  const int n = g.n;
+  const int nzb = (n + TS_Z - 1) / TS_Z;
+  const int member = blockIdx.z / nzb, zb = blockIdx.z % nzb;
+  const StencilArgs<R>& a = g.a[member];
+  const CUtensorMap* map = &g.map[member];
+  const int tid = threadIdx.y * TS_X + threadIdx.x;
+  const int x0 = blockIdx.x * TS_X, y0 = blockIdx.y * TS_Y;
+  const int ix = x0 + threadIdx.x, iy = y0 + threadIdx.y;
+  const int z0 = zb * TS_Z, z1 = min(n, z0 + TS_Z);
+  const int pfirst = z0 - 1, plast = z1;  // planes needed (inclusive)
+  if (tid == 0) {
+    for (int b = 0; b < TS_BUF; ++b) mbar_init(&bars[b], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  int issued = pfirst - 1;  // last plane whose copy was issued
+  if (tid == 0)
+    for (int p = pfirst; p <= plast && p < pfirst + TS_BUF; ++p) {
+      tma_plane<R>(map, &bars[(p - pfirst) % TS_BUF], planes[(p - pfirst) % TS_BUF], x0, y0, p);
+      issued = p;
+    }
+  int waited = pfirst - 1;  // last plane whose buffer this thread has seen complete
+  bool ok = true;
+  const bool active = ix < n && iy < n;
+  const R sc = R(*a.scale);
+  CheckSums<R> cs;
+  for (int iz = z0; iz < z1 && ok; ++iz) {
+    // planes iz-1, iz, iz+1 must have landed
+    bool mine = true;
+    while (waited < iz + 1 && mine) {
+      const int u = waited + 1 - pfirst;
+      mine = mbar_wait_bounded(&bars[u % TS_BUF], (unsigned)((u / TS_BUF) & 1));
+      if (mine) ++waited;
+    }
+    ok = __syncthreads_and(mine) != 0;
+    if (!ok) break;
+    const unsigned long long* bm = planes[(iz - 1 - pfirst) % TS_BUF];
+    const unsigned long long* bc = planes[(iz - pfirst) % TS_BUF];
+    const unsigned long long* bp = planes[(iz + 1 - pfirst) % TS_BUF];
+    if (active) {
+      const long long site = ((long long)iz * n + iy) * n + ix;
+      const bool interior = ix != 0 && iy != 0 && iz != 0;
+      if (interior) {
+        // a neighbour index 0 (the Dirichlet plane) or n (outside, zero-filled) reads 0
+        auto nb_at = [&](const unsigned long long* b, int x, int y) {
+          return (x == 0 || y == 0 || x == n || y == n) ? mk<R>(R(0), R(0)) : tile_at<R>(b, x, y, x0, y0);
+        };
+        const cpx<R> c = tile_at<R>(bc, ix, iy, x0, y0);
+        const cpx<R> xm = nb_at(bc, ix - 1, iy), xp = nb_at(bc, ix + 1, iy);
+        const cpx<R> ym = nb_at(bc, ix, iy - 1), yp = nb_at(bc, ix, iy + 1);
+        const cpx<R> zm = (iz - 1 == 0) ? mk<R>(R(0), R(0)) : tile_at<R>(bm, ix, iy, x0, y0);
+        const cpx<R> zp = (iz + 1 == n) ? mk<R>(R(0), R(0)) : tile_at<R>(bp, ix, iy, x0, y0);
+        const cpx<R> nbs = ((xm + xp) + (ym + yp)) + (zm + zp);
+        const cpx<R> h = mk<R>(-a.kcoef * (nbs.x - R(6) * c.x), -a.kcoef * (nbs.y - R(6) * c.y));
+        cpx<R> vv;
+        if (a.v_real) vv = mk<R>(reinterpret_cast<const R*>(a.v)[site], R(0));
+        else vv = reinterpret_cast<const cpx<R>*>(a.v)[site];
+        if (a.reduce) cs.add(c, h, vv);
+        if (a.write_psi) {
+          const cpx<R> d = mk<R>(R(1) + a.half_dtau * vv.x, a.half_dtau * vv.y);
+          const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), c) - cscale<R>(h, a.dtau);
+          const R inv = sc / (d.x * d.x + d.y * d.y);
+          a.out[site] = cscale<R>(cmulc<R>(num, d), inv);
+        }
+      } else if (a.write_psi) {
+        a.out[site] = mk<R>(R(0), R(0));
+      }
+    }
+    __syncthreads();  // every thread is done with plane iz-1's buffer
+    if (tid == 0 && issued < plast) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      const int p = issued + 1;
+      tma_plane<R>(map, &bars[(p - pfirst) % TS_BUF], planes[(p - pfirst) % TS_BUF], x0, y0, p);
+      issued = p;
+    }
+  }
+  if (!ok) {
+    if (tid == 0) {
+      atomicExch(g.err, 1);
+      // copies already issued may still land in this block's shared memory
+      for (int p = waited + 1; p <= issued; ++p) {
+        const int u = p - pfirst;
+        mbar_wait_bounded(&bars[u % TS_BUF], (unsigned)((u / TS_BUF) & 1));
+      }
+    }
+    return;
+  }
+  if (a.reduce) {
+    double acc[kNumSums];
+    cs.to(acc);
+    const int bid = (zb * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    warp_sum<kNumSums>(acc);
+    const int lane = tid & 31, warp = tid >> 5;
+    if (lane == 0)
+      for (int i = 0; i < kNumSums; ++i) red_s[warp * kNumSums + i] = acc[i];
+    __syncthreads();
+    if (warp == 0) {
+      double t[kNumSums];
+      for (int i = 0; i < kNumSums; ++i) t[i] = lane < (TS_X * TS_Y) / 32 ? red_s[lane * kNumSums + i] : 0.0;
+      warp_sum<kNumSums>(t);
+      if (lane == 0)
+        for (int i = 0; i < kNumSums; ++i) a.partials[(long long)bid * kPartialStride + i] = t[i];
+    }
+  }
+}
+
+}  // namespace qf

@@ -71,6 +71,7 @@ SIGNATURES = {
     "qf_batch_members": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int]),
     "qf_batch_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "qf_batch_last_error": (C.c_char_p, [_P]),
+    "qf_selftest_bounded_wait": (C.c_int, [_P]),
     "qf_last_error": (C.c_char_p, [_P]),
     "qf_version": (C.c_char_p, []),
 }

@@ -193,3 +193,16 @@ def test_state_machine_errors():
         lat10.set_kinetic(O.FFT_REL, 1.0)      # no FFT plan for N = 10
     assert e.value.status == Q.QF_EINVAL
     lat10.set_kinetic(O.FDTD, 1.0)              # FDTD takes any even N
+
+
+def test_bounded_wait_times_out_and_context_stays_usable():
+    # a barrier nothing completes: the bounded wait must give up and report QF_ETIMEOUT,
+    # after which the same handle still computes correctly
+    from paper_2211_10185_gb300 import qfdtd as Q
+
+    n, a = 16, 0.3
+    ref, gpu = _pair(n, a, O.FDTD, 1.0, "c64", I.harmonic(n, a), seed=2)
+    assert gpu.lib.qf_selftest_bounded_wait(gpu.h) == Q.QF_ETIMEOUT
+    ref.step_n(8, check_every=4)
+    gpu.step_n(8, check_every=4)
+    assert abs(gpu.energies()["e"] - ref.energies()["e"]) < 1e-5 * abs(ref.energies()["e"])
