@@ -220,7 +220,9 @@ def bytes_per_site(kernel, prec, v_real):
     vb = r if v_real else c
     table = {
         "fft_x_fwd": 2 * c, "fft_y_fwd": 2 * c, "fft_z_mid_T": 2 * c, "fft_y_inv": 2 * c,
-        "fft_x_inv_update": 3 * c + vb, "stencil_step": 2 * c + vb,
+        # read tmp, psi, V; write psi' and the next step's x transform
+        "fft_x_inv_update": 4 * c + vb,
+        "stencil_step": 2 * c + vb,
     }
     return table.get(kernel)
 

@@ -37,11 +37,12 @@ static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Kernel kinds for the per-kernel timing of qf_profile.
 enum KernelKind {
   K_FFT_X_FWD = 0, K_FFT_Y_FWD, K_FFT_Z_MID, K_FFT_Y_INV, K_FFT_X_INV_UPDATE, K_STENCIL, K_FINISH, K_GS_DOTS,
-  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_NUM_KINDS
+  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_FFT_X_INV_SUMS, K_STENCIL_SUMS, K_NUM_KINDS
 };
 static const char* kKindNames[K_NUM_KINDS] = {"fft_x_fwd", "fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
                                                "fft_x_inv_update", "stencil_step", "finish_sums", "gs_dots",
-                                               "gs_axpy", "scale_copy", "parity", "convert"};
+                                               "gs_axpy", "scale_copy", "parity", "convert", "fft_x_inv_sums",
+                                               "stencil_sums"};
 static const int kEventPool = 4096;
 
 struct Layout {
@@ -485,11 +486,11 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
     if (lat->c64()) {
       StencilTmaGroup<float> g;
       if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
-      return launch(lat, K_STENCIL, [&] { return launch_stencil_tma<float>(g, lat->st); });
+      return launch(lat, write ? K_STENCIL : K_STENCIL_SUMS, [&] { return launch_stencil_tma<float>(g, lat->st); });
     }
     StencilTmaGroup<double> g;
     if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
-    return launch(lat, K_STENCIL, [&] { return launch_stencil_tma<double>(g, lat->st); });
+    return launch(lat, write ? K_STENCIL : K_STENCIL_SUMS, [&] { return launch_stencil_tma<double>(g, lat->st); });
   }
   // FFT terms: in place on `in` (out must equal in when writing); the scratch field is tmp.
   // A step on the live psi emits the next step's first pass and may skip its own.
@@ -501,8 +502,8 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
     p.emit_next = live ? 1 : 0;
     cpx<float>* tmp = p.data;
     for (int ps = first; ps < kFftPasses; ++ps) {
-      cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
-                             [&] { return launch_fft_pass<float>(n, ps, p, tmp, lat->st, nblocks); });
+      const int kind = (ps == kFftPasses - 1 && !write) ? K_FFT_X_INV_SUMS : K_FFT_X_FWD + ps;
+      cudaError_t e = launch(lat, kind, [&] { return launch_fft_pass<float>(n, ps, p, tmp, lat->st, nblocks); });
       if (e != cudaSuccess) return e;
     }
     lat->xfwd_valid = live;
@@ -512,8 +513,8 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
   p.emit_next = live ? 1 : 0;
   cpx<double>* tmp = p.data;
   for (int ps = first; ps < kFftPasses; ++ps) {
-    cudaError_t e = launch(lat, K_FFT_X_FWD + ps,
-                           [&] { return launch_fft_pass<double>(n, ps, p, tmp, lat->st, nblocks); });
+    const int kind = (ps == kFftPasses - 1 && !write) ? K_FFT_X_INV_SUMS : K_FFT_X_FWD + ps;
+    cudaError_t e = launch(lat, kind, [&] { return launch_fft_pass<double>(n, ps, p, tmp, lat->st, nblocks); });
     if (e != cudaSuccess) return e;
   }
   lat->xfwd_valid = live;

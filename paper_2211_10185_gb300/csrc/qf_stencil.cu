@@ -22,9 +22,15 @@ int stencil_blocks(int n) {
 
 template <typename R>
 cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(stencil_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stencil_tma_smem<R>());
+    attr = true;
+  }
   const int n = g.n;
   dim3 grid((n + TS_X - 1) / TS_X, (n + TS_Y - 1) / TS_Y, ((n + TS_Z - 1) / TS_Z) * g.count);
-  stencil_tma_kernel<R><<<grid, dim3(TS_X, TS_Y), 0, st>>>(g);
+  stencil_tma_kernel<R><<<grid, dim3(TS_X, TS_Y / TS_ROWS), stencil_tma_smem<R>(), st>>>(g);
   return cudaGetLastError();
 }
 

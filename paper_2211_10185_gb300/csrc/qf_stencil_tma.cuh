@@ -1,8 +1,9 @@
 // TMA-staged FDTD step (Eq. HK0), sm_103a.
 //
-// A block owns a 32 x 8 column tile of the output and marches through a chunk of z.  One
+// A block owns a 32 x 32 column tile of the output (each thread 4 rows) and marches through
+// a chunk of z, prefetching V one plane ahead into registers.  One
 // thread streams the halo-extended z-planes of the tile (x0-2 .. x0+33 or x0-1 .. x0+32,
-// y0-1 .. y0+8) from global memory into a ring of four shared-memory buffers with
+// y0-1 .. y0+32) from global memory into a ring of four shared-memory buffers with
 // cp.async.bulk.tensor; each buffer has an mbarrier that completes when its bytes have
 // landed.  While plane z is computed (it needs planes z-1, z, z+1) the planes z+2 and z+3
 // are in flight.  Coordinates outside the lattice are filled with zeros by the copy
@@ -18,7 +19,7 @@
 
 namespace qf {
 
-constexpr int TS_X = 32, TS_Y = 8, TS_Z = 32, TS_BUF = 4;
+constexpr int TS_X = 32, TS_Y = 32, TS_ROWS = 4, TS_Z = 32, TS_BUF = 4;  // 32 x 8 threads
 constexpr unsigned kTmaSpinLimit = 1u << 24;
 
 // words of 8 bytes per tile row: c64 x0-2 .. x0+33 (36 complex); c128 x0-1 .. x0+32 as
@@ -94,8 +95,10 @@ __device__ __forceinline__ cpx<R> tile_at(const unsigned long long* buf, int ix,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TS_X* TS_Y) stencil_tma_kernel(const __grid_constant__ StencilTmaGroup<R> g) {
-  __shared__ alignas(128) unsigned long long planes[TS_BUF][TmaTile<R>::STRIDE_WORDS];
+__global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS)) stencil_tma_kernel(const __grid_constant__ StencilTmaGroup<R> g) {
+  extern __shared__ __align__(128) unsigned long long planes_dyn[];
+  unsigned long long(*planes)[TmaTile<R>::STRIDE_WORDS] =
+      reinterpret_cast<unsigned long long(*)[TmaTile<R>::STRIDE_WORDS]>(planes_dyn);
   __shared__ alignas(8) unsigned long long bars[TS_BUF];
   __shared__ double red_s[32 * kNumSums];
   const int n = g.n;
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(TS_X* TS_Y) stencil_tma_kernel(const __grid_co
   const CUtensorMap* map = &g.map[member];
   const int tid = threadIdx.y * TS_X + threadIdx.x;
   const int x0 = blockIdx.x * TS_X, y0 = blockIdx.y * TS_Y;
-  const int ix = x0 + threadIdx.x, iy = y0 + threadIdx.y;
+  const int ix = x0 + threadIdx.x;
   const int z0 = zb * TS_Z, z1 = min(n, z0 + TS_Z);
   const int pfirst = z0 - 1, plast = z1;  // planes needed (inclusive)
   if (tid == 0) {
@@ -119,12 +122,27 @@ __global__ void __launch_bounds__(TS_X* TS_Y) stencil_tma_kernel(const __grid_co
       tma_plane<R>(map, &bars[(p - pfirst) % TS_BUF], planes[(p - pfirst) % TS_BUF], x0, y0, p);
       issued = p;
     }
+  // V of this thread's sites, one plane ahead
+  auto load_v = [&](int iz, int k) {
+    const int iy = y0 + threadIdx.y + (TS_Y / TS_ROWS) * k;
+    if (ix >= n || iy >= n || iz >= z1) return mk<R>(R(0), R(0));
+    const long long site = ((long long)iz * n + iy) * n + ix;
+    return a.v_real ? mk<R>(reinterpret_cast<const R*>(a.v)[site], R(0)) : reinterpret_cast<const cpx<R>*>(a.v)[site];
+  };
+  cpx<R> vnext[TS_ROWS];
+#pragma unroll
+  for (int k = 0; k < TS_ROWS; ++k) vnext[k] = load_v(z0, k);
   int waited = pfirst - 1;  // last plane whose buffer this thread has seen complete
   bool ok = true;
-  const bool active = ix < n && iy < n;
   const R sc = R(*a.scale);
   CheckSums<R> cs;
   for (int iz = z0; iz < z1 && ok; ++iz) {
+    cpx<R> vcur[TS_ROWS];
+#pragma unroll
+    for (int k = 0; k < TS_ROWS; ++k) {
+      vcur[k] = vnext[k];
+      vnext[k] = load_v(iz + 1, k);
+    }
     // planes iz-1, iz, iz+1 must have landed
     bool mine = true;
     while (waited < iz + 1 && mine) {
@@ -137,7 +155,10 @@ __global__ void __launch_bounds__(TS_X* TS_Y) stencil_tma_kernel(const __grid_co
     const unsigned long long* bm = planes[(iz - 1 - pfirst) % TS_BUF];
     const unsigned long long* bc = planes[(iz - pfirst) % TS_BUF];
     const unsigned long long* bp = planes[(iz + 1 - pfirst) % TS_BUF];
-    if (active) {
+#pragma unroll
+    for (int k = 0; k < TS_ROWS; ++k) {
+      const int iy = y0 + threadIdx.y + (TS_Y / TS_ROWS) * k;
+      if (ix >= n || iy >= n) continue;
       const long long site = ((long long)iz * n + iy) * n + ix;
       const bool interior = ix != 0 && iy != 0 && iz != 0;
       if (interior) {
@@ -152,9 +173,7 @@ __global__ void __launch_bounds__(TS_X* TS_Y) stencil_tma_kernel(const __grid_co
         const cpx<R> zp = (iz + 1 == n) ? mk<R>(R(0), R(0)) : tile_at<R>(bp, ix, iy, x0, y0);
         const cpx<R> nbs = ((xm + xp) + (ym + yp)) + (zm + zp);
         const cpx<R> h = mk<R>(-a.kcoef * (nbs.x - R(6) * c.x), -a.kcoef * (nbs.y - R(6) * c.y));
-        cpx<R> vv;
-        if (a.v_real) vv = mk<R>(reinterpret_cast<const R*>(a.v)[site], R(0));
-        else vv = reinterpret_cast<const cpx<R>*>(a.v)[site];
+        const cpx<R> vv = vcur[k];
         if (a.reduce) cs.add(c, h, vv);
         if (a.write_psi) {
           const cpx<R> d = mk<R>(R(1) + a.half_dtau * vv.x, a.half_dtau * vv.y);
@@ -196,12 +215,18 @@ __global__ void __launch_bounds__(TS_X* TS_Y) stencil_tma_kernel(const __grid_co
     __syncthreads();
     if (warp == 0) {
       double t[kNumSums];
-      for (int i = 0; i < kNumSums; ++i) t[i] = lane < (TS_X * TS_Y) / 32 ? red_s[lane * kNumSums + i] : 0.0;
+      for (int i = 0; i < kNumSums; ++i) t[i] = lane < (TS_X * TS_Y / TS_ROWS) / 32 ? red_s[lane * kNumSums + i] : 0.0;
       warp_sum<kNumSums>(t);
       if (lane == 0)
         for (int i = 0; i < kNumSums; ++i) a.partials[(long long)bid * kPartialStride + i] = t[i];
     }
   }
+}
+
+// dynamic shared memory of the plane ring
+template <typename R>
+constexpr size_t stencil_tma_smem() {
+  return (size_t)TS_BUF * TmaTile<R>::STRIDE_WORDS * 8;
 }
 
 }  // namespace qf
