@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <string>
 #include <algorithm>
@@ -452,6 +453,7 @@ static bool stencil_group_member(qf_lattice* lat, void* in, void* out, bool writ
   if (first) {
     g.count = 0;
     g.n = lat->d.n;
+    g.zc = kStencilZChunks[2];
     g.err = &lat->sc()->err[0];
   }
   const int i = g.count;
@@ -462,6 +464,49 @@ static bool stencil_group_member(qf_lattice* lat, void* in, void* out, bool writ
   g.a[i] = stencil_args<R>(lat, in, out, write, reduce, scale);
   g.count = i + 1;
   return true;
+}
+
+// ---- autotuner: z-chunk of the TMA stencil, per (N, precision), process-wide ----------
+static std::mutex g_tune_mu;
+static std::vector<std::pair<long long, int>> g_tuned_zc;  // key (n * 2 + c64) -> zc
+
+template <typename R>
+static int tuned_zchunk(qf_lattice* lat) {
+  const long long key = (long long)lat->d.n * 2 + (lat->c64() ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& kv : g_tuned_zc)
+      if (kv.first == key) return kv.second;
+  }
+  // time one step (psi -> scratch, no sums) for each candidate; the scratch field is
+  // overwritten by the real step afterwards
+  int best = kStencilZChunks[2];
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return best;
+  for (int zc : kStencilZChunks) {
+    StencilTmaGroup<R> g;
+    if (!stencil_group_member<R>(lat, lat->psi(), lat->tmp(), true, false, &lat->sc()->scale[0], g)) break;
+    g.zc = zc;
+    float ms = 0, tot = 0;
+    bool ok = launch_stencil_tma<R>(g, lat->st) == cudaSuccess;  // warm-up
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      ok = cudaEventRecord(e0, lat->st) == cudaSuccess && launch_stencil_tma<R>(g, lat->st) == cudaSuccess &&
+           cudaEventRecord(e1, lat->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      tot += ms;
+    }
+    lat->launches += 4;
+    if (ok && tot < best_ms) {
+      best_ms = tot;
+      best = zc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_zc.push_back({key, best});
+  return best;
 }
 
 // Reads and clears the bounded-wait failure flag of a lattice.
@@ -482,14 +527,17 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
                                 int* nblocks) {
   const int n = lat->d.n;
   if (lat->kinetic == QF_KIN_FDTD) {
-    if (nblocks) *nblocks = stencil_blocks<float>(n);
+    const int zc = lat->c64() ? tuned_zchunk<float>(lat) : tuned_zchunk<double>(lat);
+    if (nblocks) *nblocks = stencil_blocks<float>(n, zc);
     if (lat->c64()) {
       StencilTmaGroup<float> g;
       if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
+      g.zc = zc;
       return launch(lat, write ? K_STENCIL : K_STENCIL_SUMS, [&] { return launch_stencil_tma<float>(g, lat->st); });
     }
     StencilTmaGroup<double> g;
     if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
+    g.zc = zc;
     return launch(lat, write ? K_STENCIL : K_STENCIL_SUMS, [&] { return launch_stencil_tma<double>(g, lat->st); });
   }
   // FFT terms: in place on `in` (out must equal in when writing); the scratch field is tmp.
@@ -935,6 +983,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
         const int cnt = (int)std::min<size_t>(kGroupMax, g.size() - off);
         if (fdtd) {
           StencilTmaGroup<float> sg;
+          const int zc = tuned_zchunk<float>(L);
           for (int j = 0; j < cnt; ++j) {
             const int q = g[off + j];
             qf_lattice* M = b->m[run[q]].lat;
@@ -942,8 +991,9 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
             if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0))
               return bfail(b, QF_ECUDA, "tensor map encoding failed");
             // one error flag per launch: the first member's
-            nblk[q] = stencil_blocks<float>(n);
+            nblk[q] = stencil_blocks<float>(n, zc);
           }
+          sg.zc = zc;
           QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
           b->launches += 1;
         } else {

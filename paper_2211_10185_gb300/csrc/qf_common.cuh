@@ -219,7 +219,7 @@ int fft_final_blocks(int n);
 bool fft_supported(int n);
 
 template <typename R>
-int stencil_blocks(int n);
+int stencil_blocks(int n, int zc = 0);
 
 // Finishing reduction: sums nblocks partial rows in index order into sc->sums, then
 // energy and (when set_scale) sc->scale[1] = 1/sqrt(norm).

@@ -15,9 +15,11 @@
 
 namespace qf {
 
+// Partial-sum rows of one launch with z-chunk zc (the most over all chunks when zc <= 0).
 template <typename R>
-int stencil_blocks(int n) {
-  return ((n + TS_X - 1) / TS_X) * ((n + TS_Y - 1) / TS_Y) * ((n + TS_Z - 1) / TS_Z);
+int stencil_blocks(int n, int zc) {
+  if (zc <= 0) zc = kStencilZChunkMin;
+  return ((n + TS_X - 1) / TS_X) * ((n + TS_Y - 1) / TS_Y) * ((n + zc - 1) / zc);
 }
 
 template <typename R>
@@ -29,7 +31,8 @@ cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st) {
     attr = true;
   }
   const int n = g.n;
-  dim3 grid((n + TS_X - 1) / TS_X, (n + TS_Y - 1) / TS_Y, ((n + TS_Z - 1) / TS_Z) * g.count);
+  if (g.zc < 1) return cudaErrorInvalidValue;
+  dim3 grid((n + TS_X - 1) / TS_X, (n + TS_Y - 1) / TS_Y, ((n + g.zc - 1) / g.zc) * g.count);
   stencil_tma_kernel<R><<<grid, dim3(TS_X, TS_Y / TS_ROWS), stencil_tma_smem<R>(), st>>>(g);
   return cudaGetLastError();
 }
@@ -78,8 +81,8 @@ cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template int stencil_blocks<float>(int);
-template int stencil_blocks<double>(int);
+template int stencil_blocks<float>(int, int);
+template int stencil_blocks<double>(int, int);
 template cudaError_t launch_stencil_tma<float>(const StencilTmaGroup<float>&, cudaStream_t);
 template cudaError_t launch_stencil_tma<double>(const StencilTmaGroup<double>&, cudaStream_t);
 

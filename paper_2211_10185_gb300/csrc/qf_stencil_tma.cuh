@@ -19,7 +19,10 @@
 
 namespace qf {
 
-constexpr int TS_X = 32, TS_Y = 32, TS_ROWS = 4, TS_Z = 32, TS_BUF = 4;  // 32 x 8 threads
+constexpr int TS_X = 32, TS_Y = 32, TS_ROWS = 4, TS_BUF = 4;  // 32 x 8 threads
+// z-chunk per block: runtime (StencilTmaGroup::zc), picked by the autotuner from these
+constexpr int kStencilZChunks[3] = {8, 16, 32};
+constexpr int kStencilZChunkMin = 8;
 constexpr unsigned kTmaSpinLimit = 1u << 24;
 
 // words of 8 bytes per tile row: c64 x0-2 .. x0+33 (36 complex); c128 x0-1 .. x0+32 as
@@ -38,6 +41,7 @@ struct alignas(64) StencilTmaGroup {
   StencilArgs<R> a[kGroupMax];
   int count;
   int n;
+  int zc;    // planes per block (z-chunk)
   int* err;  // set to 1 when a bounded wait ran out
 };
 
@@ -95,21 +99,22 @@ __device__ __forceinline__ cpx<R> tile_at(const unsigned long long* buf, int ix,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS)) stencil_tma_kernel(const __grid_constant__ StencilTmaGroup<R> g) {
+__global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), 3) stencil_tma_kernel(const __grid_constant__ StencilTmaGroup<R> g) {
   extern __shared__ __align__(128) unsigned long long planes_dyn[];
   unsigned long long(*planes)[TmaTile<R>::STRIDE_WORDS] =
       reinterpret_cast<unsigned long long(*)[TmaTile<R>::STRIDE_WORDS]>(planes_dyn);
   __shared__ alignas(8) unsigned long long bars[TS_BUF];
   __shared__ double red_s[32 * kNumSums];
   const int n = g.n;
-  const int nzb = (n + TS_Z - 1) / TS_Z;
+  const int zc = g.zc;
+  const int nzb = (n + zc - 1) / zc;
   const int member = blockIdx.z / nzb, zb = blockIdx.z % nzb;
   const StencilArgs<R>& a = g.a[member];
   const CUtensorMap* map = &g.map[member];
   const int tid = threadIdx.y * TS_X + threadIdx.x;
   const int x0 = blockIdx.x * TS_X, y0 = blockIdx.y * TS_Y;
   const int ix = x0 + threadIdx.x;
-  const int z0 = zb * TS_Z, z1 = min(n, z0 + TS_Z);
+  const int z0 = zb * zc, z1 = min(n, z0 + zc);
   const int pfirst = z0 - 1, plast = z1;  // planes needed (inclusive)
   if (tid == 0) {
     for (int b = 0; b < TS_BUF; ++b) mbar_init(&bars[b], 1);
