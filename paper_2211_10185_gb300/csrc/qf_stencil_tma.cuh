@@ -3,9 +3,9 @@
 // A block owns a 32 x 32 column tile of the output (each thread 4 rows) and marches through
 // a chunk of z, prefetching V one plane ahead into registers.  One
 // thread streams the halo-extended z-planes of the tile (x0-2 .. x0+33 or x0-1 .. x0+32,
-// y0-1 .. y0+32) from global memory into a ring of four shared-memory buffers with
+// y0-1 .. y0+32) from global memory into a ring of six shared-memory buffers with
 // cp.async.bulk.tensor; each buffer has an mbarrier that completes when its bytes have
-// landed.  While plane z is computed (it needs planes z-1, z, z+1) the planes z+2 and z+3
+// landed.  While plane z is computed (it needs planes z-1, z, z+1) the planes z+2 .. z+4
 // are in flight.  Coordinates outside the lattice are filled with zeros by the copy
 // engine; the Dirichlet planes (index 0) are masked when read.
 //
@@ -19,7 +19,7 @@
 
 namespace qf {
 
-constexpr int TS_X = 32, TS_Y = 32, TS_ROWS = 4, TS_BUF = 4;  // 32 x 8 threads
+constexpr int TS_X = 32, TS_Y = 32, TS_ROWS = 4, TS_BUF = 6;  // 32 x 8 threads
 // z-chunk per block: runtime (StencilTmaGroup::zc), picked by the autotuner from these
 constexpr int kStencilZChunks[3] = {8, 16, 32};
 constexpr int kStencilZChunkMin = 8;
