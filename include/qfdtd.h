@@ -159,6 +159,17 @@ qf_status qf_project_excited(qf_lattice* lat, int n_states, qf_energy* out);
  * renormalisation. */
 qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int target);
 
+/* Momentum-space distribution of a field (slot as in qf_get_wavefunction; needs an
+ * FFT size).  Psi(p) is the discrete Fourier transform of psi at p = 2 pi n/(N a),
+ * n_l in (-N/2, N/2]; |Psi(p)|^2 is summed over shells b = round(|n|) and normalised to
+ * total 1 (Parseval).  Sec. 3 compares momentum-space states through
+ * y(p) = sqrt(4 pi) p Psi(p), whose square is the radial density; y[b] receives
+ * sqrt(prob[b] / dp), dp = 2 pi/(N a), its magnitude from the shell probability.  *nbins
+ * always receives the number of shells, round(sqrt(3) N/2) + 1; the arrays (p and y may
+ * be NULL) need that many entries, else QF_EINVAL.  The scratch field is overwritten. */
+qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double* p, double* prob, double* y, int max_bins,
+                                   int* nbins);
+
 /* Time step, counters and sizes of the handle. */
 qf_status qf_get_info(qf_lattice* lat, qf_info* out);
 

@@ -345,3 +345,30 @@ class Lattice:
 
     def get_wavefunction(self, slot: int = -1):
         return self.psi if slot < 0 else self.states[slot]
+
+
+# --------------------------------------------------------------------------------------
+# Momentum-space distribution (Sec. 3, Fig. 2 right: y(p) = sqrt(4 pi) p Psi(p))
+# --------------------------------------------------------------------------------------
+
+def momentum_distribution(psi: np.ndarray, a: float):
+    """Radial momentum distribution of a lattice wavefunction.
+
+    Psi(p) is the DFT of psi (numpy's fftn, a library step); |Psi(p)|^2 is summed over
+    shells of the integer lattice momentum n = (n_x, n_y, n_z), n_l in (-N/2, N/2], with
+    shell b = round(|n|).  Returns (p_b, P_b, y_b): shell momentum b 2 pi / (N a), the
+    probability in the shell (sum 1, Parseval), and y_b = sqrt(P_b / dp) with
+    dp = 2 pi / (N a), the magnitude of y(p) = sqrt(4 pi) p Psi(p) for which the radial
+    density is y(p)^2 (reading: shell average for states that are not s-waves).
+    """
+    n = psi.shape[0]
+    w = np.abs(np.fft.fftn(psi)) ** 2
+    j = np.arange(n)
+    m = np.where(j <= n // 2, j, j - n).astype(np.float64)
+    kk = np.sqrt(m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2)
+    b = np.floor(kk + 0.5).astype(np.int64)
+    nb = int(b.max()) + 1
+    P = np.bincount(b.ravel(), weights=w.ravel(), minlength=nb) / np.sum(w)
+    dp = 2 * np.pi / (n * a)
+    p = np.arange(nb) * dp
+    return p, P, np.sqrt(P / dp)

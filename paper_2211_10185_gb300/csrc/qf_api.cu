@@ -3,6 +3,8 @@
 // states and parity projection.  Every arithmetic step on fields runs in the kernels of
 // qf_fft.cu, qf_stencil.cu and qf_fields.cu; this file only sequences them.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -759,6 +761,57 @@ extern "C" qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int
   qf_status s = lat->c64() ? parity_t<float>(lat, which, axis, f) : parity_t<double>(lat, which, axis, f);
   if (s != QF_OK) return s;
   if (target == -1) lat->pending_scale = false;
+  return QF_OK;
+}
+
+// Radial momentum distribution of a field (no workspace beyond the scratch field and
+// the staging area): norm, plain forward 3D transform into the scratch field, integer
+// shell histogram.
+template <typename R>
+static qf_status momentum_t(qf_lattice* lat, void* field, int nb, double* prob_host) {
+  const int n = lat->d.n;
+  const long long ns = lat->sites;
+  double* coef = lat->sc()->gs_coef;
+  const int nblk = field_blocks();
+  const cpx<R>* f = reinterpret_cast<const cpx<R>*>(field);
+  QF_CUDA(lat, launch(lat, K_GS_DOTS, [&] { return launch_dots<R>(nullptr, 0, f, ns, lat->partials(), nblk, lat->st); }));
+  QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish_dots(lat->partials(), nblk, 0, coef, lat->st); }));
+  FftPassArgs<R> p = fft_args<R>(lat, field, false, false, &lat->sc()->scale[0]);
+  cpx<R>* tmp = p.data;
+  lat->xfwd_valid = false;
+  for (int ps : {0, 1, kFftPassZForward})
+    QF_CUDA(lat, launch(lat, K_FFT_X_FWD + (ps == kFftPassZForward ? 2 : ps),
+                        [&] { return launch_fft_pass<R>(n, ps, p, tmp, lat->st, nullptr); }));
+  const long long want = (ns + 255) / 256;
+  const int blocks = (int)(want < nblk ? want : nblk);
+  unsigned long long* part = reinterpret_cast<unsigned long long*>(lat->stage());
+  double* prob = reinterpret_cast<double*>(part + (size_t)blocks * nb);
+  if ((size_t)blocks * nb * 8 + (size_t)nb * 8 > lat->L.stage_bytes) return fail(lat, QF_ENOMEM, "staging area too small");
+  QF_CUDA(lat, launch(lat, K_CONVERT, [&] { return launch_momentum_hist<R>(tmp, n, nb, coef + 4, part, blocks, lat->st); }));
+  QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_momentum_finish(part, blocks, nb, prob, lat->st); }));
+  QF_CUDA(lat, cudaMemcpyAsync(prob_host, prob, nb * sizeof(double), cudaMemcpyDeviceToHost, lat->st));
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  return QF_OK;
+}
+
+extern "C" qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double* p, double* prob, double* y,
+                                              int max_bins, int* nbins) {
+  if (!lat || !nbins) return QF_EINVAL;
+  const int n = lat->d.n;
+  const int half = n / 2;
+  const int nb = (int)std::floor(std::sqrt(3.0 * half * half) + 0.5) + 1;
+  *nbins = nb;
+  if (!fft_supported(n)) return fail(lat, QF_EINVAL, "no FFT plan for this N");
+  if (max_bins < nb || !prob) return fail(lat, QF_EINVAL, "output arrays need *nbins entries");
+  void* f = slot_ptr(lat, slot);
+  if (!f || (slot == -1 && !lat->have_psi)) return fail(lat, QF_ESTATE, "slot holds no field");
+  qf_status s = lat->c64() ? momentum_t<float>(lat, f, nb, prob) : momentum_t<double>(lat, f, nb, prob);
+  if (s != QF_OK) return s;
+  const double dp = 2.0 * M_PI / (n * lat->d.a);
+  for (int b = 0; b < nb; ++b) {
+    if (p) p[b] = b * dp;
+    if (y) y[b] = std::sqrt(prob[b] / dp);
+  }
   return QF_OK;
 }
 

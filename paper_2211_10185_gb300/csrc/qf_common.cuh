@@ -204,6 +204,7 @@ struct CheckSums {
 // (0: x forward psi -> tmp, 1: y forward, 2: z forward x T(k) z inverse, 3: y inverse,
 // 4: x inverse + update/sums); tmp is scratch.  nblocks_final: grid of the reducing pass.
 constexpr int kFftPasses = 5;
+constexpr int kFftPassZForward = 5;  // extra pass: z forward only (plain 3D transform = 0, 1, 5)
 template <typename R>
 cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st,
                             int* nblocks_final);
@@ -254,6 +255,12 @@ cudaError_t launch_real_from_f64(R* dst, const double* src, long long n, cudaStr
 template <typename R>
 cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, long long n, cudaStream_t st);
 int field_blocks();
+// Radial momentum histogram of a transformed field (shells b = round(|n|)); see
+// qf_fields.cu.  part: per-block integer histograms (blocks x nb); out: prob[nb].
+template <typename R>
+cudaError_t launch_momentum_hist(const cpx<R>* hat, int n, int nb, const double* norm, unsigned long long* part,
+                                 int blocks, cudaStream_t st);
+cudaError_t launch_momentum_finish(const unsigned long long* part, int blocks, int nb, double* prob, cudaStream_t st);
 int fft_twiddle_count(int n);
 void fft_twiddles(int n, double* re_im);
 

@@ -557,6 +557,7 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     attr_done = true;
   }
   if (nfinal) *nfinal = gx;
@@ -569,6 +570,7 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
     case 1: fft_s_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 2: fft_s_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 3: fft_s_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p); break;
+    case 5: fft_s_kernel<R, N, 2, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 4:
       if (p.v_real) final_kernel<R, N, false, true>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(p);
       else final_kernel<R, N, false, false>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(p);
@@ -591,6 +593,7 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     attr_done = true;
   }
   const dim3 gx(N * N / G::LC, g.count), gs((N / G::L) * (N / G::P), g.count);
@@ -601,6 +604,7 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
     case 1: fft_s_group_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 2: fft_s_group_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 3: fft_s_group_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 5: fft_s_group_kernel<R, N, 2, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 4:
       if (vreal) final_kernel<R, N, true, true>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
       else final_kernel<R, N, true, false>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);

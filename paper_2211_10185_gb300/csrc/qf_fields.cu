@@ -302,6 +302,64 @@ cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, lon
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// Momentum-space distribution (Sec. 3, Fig. 2 right): radial histogram of |Psi(k)|^2 over
+// shells b = round(|n|) of the integer lattice momentum n_l in (-N/2, N/2].  Each
+// contribution is scaled so the whole transform sums to 2^60 (Parseval: N^3 <psi|psi>)
+// and added as a 64-bit integer, so the histogram does not depend on the order of the
+// atomic additions.
+// ------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kFieldThreads) momentum_hist_kernel(const cpx<R>* __restrict__ hat, int n, int nb,
+                                                                      const double* __restrict__ norm,
+                                                                      unsigned long long* part) {
+  extern __shared__ unsigned long long hist_s[];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) hist_s[b] = 0ull;
+  __syncthreads();
+  const double total = *norm * (double)n * (double)n * (double)n;
+  const double scale = total > 0 ? 1152921504606846976.0 / total : 0.0;  // 2^60 / total
+  const long long sites = (long long)n * n * n;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < sites; i += stride) {
+    const int jx = (int)(i % n), jy = (int)((i / n) % n), jz = (int)(i / ((long long)n * n));
+    const int mx = jx <= n / 2 ? jx : jx - n, my = jy <= n / 2 ? jy : jy - n, mz = jz <= n / 2 ? jz : jz - n;
+    const int b = (int)(sqrt((double)(mx * mx + my * my + mz * mz)) + 0.5);
+    const cpx<R> h = hat[i];
+    const double w = (double(h.x) * double(h.x) + double(h.y) * double(h.y)) * scale;
+    atomicAdd(&hist_s[b], __double2ull_rn(w));
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) part[(long long)blockIdx.x * nb + b] = hist_s[b];
+}
+
+template <typename R>
+cudaError_t launch_momentum_hist(const cpx<R>* hat, int n, int nb, const double* norm, unsigned long long* part,
+                                 int blocks, cudaStream_t st) {
+  momentum_hist_kernel<R><<<blocks, kFieldThreads, nb * sizeof(unsigned long long), st>>>(hat, n, nb, norm, part);
+  return cudaGetLastError();
+}
+
+// prob[b] = sum over blocks of part[.][b] / sum over all shells (integer sums: exact)
+__global__ void momentum_finish_kernel(const unsigned long long* __restrict__ part, int blocks, int nb, double* prob) {
+  __shared__ unsigned long long tot_s;
+  if (threadIdx.x == 0) tot_s = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    unsigned long long s = 0;
+    for (int k = 0; k < blocks; ++k) s += part[(long long)k * nb + b];
+    prob[b] = (double)s;
+    atomicAdd(&tot_s, s);
+  }
+  __syncthreads();
+  const double tot = (double)tot_s;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) prob[b] = tot > 0 ? prob[b] / tot : 0.0;
+}
+
+cudaError_t launch_momentum_finish(const unsigned long long* part, int blocks, int nb, double* prob, cudaStream_t st) {
+  momentum_finish_kernel<<<1, 256, 0, st>>>(part, blocks, nb, prob);
+  return cudaGetLastError();
+}
+
 #define QF_INST(R)                                                                                          \
   template cudaError_t launch_dots<R>(const cpx<R>* const*, int, const cpx<R>*, long long, double*, int,   \
                                       cudaStream_t);                                                        \
@@ -312,7 +370,9 @@ cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, lon
   template cudaError_t launch_from_f64<R>(cpx<R>*, const double*, long long, cudaStream_t);                 \
   template cudaError_t launch_to_f64<R>(double*, const cpx<R>*, const double*, long long, cudaStream_t);    \
   template cudaError_t launch_real_from_f64<R>(R*, const double*, long long, cudaStream_t);                 \
-  template cudaError_t launch_pack_f64<R>(cpx<R>*, const double*, const double*, long long, cudaStream_t);
+  template cudaError_t launch_pack_f64<R>(cpx<R>*, const double*, const double*, long long, cudaStream_t); \
+  template cudaError_t launch_momentum_hist<R>(const cpx<R>*, int, int, const double*, unsigned long long*, int,  \
+                                               cudaStream_t);
 QF_INST(float)
 QF_INST(double)
 #undef QF_INST

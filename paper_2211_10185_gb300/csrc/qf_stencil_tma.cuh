@@ -148,18 +148,27 @@ __global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), 3) stencil_tma_kernel(c
       vcur[k] = vnext[k];
       vnext[k] = load_v(iz + 1, k);
     }
-    // planes iz-1, iz, iz+1 must have landed
+    // planes iz-1, iz, iz+1 must have landed: thread 0 polls (bounded), the block learns
+    // the outcome at the barrier, then every thread observes the completed phases itself
     bool mine = true;
-    while (waited < iz + 1 && mine) {
-      const int u = waited + 1 - pfirst;
-      mine = mbar_wait_bounded(&bars[u % TS_BUF], (unsigned)((u / TS_BUF) & 1));
-      if (mine) ++waited;
-    }
+    if (tid == 0)
+      while (waited < iz + 1 && mine) {
+        const int u = waited + 1 - pfirst;
+        mine = mbar_wait_bounded(&bars[u % TS_BUF], (unsigned)((u / TS_BUF) & 1));
+        if (mine) ++waited;
+      }
     ok = __syncthreads_and(mine) != 0;
     if (!ok) break;
+    if (tid != 0)
+      for (; waited < iz + 1; ++waited) {
+        const int u = waited + 1 - pfirst;
+        mbar_try_wait(&bars[u % TS_BUF], (unsigned)((u / TS_BUF) & 1));  // completed: returns at once
+      }
     const unsigned long long* bm = planes[(iz - 1 - pfirst) % TS_BUF];
     const unsigned long long* bc = planes[(iz - pfirst) % TS_BUF];
     const unsigned long long* bp = planes[(iz + 1 - pfirst) % TS_BUF];
+    // blocks away from the boundaries read neighbours without masks
+    const bool inner = x0 > 0 && y0 > 0 && x0 + TS_X < n && y0 + TS_Y < n && iz > 1 && iz + 1 < n;
 #pragma unroll
     for (int k = 0; k < TS_ROWS; ++k) {
       const int iy = y0 + threadIdx.y + (TS_Y / TS_ROWS) * k;
@@ -167,15 +176,27 @@ __global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), 3) stencil_tma_kernel(c
       const long long site = ((long long)iz * n + iy) * n + ix;
       const bool interior = ix != 0 && iy != 0 && iz != 0;
       if (interior) {
-        // a neighbour index 0 (the Dirichlet plane) or n (outside, zero-filled) reads 0
-        auto nb_at = [&](const unsigned long long* b, int x, int y) {
-          return (x == 0 || y == 0 || x == n || y == n) ? mk<R>(R(0), R(0)) : tile_at<R>(b, x, y, x0, y0);
-        };
-        const cpx<R> c = tile_at<R>(bc, ix, iy, x0, y0);
-        const cpx<R> xm = nb_at(bc, ix - 1, iy), xp = nb_at(bc, ix + 1, iy);
-        const cpx<R> ym = nb_at(bc, ix, iy - 1), yp = nb_at(bc, ix, iy + 1);
-        const cpx<R> zm = (iz - 1 == 0) ? mk<R>(R(0), R(0)) : tile_at<R>(bm, ix, iy, x0, y0);
-        const cpx<R> zp = (iz + 1 == n) ? mk<R>(R(0), R(0)) : tile_at<R>(bp, ix, iy, x0, y0);
+        cpx<R> c, xm, xp, ym, yp, zm, zp;
+        c = tile_at<R>(bc, ix, iy, x0, y0);
+        if (inner) {
+          xm = tile_at<R>(bc, ix - 1, iy, x0, y0);
+          xp = tile_at<R>(bc, ix + 1, iy, x0, y0);
+          ym = tile_at<R>(bc, ix, iy - 1, x0, y0);
+          yp = tile_at<R>(bc, ix, iy + 1, x0, y0);
+          zm = tile_at<R>(bm, ix, iy, x0, y0);
+          zp = tile_at<R>(bp, ix, iy, x0, y0);
+        } else {
+          // a neighbour index 0 (the Dirichlet plane) or n (outside, zero-filled) reads 0
+          auto nb_at = [&](const unsigned long long* b, int x, int y) {
+            return (x == 0 || y == 0 || x == n || y == n) ? mk<R>(R(0), R(0)) : tile_at<R>(b, x, y, x0, y0);
+          };
+          xm = nb_at(bc, ix - 1, iy);
+          xp = nb_at(bc, ix + 1, iy);
+          ym = nb_at(bc, ix, iy - 1);
+          yp = nb_at(bc, ix, iy + 1);
+          zm = (iz - 1 == 0) ? mk<R>(R(0), R(0)) : tile_at<R>(bm, ix, iy, x0, y0);
+          zp = (iz + 1 == n) ? mk<R>(R(0), R(0)) : tile_at<R>(bp, ix, iy, x0, y0);
+        }
         const cpx<R> nbs = ((xm + xp) + (ym + yp)) + (zm + zp);
         const cpx<R> h = mk<R>(-a.kcoef * (nbs.x - R(6) * c.x), -a.kcoef * (nbs.y - R(6) * c.y));
         const cpx<R> vv = vcur[k];

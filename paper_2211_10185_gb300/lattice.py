@@ -101,6 +101,17 @@ class Lattice:
         _check(self.h, self.lib.qf_parity_project(self.h, int(which), int(axis), int(target)),
                "qf_parity_project")
 
+    def momentum_distribution(self, slot: int = -1):
+        """(p, prob, y) over momentum shells of the field in ``slot`` (see qfdtd.h)."""
+        nb = C.c_int()
+        self.lib.qf_momentum_distribution(self.h, int(slot), None, None, None, 0, C.byref(nb))
+        p = np.empty(nb.value)
+        prob = np.empty(nb.value)
+        y = np.empty(nb.value)
+        _check(self.h, self.lib.qf_momentum_distribution(self.h, int(slot), Q.dptr(p), Q.dptr(prob), Q.dptr(y),
+                                                         nb.value, C.byref(nb)), "qf_momentum_distribution")
+        return p, prob, y
+
     def info(self) -> dict:
         i = Q.qf_info()
         _check(self.h, self.lib.qf_get_info(self.h, C.byref(i)), "qf_get_info")

@@ -206,3 +206,26 @@ def test_bounded_wait_times_out_and_context_stays_usable():
     ref.step_n(8, check_every=4)
     gpu.step_n(8, check_every=4)
     assert abs(gpu.energies()["e"] - ref.energies()["e"]) < 1e-5 * abs(ref.energies()["e"])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("n,kind", [(16, O.FFT_SYMANZIK), (24, O.FDTD), (48, O.FFT_REL)])
+def test_momentum_distribution_matches_oracle(n, kind, prec):
+    a = 0.3
+    ref, gpu = _pair(n, a, kind, 1.0, prec, I.harmonic(n, a), seed=n)
+    ref.step_n(32, check_every=16)
+    gpu.step_n(32, check_every=16)
+    p_r, P_r, y_r = O.momentum_distribution(ref.psi, a)
+    p_g, P_g, y_g = gpu.momentum_distribution()
+    assert len(P_g) == len(P_r)
+    assert np.allclose(p_g, p_r, rtol=1e-14, atol=0)
+    assert abs(P_g.sum() - 1) < 1e-12
+    tol = {"c128": 1e-12, "c64": 3e-6}[prec]
+    assert np.max(np.abs(P_g - P_r)) < tol
+    assert np.max(np.abs(y_g - y_r)) < 1e3 * tol
+    # integer shell sums: the same call gives bitwise the same histogram
+    assert np.array_equal(gpu.momentum_distribution()[1], P_g)
+    # the step after it still matches (the scratch field was reused)
+    ref.step_n(1, check_every=1)
+    gpu.step_n(1, check_every=1)
+    assert abs(gpu.energies()["e"] - ref.energies()["e"]) < {"c128": 1e-10, "c64": 1e-5}[prec] * abs(ref.energies()["e"])

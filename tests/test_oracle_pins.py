@@ -430,3 +430,45 @@ def test_excited_state_parity_for_the_oscillator():
     bound = 10 * math.exp(-2 * lat.tau)
     assert np.vdot(O.parity(v0, O.P_PLUS), O.parity(v0, O.P_PLUS)).real > 1 - bound
     assert np.vdot(O.parity(v1, O.P_PLUS), O.parity(v1, O.P_PLUS)).real < bound
+
+
+# ----------------------------------------------------------------------------------
+# Momentum-space distribution (Sec. 3, Fig. 2 right)
+# ----------------------------------------------------------------------------------
+
+def test_momentum_distribution_of_a_gaussian_matches_its_fourier_transform():
+    # psi = exp(-r^2/(2 s^2)) is well resolved (s >> a) and small at the box edge, so its
+    # lattice transform at momentum p_n = 2 pi n/(N a) is the continuum one, with
+    # |Psi(p)|^2 proportional to exp(-p^2 s^2); sum that over the modes of each shell,
+    # enumerated one by one.
+    n, a, s = 32, 0.3, 1.0
+    r = I.radius(n, a)
+    psi = np.exp(-r * r / (2 * s * s)) + 0j
+    p, P, y = O.momentum_distribution(psi, a)
+    assert P.sum() == pytest.approx(1.0, abs=1e-13)
+    dp = 2 * np.pi / (n * a)
+    shells = {}
+    half = n // 2
+    for nz in range(-half + 1, half + 1):
+        for ny in range(-half + 1, half + 1):
+            for nx in range(-half + 1, half + 1):
+                mag = (nx * nx + ny * ny + nz * nz) ** 0.5
+                b = int(mag + 0.5)
+                shells[b] = shells.get(b, 0.0) + np.exp(-(dp * mag * s) ** 2)
+    tot = sum(shells.values())
+    for b in range(0, 10):
+        assert abs(P[b] - shells[b] / tot) < 1e-5, b
+    assert np.allclose(y, np.sqrt(P / dp))
+
+
+def test_momentum_distribution_of_a_plane_wave_is_one_shell():
+    n, a = 16, 0.5
+    x = (np.arange(n) - n // 2) * a
+    q = (3, 4, 0)    # |n| = 5
+    L = n * a
+    psi = (np.exp(2j * np.pi * q[2] * x / L)[:, None, None] * np.exp(2j * np.pi * q[1] * x / L)[None, :, None]
+           * np.exp(2j * np.pi * q[0] * x / L)[None, None, :])
+    p, P, y = O.momentum_distribution(psi, a)
+    assert P[5] == pytest.approx(1.0, abs=1e-12)
+    assert np.sum(np.abs(np.delete(P, 5))) < 1e-12
+    assert p[5] == pytest.approx(5 * 2 * np.pi / (n * a))
