@@ -66,11 +66,16 @@ typedef enum {
 /* Bulk precision: complex FP32 fields with FP64 reductions, or complex FP64 throughout. */
 typedef enum { QF_PREC_C64 = 0, QF_PREC_C128 = 1 } qf_precision;
 
-/* Parity projectors of Sec. 3. */
+/* Parity projectors of Sec. 3, and d-wave projectors (listed by the paper as future
+ * work; reading: products of single-axis mirror projectors).  R_i mirrors axis i
+ * (site i -> (N - i) mod N); for QF_P_D_K and QF_P_D2_K, i and j are the two axes other
+ * than k, and S_ij exchanges them. */
 typedef enum {
   QF_P_PLUS = 0,     /* (psi(r) + psi(-r))/2                                             */
   QF_P_MINUS = 1,    /* (psi(r) - psi(-r))/2                                             */
-  QF_P_MINUS_PK = 2  /* P^-_{p_k}: odd in axis k, even under flipping the other two; 1/4 */
+  QF_P_MINUS_PK = 2, /* P^-_{p_k}: odd in axis k, even under flipping the other two; 1/4 */
+  QF_P_D_K = 3,      /* (1 - R_i)(1 - R_j)(1 + R_k)/8: d_xy-like around axis k         */
+  QF_P_D2_K = 4      /* (1 - S_ij)/2 (1 + R_i)(1 + R_j)(1 + R_k)/8: d_{x^2-y^2}-like     */
 } qf_parity;
 
 typedef struct {
@@ -153,7 +158,8 @@ qf_status qf_energies(qf_lattice* lat, qf_energy* out);
  * min(3, n_snap); QF_ESTATE when fewer snapshots are held. */
 qf_status qf_project_excited(qf_lattice* lat, int n_states, qf_energy* out);
 
-/* Applies a parity projector (qf_parity; axis 1..3 = x, y, z for QF_P_MINUS_PK) to the
+/* Applies a parity projector (qf_parity; axis 1..3 = x, y, z for QF_P_MINUS_PK and the
+ * d-wave projectors) to the
  * live psi (target -1) or to Gram-Schmidt state 0..2 in place and renormalises it to
  * unit norm (a zero result stays zero).  Projection of the live psi cancels a pending
  * renormalisation. */
@@ -169,6 +175,14 @@ qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int target);
  * be NULL) need that many entries, else QF_EINVAL.  The scratch field is overwritten. */
 qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double* p, double* prob, double* y, int max_bins,
                                    int* nbins);
+
+/* CUDA-graph replay in qf_step_n (on by default; no counterpart in the paper).  After a
+ * check step, the check_every - 1 steps up to the next check issue the same launches
+ * every time; they are captured once into a graph (per check interval and FDTD buffer
+ * parity) and replayed.  Used when the interval fits inside max_steps, snapshots fall at
+ * its end (snap_every 0 or equal to check_every) and per-kernel profiling is off.
+ * Changing the potential or the kinetic term drops the captured graphs. */
+qf_status qf_use_graphs(qf_lattice* lat, int enable);
 
 /* Time step, counters and sizes of the handle. */
 qf_status qf_get_info(qf_lattice* lat, qf_info* out);

@@ -45,7 +45,7 @@ import math
 import numpy as np
 
 FDTD, FFT_NAIVE, FFT_SYMANZIK, FFT_REL = 0, 1, 2, 3
-P_PLUS, P_MINUS, P_MINUS_PK = 0, 1, 2
+P_PLUS, P_MINUS, P_MINUS_PK, P_D_K, P_D2_K = 0, 1, 2, 3, 4
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENOTCONV = range(7)
 
@@ -170,20 +170,37 @@ _NP_AXIS = {1: 2, 2: 1, 3: 0}
 
 
 def parity(psi: np.ndarray, which: int, axis: int = 3) -> np.ndarray:
-    """P^+, P^- and P^-_{p_k} (Sec. 3), without renormalisation.
+    """P^+, P^- and P^-_{p_k} (Sec. 3) and the d-wave projectors, without renormalisation.
 
     P^{+-} psi(r) = (psi(r) +- psi(-r)) / 2.  P^-_{p_k} (k = ``axis``) =
     ((psi(r) + psi(r with the two other axes flipped)) - (psi(r with axis k flipped)
     + psi(-r))) / 4, summed in that grouping so that mirror images are bitwise exact.
+
+    d-wave projectors (the "new projection operators (for instance, d-wave states)" the
+    paper lists as future work; reading): with the single-axis mirrors R_i, R_j of the
+    two axes other than k and R_k of axis k,
+      P_{d,k}  = (1 - R_i)(1 - R_j)(1 + R_k)/8   (d_xy-like for k = z: odd in x and in y),
+      P_{d2,k} = (1 - S_ij)/2 (1 + R_i)(1 + R_j)(1 + R_k)/8   (d_{x^2-y^2}-like for k = z),
+    S_ij exchanging the coordinates i and j.  Both are evaluated as ((a + b) - (c + d))
+    groupings of mirror images so that the symmetries hold bitwise.
     """
     if which == P_PLUS:
         return 0.5 * (psi + mirror(psi))
     if which == P_MINUS:
         return 0.5 * (psi - mirror(psi))
+    k = _NP_AXIS[axis]
+    i, j = tuple(ax for ax in (0, 1, 2) if ax != k)
     if which == P_MINUS_PK:
-        k = _NP_AXIS[axis]
-        others = tuple(ax for ax in (0, 1, 2) if ax != k)
-        return 0.25 * ((psi + mirror(psi, others)) - (mirror(psi, (k,)) + mirror(psi)))
+        return 0.25 * ((psi + mirror(psi, (i, j))) - (mirror(psi, (k,)) + mirror(psi)))
+    if which in (P_D_K, P_D2_K):
+        # (1 + R_k)/2 first: even part along k
+        e = 0.5 * (psi + mirror(psi, (k,)))
+        if which == P_D_K:
+            # (1 - R_i)(1 - R_j)/4 = ((1 + R_i R_j) - (R_i + R_j))/4
+            return 0.25 * ((e + mirror(e, (i, j))) - (mirror(e, (i,)) + mirror(e, (j,))))
+        # (1 + R_i)(1 + R_j)/4, then (1 - S_ij)/2
+        f = 0.25 * ((e + mirror(e, (i, j))) + (mirror(e, (i,)) + mirror(e, (j,))))
+        return 0.5 * (f - np.swapaxes(f, i, j))
     raise ValueError(which)
 
 

@@ -118,6 +118,13 @@ struct qf_lattice {
   // the scratch field holds the forward x transform of the live psi (written by the
   // previous step's final pass), so the next FFT step starts at its second pass
   bool xfwd_valid = false;
+  // CUDA graphs of the check_every-1 steps that follow a check (see run_chunk_graph)
+  struct Graph {
+    int check_every, live;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  bool use_graphs = true;
   // tensor maps of the two field buffers for the TMA-staged stencil
   CUtensorMap fmap[2];
   bool fmap_ok = false;
@@ -144,6 +151,11 @@ struct qf_lattice {
   double* stage() const { return reinterpret_cast<double*>(ws + L.stage); }
   bool c64() const { return d.prec == QF_PREC_C64; }
 };
+
+static void drop_graphs(qf_lattice* lat) {
+  for (auto& g : lat->graphs) cudaGraphExecDestroy(g.exec);
+  lat->graphs.clear();
+}
 
 static qf_status fail(qf_lattice* lat, qf_status s, const std::string& msg) {
   if (lat) lat->err = msg;
@@ -259,6 +271,7 @@ extern "C" qf_status qf_destroy_lattice(qf_lattice* lat) {
   cudaStreamSynchronize(lat->st);
   prof_harvest(lat);
   for (cudaEvent_t e : lat->ev_free) cudaEventDestroy(e);
+  drop_graphs(lat);
   delete lat;
   return QF_OK;
 }
@@ -311,6 +324,7 @@ extern "C" qf_status qf_set_potential(qf_lattice* lat, const double* v_re, const
   if (s != QF_OK) return s;
   lat->have_v = true;
   lat->v_real = (v_im == nullptr);
+  drop_graphs(lat);
   return QF_OK;
 }
 
@@ -329,6 +343,7 @@ extern "C" qf_status qf_set_kinetic(qf_lattice* lat, int kinetic, double mass, d
   if (kinetic != QF_KIN_FDTD && !fft_supported(lat->d.n))
     return fail(lat, QF_EINVAL, "no FFT plan for this N (use 8,12,16,24,32,48,64,96,128,192,256,384,512)");
   const double a = lat->d.a;
+  drop_graphs(lat);
   lat->kinetic = kinetic;
   lat->mass = mass;
   lat->dtau = dtau > 0 ? dtau : default_dtau(kinetic, a, mass);
@@ -621,6 +636,48 @@ static qf_status read_energy(qf_lattice* lat, double* e3) {
   return QF_OK;
 }
 
+// The check_every - 1 steps after a check step issue the same launches every time (same
+// buffers; the first uses the pending renormalisation; FFT steps start at their second
+// pass), so they are captured once into a CUDA graph per (check_every, FDTD buffer
+// parity) and replayed.  Snapshot copies and host bookkeeping stay outside the graph.
+static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every) {
+  const int k = check_every - 1;
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : lat->graphs)
+    if (g.check_every == check_every && g.live == lat->live) exec = g.exec;
+  if (!exec) {
+    // capture the k steps without touching the handle's state
+    const int live0 = lat->live;
+    const bool xv0 = lat->xfwd_valid, ps0 = lat->pending_scale;
+    const int64_t launches0 = lat->launches;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(lat->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int s = 0; s < k && e == cudaSuccess; ++s) {
+      const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[0];
+      void* in = lat->psi();
+      void* out = lat->kinetic == QF_KIN_FDTD ? lat->tmp() : in;
+      e = kinetic_pass(lat, in, out, true, false, scale, nullptr);
+      lat->pending_scale = false;
+      if (lat->kinetic == QF_KIN_FDTD) lat->live = 1 - lat->live;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(lat->st, &graph);
+    lat->live = live0;
+    lat->xfwd_valid = xv0;
+    lat->pending_scale = ps0;
+    lat->launches = launches0;
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    lat->graphs.push_back({check_every, live0, exec});
+  }
+  cudaError_t e = cudaGraphLaunch(exec, lat->st);
+  if (e != cudaSuccess) return e;
+  lat->launches += (int64_t)k * (lat->kinetic == QF_KIN_FDTD ? 1 : kFftPasses - 1);
+  return cudaSuccess;
+}
+
 extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_abs, int check_every, int snap_every,
                                int64_t* steps_done) {
   if (steps_done) *steps_done = 0;
@@ -650,6 +707,27 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
       if (record_check(lat, e3, t, tau_t, tol_abs, 0.0)) {
         status = QF_OK;
         break;
+      }
+      // the rest of the check interval as one graph replay when it fits entirely
+      const int k = check_every - 1;
+      const bool snaps_at_end = snap_every == 0 || snap_every == check_every;
+      const bool fft_ready = fdtd || lat->xfwd_valid;
+      if (lat->use_graphs && !lat->prof && k >= 2 && done + k <= max_steps && snaps_at_end && fft_ready &&
+          lat->pending_scale) {
+        QF_CUDA(lat, run_chunk_graph(lat, check_every));
+        for (int s = 0; s < k; ++s) {
+          lat->tau += lat->dtau;
+          if (fdtd) lat->live = 1 - lat->live;
+        }
+        lat->step += k;
+        lat->pending_scale = false;
+        done += k;
+        if (snap_every > 0 && lat->step % snap_every == 0) {
+          lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
+          QF_CUDA(lat, cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(),
+                                       (size_t)lat->sites * (lat->c64() ? 8 : 16), cudaMemcpyDeviceToDevice, lat->st));
+          if (lat->snap_count < lat->d.n_snap) lat->snap_count++;
+        }
       }
     }
   }
@@ -753,8 +831,8 @@ static qf_status parity_t(qf_lattice* lat, int which, int axis, void* target) {
 
 extern "C" qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int target) {
   if (!lat) return QF_EINVAL;
-  if (which < QF_P_PLUS || which > QF_P_MINUS_PK) return fail(lat, QF_EINVAL, "unknown projector");
-  if (which == QF_P_MINUS_PK && (axis < 1 || axis > 3)) return fail(lat, QF_EINVAL, "axis must be 1..3");
+  if (which < QF_P_PLUS || which > QF_P_D2_K) return fail(lat, QF_EINVAL, "unknown projector");
+  if (which >= QF_P_MINUS_PK && (axis < 1 || axis > 3)) return fail(lat, QF_EINVAL, "axis must be 1..3");
   if (target < -1 || target > 2) return fail(lat, QF_EINVAL, "target must be -1..2");
   void* f = slot_ptr(lat, target);
   if (!f || (target == -1 && !lat->have_psi)) return fail(lat, QF_ESTATE, "target holds no field");
@@ -874,6 +952,13 @@ extern "C" const char* qf_last_error(const qf_lattice* lat) {
 }
 
 extern "C" const char* qf_version(void) { return kVersion; }
+
+extern "C" qf_status qf_use_graphs(qf_lattice* lat, int enable) {
+  if (!lat) return QF_EINVAL;
+  lat->use_graphs = enable != 0;
+  if (!lat->use_graphs) drop_graphs(lat);
+  return QF_OK;
+}
 
 extern "C" qf_status qf_selftest_bounded_wait(qf_lattice* lat) {
   if (!lat) return QF_EINVAL;

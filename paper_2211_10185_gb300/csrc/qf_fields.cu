@@ -224,12 +224,42 @@ __global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restric
       const cpx<R> q = at(mx, my, mz);
       o = which == 0 ? p + q : p - q;
       o = cscale<R>(o, R(0.5));
-    } else {
+    } else if (which == 2) {
       // axis k in {1, 2, 3} = x, y, z; the other two axes flip together
       const int fx = axis == 1 ? ix : mx, fy = axis == 2 ? iy : my, fz = axis == 3 ? iz : mz;  // others flipped
       const int gx = axis == 1 ? mx : ix, gy = axis == 2 ? my : iy, gz = axis == 3 ? mz : iz;  // axis k flipped
       o = (p + at(fx, fy, fz)) - (at(gx, gy, gz) + at(mx, my, mz));
       o = cscale<R>(o, R(0.25));
+    } else {
+      // d-wave projectors: e = (1 + R_k)/2 psi at the four mirror images over the two other
+      // axes (i, j), then (1 - R_i)(1 - R_j)/4 (which 3) or (1 + R_i)(1 + R_j)/4 followed by
+      // the antisymmetrisation over exchanging i and j (which 4).  c[0..2] = (x, y, z).
+      const int ka = axis - 1, ia = ka == 0 ? 1 : 0, ja = ka == 2 ? 1 : 2;
+      auto mir = [&](int c) { return c == 0 ? 0 : n - c; };
+      auto ev = [&](const int* c) {
+        int d[3] = {c[0], c[1], c[2]};
+        const cpx<R> a0 = at(d[0], d[1], d[2]);
+        d[ka] = mir(d[ka]);
+        return cscale<R>(a0 + at(d[0], d[1], d[2]), R(0.5));
+      };
+      auto quad = [&](const int* c, bool odd) {
+        int cij[3] = {c[0], c[1], c[2]}, ci[3] = {c[0], c[1], c[2]}, cj[3] = {c[0], c[1], c[2]};
+        cij[ia] = mir(c[ia]);
+        cij[ja] = mir(c[ja]);
+        ci[ia] = mir(c[ia]);
+        cj[ja] = mir(c[ja]);
+        const cpx<R> s1 = ev(c) + ev(cij), s2 = ev(ci) + ev(cj);
+        return cscale<R>(odd ? s1 - s2 : s1 + s2, R(0.25));
+      };
+      const int c0[3] = {ix, iy, iz};
+      if (which == 3) {
+        o = quad(c0, true);
+      } else {
+        int cs[3] = {ix, iy, iz};
+        cs[ia] = c0[ja];
+        cs[ja] = c0[ia];
+        o = cscale<R>(quad(c0, false) - quad(cs, false), R(0.5));
+      }
     }
     dst[i] = o;
     nrm.add_prod(o.x, o.x);

@@ -118,6 +118,9 @@ class Lattice:
         return dict(dtau=i.dtau, step=i.step, tau=i.tau, kinetic=i.kinetic, n_snapshots=i.n_snapshots,
                     workspace_bytes=i.workspace_bytes, launches=i.launches)
 
+    def use_graphs(self, enable: bool = True):
+        _check(self.h, self.lib.qf_use_graphs(self.h, int(bool(enable))), "qf_use_graphs")
+
     def profile(self, enable: bool = True):
         _check(self.h, self.lib.qf_profile(self.h, int(bool(enable))), "qf_profile")
 

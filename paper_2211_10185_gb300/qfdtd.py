@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "QF_OK", 1: "QF_EINVAL", 2: "QF_ENOMEM", 3: "QF_ECUDA", 4: "Q
                 5: "QF_ETIMEOUT", 6: "QF_ENOTCONV"}
 QF_KIN_FDTD, QF_KIN_FFT_NAIVE, QF_KIN_FFT_SYMANZIK, QF_KIN_FFT_REL = range(4)
 QF_PREC_C64, QF_PREC_C128 = 0, 1
-QF_P_PLUS, QF_P_MINUS, QF_P_MINUS_PK = 0, 1, 2
+QF_P_PLUS, QF_P_MINUS, QF_P_MINUS_PK, QF_P_D_K, QF_P_D2_K = 0, 1, 2, 3, 4
 QF_BATCH_RUNNING = -1
 
 
@@ -73,6 +73,7 @@ SIGNATURES = {
     "qf_batch_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "qf_batch_last_error": (C.c_char_p, [_P]),
     "qf_selftest_bounded_wait": (C.c_int, [_P]),
+    "qf_use_graphs": (C.c_int, [_P, C.c_int]),
     "qf_last_error": (C.c_char_p, [_P]),
     "qf_version": (C.c_char_p, []),
 }

@@ -137,7 +137,8 @@ def test_excited_states_match_oracle_at_identical_snapshots(kind, prec):
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("which,axis", [(O.P_PLUS, 3), (O.P_MINUS, 3), (O.P_MINUS_PK, 1), (O.P_MINUS_PK, 2),
-                                        (O.P_MINUS_PK, 3)])
+                                        (O.P_MINUS_PK, 3), (O.P_D_K, 3), (O.P_D_K, 1), (O.P_D2_K, 3),
+                                        (O.P_D2_K, 2)])
 @pytest.mark.parametrize("n", [8, 12, 24])
 def test_parity_projection_matches_oracle_and_is_exactly_symmetric(n, which, axis, prec):
     a = 0.3
@@ -151,11 +152,21 @@ def test_parity_projection_matches_oracle_and_is_exactly_symmetric(n, which, axi
         assert np.array_equal(out, O.mirror(out))
     elif which == O.P_MINUS:
         assert np.array_equal(out, -O.mirror(out))
-    else:
+    elif which == O.P_MINUS_PK:
         k = O._NP_AXIS[axis]
         others = tuple(x for x in (0, 1, 2) if x != k)
         assert np.array_equal(out, -O.mirror(out, (k,)))
         assert np.array_equal(out, O.mirror(out, others))
+    else:
+        k = O._NP_AXIS[axis]
+        i, j = tuple(x for x in (0, 1, 2) if x != k)
+        assert np.array_equal(out, O.mirror(out, (k,)))
+        if which == O.P_D_K:
+            assert np.array_equal(out, -O.mirror(out, (i,)))
+            assert np.array_equal(out, -O.mirror(out, (j,)))
+        else:
+            assert np.array_equal(out, O.mirror(out, (i,)))
+            assert np.array_equal(out, -np.swapaxes(out, i, j))
 
 
 def test_parity_of_a_gs_state_target():
@@ -229,3 +240,18 @@ def test_momentum_distribution_matches_oracle(n, kind, prec):
     ref.step_n(1, check_every=1)
     gpu.step_n(1, check_every=1)
     assert abs(gpu.energies()["e"] - ref.energies()["e"]) < {"c128": 1e-10, "c64": 1e-5}[prec] * abs(ref.energies()["e"])
+
+
+@pytest.mark.parametrize("kind,prec", [(O.FDTD, "c64"), (O.FFT_REL, "c64"), (O.FDTD, "c128"), (O.FFT_NAIVE, "c128")])
+def test_graph_replay_is_bitwise_identical_to_launches(kind, prec):
+    n, a = 24, 0.25
+    v = I.cornell(n, a, 0.5, 0.2)
+    _, g1 = _pair(n, a, kind, 1.1, prec, v, seed=4)
+    _, g2 = _pair(n, a, kind, 1.1, prec, v, seed=4)
+    g2.use_graphs(False)
+    for lat in (g1, g2):
+        lat.step_n(3 * 32 + 5, check_every=32, snap_every=32)
+    assert np.array_equal(g1.get_wavefunction(), g2.get_wavefunction())
+    assert g1.energies() == g2.energies()
+    assert np.array_equal(g1.get_wavefunction(100), g2.get_wavefunction(100))
+    assert g1.info()["step"] == g2.info()["step"] == 101

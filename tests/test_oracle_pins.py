@@ -472,3 +472,42 @@ def test_momentum_distribution_of_a_plane_wave_is_one_shell():
     assert P[5] == pytest.approx(1.0, abs=1e-12)
     assert np.sum(np.abs(np.delete(P, 5))) < 1e-12
     assert p[5] == pytest.approx(5 * 2 * np.pi / (n * a))
+
+
+def test_d_wave_projectors_on_analytic_states():
+    # d_xy ~ x y g, d_{x^2-y^2} ~ (x^2 - y^2) g, with g = exp(-r^2/2); s ~ g, p_x ~ x g
+    n, a = 16, 0.75
+    x = (np.arange(n) - n // 2) * a
+    X, Y, Z = x[None, None, :], x[None, :, None], x[:, None, None]
+    g = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / 2) * np.ones((n, n, n))
+    z = I.zero_dirichlet_planes
+    s, px = z(g + 0j), z(X * g + 0j)
+    dxy, dx2y2, dyz = z(X * Y * g + 0j), z((X ** 2 - Y ** 2) * g + 0j), z(Y * Z * g + 0j)
+    D, D2 = O.P_D_K, O.P_D2_K
+    assert np.max(np.abs(O.parity(dxy, D, 3) - dxy)) < 1e-15          # d_xy: kept by P_{d,z}
+    assert np.max(np.abs(O.parity(dyz, D, 1) - dyz)) < 1e-15          # d_yz: kept by P_{d,x}
+    assert np.max(np.abs(O.parity(dx2y2, D2, 3) - dx2y2)) < 1e-15     # d_{x^2-y^2}: kept by P_{d2,z}
+    for f in (s, px, dx2y2, dyz):
+        assert np.max(np.abs(O.parity(f, D, 3))) < 1e-15
+    for f in (s, px, dxy, dyz):
+        assert np.max(np.abs(O.parity(f, D2, 3))) < 1e-15
+
+
+def test_d_wave_projectors_are_idempotent_and_exactly_symmetric():
+    n = 12
+    psi = _rand(n, 12)
+    for which in (O.P_D_K, O.P_D2_K):
+        for k in (1, 2, 3):
+            q = O.parity(psi, which, k)
+            assert np.max(np.abs(O.parity(q, which, k) - q)) < 1e-15
+            kk = O._NP_AXIS[k]
+            i, j = tuple(ax for ax in (0, 1, 2) if ax != kk)
+            assert np.array_equal(q, O.mirror(q, (kk,)))                  # even along k
+            if which == O.P_D_K:
+                assert np.array_equal(q, -O.mirror(q, (i,)))              # odd along i
+                assert np.array_equal(q, -O.mirror(q, (j,)))              # odd along j
+            else:
+                assert np.array_equal(q, O.mirror(q, (i,)))
+                assert np.array_equal(q, -np.swapaxes(q, i, j))            # odd under i <-> j
+            # d projections are orthogonal to P+ (s, d) ... and to P- (p, f) complements
+            assert np.max(np.abs(O.parity(q, O.P_MINUS))) < 1e-15
