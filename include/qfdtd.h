@@ -179,10 +179,22 @@ qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double* p, double*
 /* CUDA-graph replay in qf_step_n (on by default; no counterpart in the paper).  After a
  * check step, the check_every - 1 steps up to the next check issue the same launches
  * every time; they are captured once into a graph (per check interval and FDTD buffer
- * parity) and replayed.  Used when the interval fits inside max_steps, snapshots fall at
- * its end (snap_every 0 or equal to check_every) and per-kernel profiling is off.
+ * parity) and replayed.  Used when the handle's stream is not the legacy default stream
+ * (which cannot be captured), the interval fits inside max_steps, snapshots fall at its
+ * end (snap_every 0 or equal to check_every) and per-kernel profiling is off; if a
+ * capture fails, the handle continues with ordinary launches.
  * Changing the potential or the kinetic term drops the captured graphs. */
 qf_status qf_use_graphs(qf_lattice* lat, int enable);
+
+/* Warm start across lattice sizes (no counterpart in the paper; it shortens solves by
+ * starting from a converged coarser solution).  Sets the live psi of `fine` to the
+ * trigonometric interpolation of the field `coarse_slot` of `coarse` (slot as in
+ * qf_get_wavefunction): fine must have 2N sites, spacing a/2 (the same box) and the same
+ * precision, and both sizes FFT plans.  Coarse DFT modes with |n_l| < N/2 are kept, each
+ * axis' Nyquist coefficient is split between +-N/2, the rest of the fine spectrum is
+ * zero; fine site 2j then equals coarse site j.  Both scratch fields are overwritten;
+ * the call synchronises both streams. */
+qf_status qf_prolong(qf_lattice* coarse, int coarse_slot, qf_lattice* fine);
 
 /* Time step, counters and sizes of the handle. */
 qf_status qf_get_info(qf_lattice* lat, qf_info* out);

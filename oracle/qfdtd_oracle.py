@@ -389,3 +389,35 @@ def momentum_distribution(psi: np.ndarray, a: float):
     dp = 2 * np.pi / (n * a)
     p = np.arange(nb) * dp
     return p, P, np.sqrt(P / dp)
+
+
+# --------------------------------------------------------------------------------------
+# Warm start across lattice sizes: spectral prolongation N -> 2N on the same box
+# --------------------------------------------------------------------------------------
+
+def prolong(psi_c: np.ndarray) -> np.ndarray:
+    """Trigonometric interpolation of an N^3 field onto the 2N^3 lattice of the same box
+    (a_fine = a / 2; fine site 2 j sits on coarse site j).  The coarse DFT coefficients
+    with |n_l| < N/2 are kept; the Nyquist coefficient of each axis (n_l = N/2) is split
+    into equal halves at +N/2 and -N/2 (reading); all other fine modes are zero."""
+    nc = psi_c.shape[0]
+    nf = 2 * nc
+    h = nc // 2
+    c = np.fft.fftn(psi_c)
+    # per axis: coarse index -> list of (fine index, weight)
+    idx = []
+    for j in range(nc):
+        m = j if j <= h else j - nc
+        if m == h:
+            idx.append([(h, 0.5), (nf - h, 0.5)])
+        else:
+            idx.append([(m % nf, 1.0)])
+    f = np.zeros((nf, nf, nf), dtype=np.complex128)
+    for jz in range(nc):
+        for jy in range(nc):
+            for (fy, wy) in idx[jy]:
+                for (fz, wz) in idx[jz]:
+                    for jx in range(nc):
+                        for (fx, wx) in idx[jx]:
+                            f[fz, fy, fx] += (wz * wy * wx) * c[jz, jy, jx]
+    return np.fft.ifftn(f) * (nf ** 3 / nc ** 3)

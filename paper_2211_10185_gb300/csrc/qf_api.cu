@@ -662,6 +662,10 @@ static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every) {
       if (lat->kinetic == QF_KIN_FDTD) lat->live = 1 - lat->live;
     }
     cudaError_t e2 = cudaStreamEndCapture(lat->st, &graph);
+    if (e2 != cudaSuccess && graph) {
+      cudaGraphDestroy(graph);
+      graph = nullptr;
+    }
     lat->live = live0;
     lat->xfwd_valid = xv0;
     lat->pending_scale = ps0;
@@ -712,9 +716,17 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
       const int k = check_every - 1;
       const bool snaps_at_end = snap_every == 0 || snap_every == check_every;
       const bool fft_ready = fdtd || lat->xfwd_valid;
-      if (lat->use_graphs && !lat->prof && k >= 2 && done + k <= max_steps && snaps_at_end && fft_ready &&
-          lat->pending_scale) {
-        QF_CUDA(lat, run_chunk_graph(lat, check_every));
+      // (the legacy default stream cannot be captured; a failed capture falls back to
+      // ordinary launches for the rest of the handle's life)
+      const bool capturable = lat->st != nullptr && lat->st != cudaStreamLegacy && lat->st != cudaStreamPerThread;
+      if (lat->use_graphs && capturable && !lat->prof && k >= 2 && done + k <= max_steps && snaps_at_end &&
+          fft_ready && lat->pending_scale) {
+        if (run_chunk_graph(lat, check_every) != cudaSuccess) {
+          cudaGetLastError();
+          lat->use_graphs = false;
+          drop_graphs(lat);
+          continue;
+        }
         for (int s = 0; s < k; ++s) {
           lat->tau += lat->dtau;
           if (fdtd) lat->live = 1 - lat->live;
@@ -890,6 +902,42 @@ extern "C" qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double*
     if (p) p[b] = b * dp;
     if (y) y[b] = std::sqrt(prob[b] / dp);
   }
+  return QF_OK;
+}
+
+// Warm start: spectral prolongation of a coarse field onto a lattice of twice the size.
+template <typename R>
+static qf_status prolong_t(qf_lattice* c, void* cfield, qf_lattice* f) {
+  const int nc = c->d.n, nf = f->d.n;
+  FftPassArgs<R> pc = fft_args<R>(c, cfield, false, false, &c->sc()->scale[0]);
+  c->xfwd_valid = false;
+  for (int ps : {0, 1, kFftPassZForward})
+    QF_CUDA(c, launch(c, K_FFT_X_FWD, [&] { return launch_fft_pass<R>(nc, ps, pc, pc.data, c->st, nullptr); }));
+  QF_CUDA(c, cudaStreamSynchronize(c->st));
+  FftPassArgs<R> pf = fft_args<R>(f, f->psi(), false, false, &f->sc()->scale[0]);
+  const double scale = 1.0 / ((double)nc * nc * nc);
+  QF_CUDA(f, launch(f, K_CONVERT, [&] { return launch_pad_spectrum<R>(pc.data, nc, pf.data, scale, f->st); }));
+  f->xfwd_valid = false;
+  for (int ps : {kFftPassZInverse, 3, kFftPassXInverse})
+    QF_CUDA(f, launch(f, K_FFT_Y_INV, [&] { return launch_fft_pass<R>(nf, ps, pf, pf.data, f->st, nullptr); }));
+  QF_CUDA(f, cudaMemcpyAsync(f->psi(), pf.data, (size_t)f->sites * sizeof(cpx<R>), cudaMemcpyDeviceToDevice, f->st));
+  QF_CUDA(f, cudaStreamSynchronize(f->st));
+  return QF_OK;
+}
+
+extern "C" qf_status qf_prolong(qf_lattice* coarse, int coarse_slot, qf_lattice* fine) {
+  if (!coarse || !fine) return QF_EINVAL;
+  if (fine->d.n != 2 * coarse->d.n || fine->d.prec != coarse->d.prec ||
+      std::fabs(fine->d.a * 2.0 - coarse->d.a) > 1e-12 * coarse->d.a)
+    return fail(fine, QF_EINVAL, "fine lattice must have 2N sites, spacing a/2 and the same precision");
+  if (!fft_supported(coarse->d.n) || !fft_supported(fine->d.n))
+    return fail(fine, QF_EINVAL, "both sizes need FFT plans");
+  void* cf = slot_ptr(coarse, coarse_slot);
+  if (!cf || (coarse_slot == -1 && !coarse->have_psi)) return fail(fine, QF_ESTATE, "coarse slot holds no field");
+  qf_status s = coarse->c64() ? prolong_t<float>(coarse, cf, fine) : prolong_t<double>(coarse, cf, fine);
+  if (s != QF_OK) return s;
+  fine->have_psi = true;
+  fine->pending_scale = false;
   return QF_OK;
 }
 

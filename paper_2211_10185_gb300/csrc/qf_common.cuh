@@ -204,7 +204,9 @@ struct CheckSums {
 // (0: x forward psi -> tmp, 1: y forward, 2: z forward x T(k) z inverse, 3: y inverse,
 // 4: x inverse + update/sums); tmp is scratch.  nblocks_final: grid of the reducing pass.
 constexpr int kFftPasses = 5;
-constexpr int kFftPassZForward = 5;  // extra pass: z forward only (plain 3D transform = 0, 1, 5)
+// extra passes for plain transforms: forward = 0, 1, 5 (psi -> data); inverse, in place
+// on data and unnormalised = 6 (z), 3 (y), 7 (x)
+constexpr int kFftPassZForward = 5, kFftPassZInverse = 6, kFftPassXInverse = 7;
 template <typename R>
 cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st,
                             int* nblocks_final);
@@ -261,6 +263,9 @@ template <typename R>
 cudaError_t launch_momentum_hist(const cpx<R>* hat, int n, int nb, const double* norm, unsigned long long* part,
                                  int blocks, cudaStream_t st);
 cudaError_t launch_momentum_finish(const unsigned long long* part, int blocks, int nb, double* prob, cudaStream_t st);
+// Spectral zero-padding of an nc^3 transform into an (2 nc)^3 one (see qf_fields.cu).
+template <typename R>
+cudaError_t launch_pad_spectrum(const cpx<R>* coarse, int nc, cpx<R>* fine, double scale, cudaStream_t st);
 int fft_twiddle_count(int n);
 void fft_twiddles(int n, double* re_im);
 

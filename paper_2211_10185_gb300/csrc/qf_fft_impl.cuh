@@ -299,7 +299,8 @@ template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
 __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bid) {
   using G = Geom<R, N>;
   constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
-  constexpr bool INV = is_final(OP);
+  constexpr bool FIN = is_final(OP);
+  constexpr bool INV = FIN || OP == OP_INV;
   constexpr bool WRITE = (OP == OP_FINAL || OP == OP_FINAL_SUMS);
   constexpr bool SUMS = (OP == OP_FINAL_SUMS || OP == OP_SUMS);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -320,10 +321,10 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
     for (int r = 0; r < R0; ++r) v[b * R0 + r] = in[base + e_in<N, 0>(g, b, r)];
 
   // final pass: psi and V at the sites this thread will write (natural order)
-  cpx<R> pv[INV ? EPT : 1];
-  cpx<R> vv[INV && !VREAL ? EPT : 1];
-  R vr_[INV && VREAL ? EPT : 1];
-  if constexpr (INV) {
+  cpx<R> pv[FIN ? EPT : 1];
+  cpx<R> vv[FIN && !VREAL ? EPT : 1];
+  R vr_[FIN && VREAL ? EPT : 1];
+  if constexpr (FIN) {
     const cpx<R>* __restrict__ psi_in = a.psi;
 #pragma unroll
     for (int b = 0; b < EPT / RL; ++b)
@@ -348,7 +349,7 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
   Tile<R, N, false> t{data_s, line};
   run_stages<R, N, false, INV, 0, S - 1>(v, g, t, tw_s);
 
-  if constexpr (OP == OP_FWD) {
+  if constexpr (OP == OP_FWD || OP == OP_INV) {
 #pragma unroll
     for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
@@ -558,6 +559,8 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
     cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_kernel<R, N, 2, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_x_kernel<R, N, OP_INV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
     attr_done = true;
   }
   if (nfinal) *nfinal = gx;
@@ -571,6 +574,8 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
     case 2: fft_s_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 3: fft_s_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p); break;
     case 5: fft_s_kernel<R, N, 2, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(p); break;
+    case 6: fft_s_kernel<R, N, 2, OP_INV><<<gs, G::THREADS_S, ss, st>>>(p); break;
+    case 7: fft_x_kernel<R, N, OP_INV, false><<<gx, G::THREADS_X, sx, st>>>(p); break;
     case 4:
       if (p.v_real) final_kernel<R, N, false, true>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(p);
       else final_kernel<R, N, false, false>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(p);
@@ -594,6 +599,8 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_x_group_kernel<R, N, OP_INV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
     attr_done = true;
   }
   const dim3 gx(N * N / G::LC, g.count), gs((N / G::L) * (N / G::P), g.count);
@@ -605,6 +612,8 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
     case 2: fft_s_group_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 3: fft_s_group_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
     case 5: fft_s_group_kernel<R, N, 2, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 6: fft_s_group_kernel<R, N, 2, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 7: fft_x_group_kernel<R, N, OP_INV, false><<<gx, G::THREADS_X, sx, st>>>(g); break;
     case 4:
       if (vreal) final_kernel<R, N, true, true>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
       else final_kernel<R, N, true, false>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);

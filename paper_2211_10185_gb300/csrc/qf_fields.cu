@@ -390,6 +390,44 @@ cudaError_t launch_momentum_finish(const unsigned long long* part, int blocks, i
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------
+// Spectral prolongation nc -> nf = 2 nc on the same box: fine mode m_l in (-nf/2, nf/2]
+// takes the coarse mode m_l (mod nc) with weight 1 if |m_l| < nc/2, with weight 1/2 if
+// |m_l| = nc/2 (the coarse Nyquist coefficient split between +-nc/2), else 0, times
+// `scale` (the inverse transform that follows is unnormalised).
+// ------------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kFieldThreads) pad_spectrum_kernel(const cpx<R>* __restrict__ coarse, int nc,
+                                                                     cpx<R>* __restrict__ fine, double scale) {
+  const int nf = 2 * nc, h = nc / 2;
+  const long long total = (long long)nf * nf * nf;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  auto map = [&](int f, double* w) {
+    const int m = f <= nf / 2 ? f : f - nf;
+    const int am = m < 0 ? -m : m;
+    *w = am < h ? 1.0 : (am == h ? 0.5 : 0.0);
+    return (m % nc + nc) % nc;
+  };
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int fx = (int)(i % nf), fy = (int)((i / nf) % nf), fz = (int)(i / ((long long)nf * nf));
+    double wx, wy, wz;
+    const int cx = map(fx, &wx), cy = map(fy, &wy), cz = map(fz, &wz);
+    const double w = wx * wy * wz * scale;
+    cpx<R> o = mk<R>(R(0), R(0));
+    if (w != 0.0) {
+      const cpx<R> c = coarse[((long long)cz * nc + cy) * nc + cx];
+      o = mk<R>(R(double(c.x) * w), R(double(c.y) * w));
+    }
+    fine[i] = o;
+  }
+}
+
+template <typename R>
+cudaError_t launch_pad_spectrum(const cpx<R>* coarse, int nc, cpx<R>* fine, double scale, cudaStream_t st) {
+  pad_spectrum_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(coarse, nc, fine, scale);
+  return cudaGetLastError();
+}
+
 #define QF_INST(R)                                                                                          \
   template cudaError_t launch_dots<R>(const cpx<R>* const*, int, const cpx<R>*, long long, double*, int,   \
                                       cudaStream_t);                                                        \
@@ -402,7 +440,8 @@ cudaError_t launch_momentum_finish(const unsigned long long* part, int blocks, i
   template cudaError_t launch_real_from_f64<R>(R*, const double*, long long, cudaStream_t);                 \
   template cudaError_t launch_pack_f64<R>(cpx<R>*, const double*, const double*, long long, cudaStream_t); \
   template cudaError_t launch_momentum_hist<R>(const cpx<R>*, int, int, const double*, unsigned long long*, int,  \
-                                               cudaStream_t);
+                                               cudaStream_t);                                                       \
+  template cudaError_t launch_pad_spectrum<R>(const cpx<R>*, int, cpx<R>*, double, cudaStream_t);
 QF_INST(float)
 QF_INST(double)
 #undef QF_INST

@@ -1,8 +1,10 @@
 """``Lattice``: one libqfdtd handle whose device workspace and stream come from torch.
 
 Thin marshalling over the C ABI (include/qfdtd.h): numpy FP64 host arrays in and out,
-a torch uint8 CUDA tensor as the caller-owned workspace, torch's current stream (or a
-given one) for all GPU work.  Every method maps to one C entry point.
+a torch uint8 CUDA tensor as the caller-owned workspace, and a dedicated torch stream (or
+a given one) for all GPU work: the library synchronises it in every call that returns
+host data; torch work on other streams that reads a field (``field_tensor``) must wait
+for it.  Every method maps to one C entry point.
 """
 from __future__ import annotations
 
@@ -33,9 +35,14 @@ class Lattice:
         nbytes = C.c_size_t()
         _check(None, self.lib.qf_workspace_bytes(C.byref(self.desc), C.byref(nbytes)), "qf_workspace_bytes")
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
-        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        # a stream of its own: CUDA graphs cannot capture the legacy default stream
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
         # the caller (this object) owns the device memory; 256-byte alignment is guaranteed
         self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=dev)
+        # stream-ordered hand-over: the block may have been used on the allocating stream
+        # before, and must not be reused there while this lattice's stream still runs
+        self.stream.wait_stream(torch.cuda.current_stream(dev))
+        self.workspace.record_stream(self.stream)
         h = C.c_void_p()
         _check(None, self.lib.qf_create_lattice(C.byref(self.desc), C.c_void_p(self.workspace.data_ptr()),
                                                 nbytes.value, C.c_void_p(self.stream.cuda_stream),
@@ -100,6 +107,10 @@ class Lattice:
     def parity_project(self, which: int, axis: int = 3, target: int = -1):
         _check(self.h, self.lib.qf_parity_project(self.h, int(which), int(axis), int(target)),
                "qf_parity_project")
+
+    def prolong_from(self, coarse: "Lattice", slot: int = -1):
+        """Live psi <- spectral interpolation of ``coarse``'s field (N/2 sites, spacing 2a)."""
+        _check(self.h, self.lib.qf_prolong(coarse.h, int(slot), self.h), "qf_prolong")
 
     def momentum_distribution(self, slot: int = -1):
         """(p, prob, y) over momentum shells of the field in ``slot`` (see qfdtd.h)."""

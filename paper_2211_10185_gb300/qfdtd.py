@@ -58,6 +58,7 @@ SIGNATURES = {
     "qf_project_excited": (C.c_int, [_P, C.c_int, C.POINTER(qf_energy)]),
     "qf_parity_project": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
     "qf_get_info": (C.c_int, [_P, C.POINTER(qf_info)]),
+    "qf_prolong": (C.c_int, [_P, C.c_int, _P]),
     "qf_momentum_distribution": (C.c_int, [_P, C.c_int, _D, _D, _D, C.c_int, C.POINTER(C.c_int)]),
     "qf_field_pointer": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
     "qf_profile": (C.c_int, [_P, C.c_int]),

@@ -97,28 +97,41 @@ class Request:
     tol_rel: float = 1e-7
     max_steps: int = 20000
     dtau: float | None = None
+    warm_start: bool = False   # solve on N/2 first, then prolong (FFT kinetic terms)
 
-    def potential(self):
-        return I.cornell(self.n, self.a, self.kappa, self.sigma, 0.0)
+    def potential(self, n: int | None = None, a: float | None = None):
+        return I.cornell(n or self.n, a or self.a, self.kappa, self.sigma, 0.0)
 
-    def initial_state(self):
+    def initial_state(self, n: int | None = None, a: float | None = None):
         """Seeded Gaussian blob with a seeded width (cheap to generate for large N);
         zero on the Dirichlet planes for the FDTD term."""
+        n, a = n or self.n, a or self.a
         rng = np.random.default_rng(self.seed)
         w = rng.uniform(0.5, 2.0) / math.sqrt(self.mass)
-        r = I.radius(self.n, self.a)
+        r = I.radius(n, a)
         psi = np.exp(-0.5 * (r / w) ** 2).astype(np.complex128)
         if self.kinetic == I.FDTD:
             psi = I.zero_dirichlet_planes(psi)
         return psi
 
-    def workspace_bytes(self) -> int:
+    def coarse(self) -> bool:
+        """Whether this request starts on the N/2 lattice (FFT terms, N/2 >= 16 with a plan)."""
+        return (self.warm_start and self.kinetic != I.FDTD and self.n % 2 == 0
+                and (self.n // 2) in (16, 24, 32, 48, 64, 96, 128, 192, 256))
+
+    def workspace_bytes(self, n: int | None = None, a: float | None = None) -> int:
         lib = Q.load()
-        d = Q.qf_lattice_desc(self.n, self.a, Q.QF_PREC_C64 if self.precision == "c64" else Q.QF_PREC_C128, 3)
+        d = Q.qf_lattice_desc(n or self.n, a or self.a,
+                              Q.QF_PREC_C64 if self.precision == "c64" else Q.QF_PREC_C128, 3)
         nb = C.c_size_t()
         if lib.qf_workspace_bytes(C.byref(d), C.byref(nb)) != Q.QF_OK:
             raise ValueError("unsupported request")
         return nb.value
+
+    def footprint(self) -> int:
+        """Device bytes reserved at admission (both lattices for a warm start)."""
+        fine = self.workspace_bytes()
+        return fine + (self.workspace_bytes(self.n // 2, 2 * self.a) if self.coarse() else 0)
 
 
 @dataclasses.dataclass
@@ -131,6 +144,7 @@ class Result:
     arrival: float
     admitted: float
     finished: float
+    coarse_steps: int = 0
 
     @property
     def latency(self) -> float:
@@ -175,33 +189,52 @@ class Server:
     def _admit(self, now: float):
         kept = []
         for req in self.queue:
-            need = req.workspace_bytes()
+            need = req.footprint()
             if self.in_use + need > self.budget:
                 kept.append(req)
                 continue
-            lat = Lattice(req.n, req.a, precision=req.precision, stream=self.batch.stream)
-            lat.set_potential(req.potential())
-            lat.set_kinetic(req.kinetic, req.mass, req.dtau)
-            lat.set_wavefunction(req.initial_state())
-            self.batch.add(lat, req.max_steps, req.tol_abs, req.tol_rel)
-            self.active[req.rid] = (req, lat, now)
+            if req.coarse():
+                n, a = req.n // 2, 2 * req.a
+                lat = Lattice(n, a, precision=req.precision, stream=self.batch.stream)
+                lat.set_potential(req.potential(n, a))
+                lat.set_kinetic(req.kinetic, req.mass, req.dtau)
+                lat.set_wavefunction(req.initial_state(n, a))
+                self.batch.add(lat, req.max_steps, 10 * req.tol_abs, 10 * req.tol_rel)
+                self.active[req.rid] = (req, lat, now, "coarse", 0)
+            else:
+                lat = self._fine(req)
+                lat.set_wavefunction(req.initial_state())
+                self.batch.add(lat, req.max_steps, req.tol_abs, req.tol_rel)
+                self.active[req.rid] = (req, lat, now, "fine", 0)
             self.in_use += need
             self.peak_in_use = max(self.peak_in_use, self.in_use)
         self.queue = kept
 
+    def _fine(self, req: Request) -> Lattice:
+        lat = Lattice(req.n, req.a, precision=req.precision, stream=self.batch.stream)
+        lat.set_potential(req.potential())
+        lat.set_kinetic(req.kinetic, req.mass, req.dtau)
+        return lat
+
     def _retire(self, now: float):
         status = self.batch.status()
-        done = []
-        for lat, (st, steps) in zip(list(self.batch.members), status):
-            if st == Q.QF_BATCH_RUNNING:
-                continue
-            done.append((lat, st, steps))
+        done = [(lat, st, steps) for lat, (st, steps) in zip(list(self.batch.members), status)
+                if st != Q.QF_BATCH_RUNNING]
         for lat, st, steps in done:
-            rid = next(r for r, (_, l, _) in self.active.items() if l is lat)
-            req, _, admitted = self.active.pop(rid)
-            e = lat.energies()
-            self.results.append(Result(rid, st, steps, e["e"], e["de"], req.arrival, admitted, now))
+            rid = next(r for r, v in self.active.items() if v[1] is lat)
+            req, _, admitted, phase, coarse_steps = self.active.pop(rid)
             self.batch.remove(lat)
+            if phase == "coarse":
+                # warm start: prolong the coarse solution onto the requested lattice
+                fine = self._fine(req)
+                fine.prolong_from(lat)
+                lat.close()
+                self.batch.add(fine, req.max_steps, req.tol_abs, req.tol_rel)
+                self.active[rid] = (req, fine, admitted, "fine", steps)
+                self.in_use -= req.footprint() - req.workspace_bytes()
+                continue
+            e = lat.energies()
+            self.results.append(Result(rid, st, steps, e["e"], e["de"], req.arrival, admitted, now, coarse_steps))
             self.in_use -= req.workspace_bytes()
             lat.close()
 

@@ -117,3 +117,25 @@ def test_server_retires_all_requests_within_budget_and_matches_alone():
         assert r1.status == r2.status and r1.steps == r2.steps
         assert r1.energy == r2.energy
         assert r1.status in (Q.QF_OK, Q.QF_ENOTCONV)
+
+
+def test_warm_start_converges_to_the_same_state_in_fewer_fine_steps():
+    import dataclasses
+
+    from paper_2211_10185_gb300 import qfdtd as Q
+    from paper_2211_10185_gb300.serve import Server, served_mix
+
+    reqs = [r for r in served_mix(40, rate=1000.0, sizes=(48, 64), seed=5, max_steps=6000, kinetics=(1, 2, 3))][:4]
+    budget = 8 * max(r.footprint() for r in reqs)
+    cold = Server(budget, chunk=64).run(reqs, realtime=False)
+    warm_reqs = [dataclasses.replace(r, warm_start=True) for r in reqs]
+    srv = Server(budget, chunk=64)
+    warm = srv.run(warm_reqs, realtime=False)
+    assert srv.peak_in_use <= budget
+    c = {r.rid: r for r in cold}
+    for r in warm:
+        assert r.coarse_steps > 0
+        if r.status == Q.QF_OK and c[r.rid].status == Q.QF_OK:
+            # the same ground state (tolerance-level agreement), reached in fewer fine steps
+            assert abs(r.energy - c[r.rid].energy) < 1e-5 * max(1.0, abs(c[r.rid].energy))
+            assert r.steps <= c[r.rid].steps

@@ -255,3 +255,20 @@ def test_graph_replay_is_bitwise_identical_to_launches(kind, prec):
     assert g1.energies() == g2.energies()
     assert np.array_equal(g1.get_wavefunction(100), g2.get_wavefunction(100))
     assert g1.info()["step"] == g2.info()["step"] == 101
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("nc", [8, 12, 16, 24])
+def test_prolongation_matches_oracle(nc, prec):
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    a = 0.4
+    coarse = Lattice(nc, a, precision=prec)
+    psi = I.gaussian_field(nc, nc + 1)
+    coarse.set_wavefunction(psi)
+    fine = Lattice(2 * nc, a / 2, precision=prec)
+    fine.prolong_from(coarse)
+    ref = O.prolong(coarse.get_wavefunction())
+    got = fine.get_wavefunction()
+    assert _rel(got, ref) < {"c128": 1e-13, "c64": 1e-6}[prec]
+    assert np.max(np.abs(got[::2, ::2, ::2] - coarse.get_wavefunction())) < {"c128": 1e-12, "c64": 1e-5}[prec]

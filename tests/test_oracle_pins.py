@@ -511,3 +511,30 @@ def test_d_wave_projectors_are_idempotent_and_exactly_symmetric():
                 assert np.array_equal(q, -np.swapaxes(q, i, j))            # odd under i <-> j
             # d projections are orthogonal to P+ (s, d) ... and to P- (p, f) complements
             assert np.max(np.abs(O.parity(q, O.P_MINUS))) < 1e-15
+
+
+# ----------------------------------------------------------------------------------
+# Spectral prolongation N -> 2N (warm start across lattice sizes)
+# ----------------------------------------------------------------------------------
+
+def test_prolongation_keeps_coarse_values_and_band_limited_functions():
+    nc = 8
+    psi = _rand(nc, 13)
+    f = O.prolong(psi)
+    # fine site 2 j coincides with coarse site j
+    assert np.max(np.abs(f[::2, ::2, ::2] - psi)) < 1e-13
+    # a band-limited periodic function is reproduced at every fine site
+    L = 2 * np.pi
+    xc = (np.arange(nc) - nc // 2) * (L / nc)
+    xf = (np.arange(2 * nc) - nc) * (L / (2 * nc))
+
+    def fn(x):
+        X, Y, Z = x[None, None, :], x[None, :, None], x[:, None, None]
+        return np.exp(1j * (2 * X - Y)) + 0.5 * np.cos(3 * Z) * np.sin(X) + 0.2
+
+    assert np.max(np.abs(O.prolong(fn(xc)) - fn(xf))) < 1e-12
+    # the Nyquist mode cos(4 x) (coarse N = 8) stays real and even on the fine grid
+    nyq = np.cos(4 * xc)[None, None, :] * np.ones((nc, nc, nc))
+    fny = O.prolong(nyq + 0j)
+    assert np.max(np.abs(fny.imag)) < 1e-13
+    assert np.max(np.abs(fny[::2, ::2, ::2] - nyq)) < 1e-13
