@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--workload", default="cornell_rel_n256")
     ap.add_argument("--n", type=int, default=None, help="override the lattice size")
     ap.add_argument("--precision", default=None, choices=[None, "c64", "c128"])
+    ap.add_argument("--tblock", type=int, default=2, choices=[1, 2],
+                    help="FDTD steps per pass over HBM (complex FP32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
@@ -223,13 +225,15 @@ def bytes_per_site(kernel, prec, v_real):
         # read tmp, psi, V; write psi' and the next step's x transform
         "fft_x_inv_update": 4 * c + vb,
         "stencil_step": 2 * c + vb,
+        # two steps per launch: read psi_t and V, write psi_{t+2}
+        "stencil_2step": 2 * c + vb,
     }
     return table.get(kernel)
 
 
 def source_digest():
     h = hashlib.sha256()
-    for f in ("qf_fft_impl.cuh", "qf_common.cuh", "qf_stencil.cu"):
+    for f in ("qf_fft_impl.cuh", "qf_common.cuh", "qf_stencil.cu", "qf_stencil_tma.cuh", "qf_stencil_tb.cuh"):
         with open(os.path.join(ROOT, "paper_2211_10185_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -381,6 +385,7 @@ def run_ours(args):
     lat.set_potential(v)
     lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
     lat.set_wavefunction(psi0)
+    lat.set_temporal_blocking(args.tblock)
 
     def bench_step():
         lat.step_n(CHUNK, tol=0.0, check_every=CHUNK, snap_every=CHUNK)
@@ -462,7 +467,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == "c64" else "f64",
             "data": "synthetic (seeded SplitMix64/Box-Muller psi0, analytic Cornell potential); replicas per GPU",
-            "config": dict(workload_config(w, prec), parallelism=f"replicas x{world}"),
+            "config": dict(workload_config(w, prec), parallelism=f"replicas x{world}",
+                           **({"temporal_block": args.tblock} if w["kinetic"] == I.FDTD and prec == "c64" else {})),
             "roofline": roof,
             "kernels": kernels,
             "profiled_region_ms_per_step": ms_prof / args.steps,

@@ -101,6 +101,7 @@ typedef struct {
   int n_snapshots;    /* snapshots currently held (<= n_snap)                        */
   size_t workspace_bytes;
   int64_t launches;   /* kernels this handle has launched so far                     */
+  int temporal_block; /* FDTD steps fused per pass (qf_set_temporal_blocking)         */
 } qf_info;
 
 typedef struct {
@@ -185,6 +186,16 @@ qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double* p, double*
  * capture fails, the handle continues with ordinary launches.
  * Changing the potential or the kinetic term drops the captured graphs. */
 qf_status qf_use_graphs(qf_lattice* lat, int enable);
+
+/* Temporal blocking of the FDTD step (the step of Sec. 2 with the Eq. HK0 term; no
+ * counterpart in the paper).  k = 2, the default: on complex-FP32 lattices qf_step_n
+ * runs two consecutive steps with no check at either and no snapshot after the first as
+ * one pass over HBM (psi_t and V read once, psi_{t+2} written once, psi_{t+1} kept in
+ * shared memory).  The fields are bitwise those of two single steps.  Requires the live
+ * field to be zero on the Dirichlet planes, which holds after any FDTD step; the first
+ * step after qf_set_wavefunction always runs alone.  k = 1 runs every step alone.  Other
+ * precisions and kinetic terms ignore the setting.  QF_EINVAL unless k is 1 or 2. */
+qf_status qf_set_temporal_blocking(qf_lattice* lat, int k);
 
 /* Warm start across lattice sizes (no counterpart in the paper; it shortens solves by
  * starting from a converged coarser solution).  Sets the live psi of `fine` to the

@@ -16,10 +16,12 @@
 
 #include "../../include/qfdtd.h"
 #include "qf_common.cuh"
-#include "qf_stencil_tma.cuh"
+#include "qf_stencil_tb.cuh"
 
 namespace qf {
 bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64);
+bool encode_tb_map(CUtensorMap* map, void* field, int n);
+cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st);
 cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st);
 template <typename R>
 cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st);
@@ -40,12 +42,12 @@ static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Kernel kinds for the per-kernel timing of qf_profile.
 enum KernelKind {
   K_FFT_X_FWD = 0, K_FFT_Y_FWD, K_FFT_Z_MID, K_FFT_Y_INV, K_FFT_X_INV_UPDATE, K_STENCIL, K_FINISH, K_GS_DOTS,
-  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_FFT_X_INV_SUMS, K_STENCIL_SUMS, K_NUM_KINDS
+  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_FFT_X_INV_SUMS, K_STENCIL_SUMS, K_STENCIL_2STEP, K_NUM_KINDS
 };
 static const char* kKindNames[K_NUM_KINDS] = {"fft_x_fwd", "fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
                                                "fft_x_inv_update", "stencil_step", "finish_sums", "gs_dots",
                                                "gs_axpy", "scale_copy", "parity", "convert", "fft_x_inv_sums",
-                                               "stencil_sums"};
+                                               "stencil_sums", "stencil_2step"};
 static const int kEventPool = 4096;
 
 struct Layout {
@@ -120,14 +122,23 @@ struct qf_lattice {
   bool xfwd_valid = false;
   // CUDA graphs of the check_every-1 steps that follow a check (see run_chunk_graph)
   struct Graph {
-    int check_every, live;
+    int check_every, live, tblock;
     cudaGraphExec_t exec;
+    int flips;         // FDTD buffer swaps done by the replay
+    int64_t launches;  // kernels in the graph
   };
   std::vector<Graph> graphs;
   bool use_graphs = true;
-  // tensor maps of the two field buffers for the TMA-staged stencil
+  // tensor maps of the two field buffers for the TMA-staged stencil (one-site halo) and
+  // for the two-step stencil (two-site halo, complex FP32)
   CUtensorMap fmap[2];
   bool fmap_ok = false;
+  CUtensorMap tbmap[2];
+  bool tbmap_ok = false;
+  // FDTD steps fused per pass (1 or 2) and whether the live field is known to be zero on
+  // the Dirichlet planes (it is after any FDTD step), which the two-step kernel needs
+  int tblock = 2;
+  bool clean = false;
   std::string err;
   // launch accounting and optional CUDA-event timing per kernel kind
   int64_t launches = 0;
@@ -262,6 +273,8 @@ extern "C" qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws
   }
   lat->fmap_ok = encode_stencil_map(&lat->fmap[0], lat->field(0), desc->n, desc->prec == QF_PREC_C64) &&
                  encode_stencil_map(&lat->fmap[1], lat->field(1), desc->n, desc->prec == QF_PREC_C64);
+  lat->tbmap_ok = desc->prec == QF_PREC_C64 && encode_tb_map(&lat->tbmap[0], lat->field(0), desc->n) &&
+                  encode_tb_map(&lat->tbmap[1], lat->field(1), desc->n);
   *out = lat;
   return QF_OK;
 }
@@ -344,6 +357,7 @@ extern "C" qf_status qf_set_kinetic(qf_lattice* lat, int kinetic, double mass, d
     return fail(lat, QF_EINVAL, "no FFT plan for this N (use 8,12,16,24,32,48,64,96,128,192,256,384,512)");
   const double a = lat->d.a;
   drop_graphs(lat);
+  lat->clean = false;
   lat->kinetic = kinetic;
   lat->mass = mass;
   lat->dtau = dtau > 0 ? dtau : default_dtau(kinetic, a, mass);
@@ -383,6 +397,7 @@ extern "C" qf_status qf_set_wavefunction(qf_lattice* lat, const double* re_im) {
   lat->have_psi = true;
   lat->pending_scale = false;
   lat->xfwd_valid = false;
+  lat->clean = false;
   return QF_OK;
 }
 
@@ -458,7 +473,8 @@ static StencilArgs<R> stencil_args(qf_lattice* lat, void* in, void* out, bool wr
                                    const double* scale) {
   const double a = lat->d.a, m = lat->mass, dt = lat->dtau;
   return StencilArgs<R>{reinterpret_cast<const cpx<R>*>(in), reinterpret_cast<cpx<R>*>(out), lat->ws + lat->L.v,
-                        lat->v_real, (R)(1.0 / (2.0 * m * a * a)), (R)(0.5 * dt), (R)dt, scale, lat->partials(),
+                        lat->v_real, (R)(1.0 / (2.0 * m * a * a)), (R)(0.5 * dt), (R)dt,
+                        (R)(dt / (2.0 * m * a * a)), scale, lat->partials(),
                         write ? 1 : 0, reduce ? 1 : 0};
 }
 
@@ -538,6 +554,77 @@ static qf_status check_device_error(qf_lattice* lat) {
   return QF_OK;
 }
 
+// ---- two FDTD steps per pass (complex FP32) ----------------------------------------------
+static void tb_args(qf_lattice* lat, const double* scale, int zc, StencilTbArgs& g) {
+  const double a = lat->d.a, m = lat->mass, dt = lat->dtau;
+  g.map = lat->tbmap[lat->live];
+  g.out = reinterpret_cast<cpx<float>*>(lat->tmp());
+  g.v = lat->ws + lat->L.v;
+  g.v_real = lat->v_real ? 1 : 0;
+  // the same single-precision constants as the single-step kernel
+  g.half_dtau = (float)(0.5 * dt);
+  g.kd = (float)(dt / (2.0 * m * a * a));
+  g.scale = scale;
+  g.n = lat->d.n;
+  g.zc = zc;
+  g.err = &lat->sc()->err[0];
+}
+
+static std::vector<std::pair<long long, int>> g_tuned_tb;  // key n -> zc
+
+// z-chunk of the two-step kernel per N, timed on first use (psi -> scratch; the scratch
+// field is overwritten by the real pass afterwards).  Must not run during a capture.
+static int tuned_tb_zchunk(qf_lattice* lat) {
+  const long long key = lat->d.n;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto& kv : g_tuned_tb)
+      if (kv.first == key) return kv.second;
+  }
+  int best = kTbZChunks[1];
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return best;
+  for (int zc : kTbZChunks) {
+    StencilTbArgs g;
+    tb_args(lat, &lat->sc()->scale[0], zc, g);
+    float ms = 0, tot = 0;
+    bool ok = launch_stencil_tb(g, lat->st) == cudaSuccess;  // warm-up
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      ok = cudaEventRecord(e0, lat->st) == cudaSuccess && launch_stencil_tb(g, lat->st) == cudaSuccess &&
+           cudaEventRecord(e1, lat->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      tot += ms;
+    }
+    lat->launches += 4;
+    if (ok && tot < best_ms) {
+      best_ms = tot;
+      best = zc;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_tb.push_back({key, best});
+  return best;
+}
+
+// Whether steps t and t+1 may run as one two-step pass: complex FP32 FDTD with blocking
+// on and a clean live field, no check at t or t+1 and no snapshot after step t.
+static bool fuse_pair(const qf_lattice* lat, int64_t t, int check_every, int snap_every) {
+  if (lat->kinetic != QF_KIN_FDTD || !lat->c64() || lat->tblock < 2 || !lat->clean || !lat->tbmap_ok) return false;
+  if (check_every > 0 && (t % check_every == 0 || (t + 1) % check_every == 0)) return false;
+  if (snap_every > 0 && (t + 1) % snap_every == 0) return false;
+  return true;
+}
+
+// psi_{t+2} into the scratch field; `scale` renormalises the first of the two steps.
+static cudaError_t fdtd_pair(qf_lattice* lat, const double* scale, int zc) {
+  StencilTbArgs g;
+  tb_args(lat, scale, zc, g);
+  return launch(lat, K_STENCIL_2STEP, [&] { return launch_stencil_tb(g, lat->st); });
+}
+
 // One kinetic application on `in` (psi' written to `out` when write), with FP64 sums
 // when reduce; returns the number of partial rows written through nblocks.
 static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write, bool reduce, const double* scale,
@@ -586,6 +673,19 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
   return cudaSuccess;
 }
 
+// Copies the live field into the next ring slot when the step count is a multiple of
+// snap_every.
+static cudaError_t take_snapshot(qf_lattice* lat, int snap_every, cudaStream_t st) {
+  if (snap_every > 0 && lat->step % snap_every == 0) {
+    lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
+    cudaError_t e = cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(), (size_t)lat->sites * (lat->c64() ? 8 : 16),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    if (lat->snap_count < lat->d.n_snap) lat->snap_count++;
+  }
+  return cudaSuccess;
+}
+
 // Bookkeeping after the kinetic pass of step t has been issued on `st` (shared by
 // qf_step_n and qf_batch_step so both advance a lattice identically): finishing sums and
 // the pending renormalisation on a check step, buffer swap (FDTD), counters, snapshot.
@@ -596,17 +696,25 @@ static cudaError_t after_step(qf_lattice* lat, bool check, int nb, int snap_ever
     if (e != cudaSuccess) return e;
     lat->pending_scale = true;
   }
-  if (lat->kinetic == QF_KIN_FDTD) lat->live = 1 - lat->live;
+  if (lat->kinetic == QF_KIN_FDTD) {
+    lat->live = 1 - lat->live;
+    lat->clean = true;
+  }
   lat->step += 1;
   lat->tau += lat->dtau;
-  if (snap_every > 0 && lat->step % snap_every == 0) {
-    lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
-    cudaError_t e = cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(), (size_t)lat->sites * (lat->c64() ? 8 : 16),
-                                    cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return e;
-    if (lat->snap_count < lat->d.n_snap) lat->snap_count++;
+  return take_snapshot(lat, snap_every, st);
+}
+
+// Bookkeeping after a two-step pass (steps t and t+1): one buffer swap, two steps.
+static cudaError_t after_pair(qf_lattice* lat, int snap_every, cudaStream_t st) {
+  lat->pending_scale = false;
+  lat->live = 1 - lat->live;
+  lat->clean = true;
+  for (int i = 0; i < 2; ++i) {
+    lat->step += 1;
+    lat->tau += lat->dtau;
   }
-  return cudaSuccess;
+  return take_snapshot(lat, snap_every, st);
 }
 
 // Records the energy of the check at step t; returns whether |E_t - E_prev| < tol where
@@ -638,47 +746,74 @@ static qf_status read_energy(qf_lattice* lat, double* e3) {
 
 // The check_every - 1 steps after a check step issue the same launches every time (same
 // buffers; the first uses the pending renormalisation; FFT steps start at their second
-// pass), so they are captured once into a CUDA graph per (check_every, FDTD buffer
-// parity) and replayed.  Snapshot copies and host bookkeeping stay outside the graph.
-static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every) {
+// pass; FDTD steps pair up as in the uncaptured loop), so they are captured once into a
+// CUDA graph per (check_every, FDTD buffer parity, blocking) and replayed.  Snapshot
+// copies and host bookkeeping stay outside the graph.  *flips receives the number of
+// FDTD buffer swaps the replay did.
+static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every, int* flips) {
   const int k = check_every - 1;
-  cudaGraphExec_t exec = nullptr;
+  const qf_lattice::Graph* hit = nullptr;
   for (auto& g : lat->graphs)
-    if (g.check_every == check_every && g.live == lat->live) exec = g.exec;
-  if (!exec) {
+    if (g.check_every == check_every && g.live == lat->live && g.tblock == lat->tblock) hit = &g;
+  if (!hit) {
     // capture the k steps without touching the handle's state
     const int live0 = lat->live;
-    const bool xv0 = lat->xfwd_valid, ps0 = lat->pending_scale;
+    const bool xv0 = lat->xfwd_valid, ps0 = lat->pending_scale, clean0 = lat->clean;
     const int64_t launches0 = lat->launches;
+    const bool pairs = lat->kinetic == QF_KIN_FDTD && lat->c64() && lat->tblock >= 2 && lat->tbmap_ok;
+    const int tzc = pairs ? tuned_tb_zchunk(lat) : 0;  // timed outside the capture
+    if (lat->kinetic == QF_KIN_FDTD) {
+      if (lat->c64()) tuned_zchunk<float>(lat);
+      else tuned_zchunk<double>(lat);
+    }
+    int nflip = 0;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(lat->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
-    for (int s = 0; s < k && e == cudaSuccess; ++s) {
+    int64_t t = lat->step;
+    for (int s = 0; s < k && e == cudaSuccess;) {
       const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[0];
-      void* in = lat->psi();
-      void* out = lat->kinetic == QF_KIN_FDTD ? lat->tmp() : in;
-      e = kinetic_pass(lat, in, out, true, false, scale, nullptr);
+      if (pairs && s + 2 <= k && fuse_pair(lat, t, check_every, check_every)) {
+        e = fdtd_pair(lat, scale, tzc);
+        s += 2;
+        t += 2;
+      } else {
+        void* in = lat->psi();
+        void* out = lat->kinetic == QF_KIN_FDTD ? lat->tmp() : in;
+        e = kinetic_pass(lat, in, out, true, false, scale, nullptr);
+        s += 1;
+        t += 1;
+      }
       lat->pending_scale = false;
-      if (lat->kinetic == QF_KIN_FDTD) lat->live = 1 - lat->live;
+      if (lat->kinetic == QF_KIN_FDTD) {
+        lat->live = 1 - lat->live;
+        lat->clean = true;
+        ++nflip;
+      }
     }
     cudaError_t e2 = cudaStreamEndCapture(lat->st, &graph);
     if (e2 != cudaSuccess && graph) {
       cudaGraphDestroy(graph);
       graph = nullptr;
     }
+    const int64_t nlaunch = lat->launches - launches0;
     lat->live = live0;
     lat->xfwd_valid = xv0;
     lat->pending_scale = ps0;
+    lat->clean = clean0;
     lat->launches = launches0;
     if (e == cudaSuccess) e = e2;
+    cudaGraphExec_t exec = nullptr;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) return e;
-    lat->graphs.push_back({check_every, live0, exec});
+    lat->graphs.push_back({check_every, live0, lat->tblock, exec, nflip, nlaunch});
+    hit = &lat->graphs.back();
   }
-  cudaError_t e = cudaGraphLaunch(exec, lat->st);
+  cudaError_t e = cudaGraphLaunch(hit->exec, lat->st);
   if (e != cudaSuccess) return e;
-  lat->launches += (int64_t)k * (lat->kinetic == QF_KIN_FDTD ? 1 : kFftPasses - 1);
+  lat->launches += hit->launches;
+  *flips = hit->flips;
   return cudaSuccess;
 }
 
@@ -698,6 +833,13 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
     const double tau_t = lat->tau;
     const bool check = check_every > 0 && t % check_every == 0;
     const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[0];
+    if (done + 2 <= max_steps && fuse_pair(lat, t, check_every, snap_every)) {
+      const int tzc = tuned_tb_zchunk(lat);
+      QF_CUDA(lat, fdtd_pair(lat, scale, tzc));
+      QF_CUDA(lat, after_pair(lat, snap_every, lat->st));
+      done += 2;
+      continue;
+    }
     int nb = 0;
     void* in = lat->psi();
     void* out = fdtd ? lat->tmp() : in;
@@ -721,25 +863,22 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
       const bool capturable = lat->st != nullptr && lat->st != cudaStreamLegacy && lat->st != cudaStreamPerThread;
       if (lat->use_graphs && capturable && !lat->prof && k >= 2 && done + k <= max_steps && snaps_at_end &&
           fft_ready && lat->pending_scale) {
-        if (run_chunk_graph(lat, check_every) != cudaSuccess) {
+        int flips = 0;
+        if (run_chunk_graph(lat, check_every, &flips) != cudaSuccess) {
           cudaGetLastError();
           lat->use_graphs = false;
           drop_graphs(lat);
           continue;
         }
-        for (int s = 0; s < k; ++s) {
-          lat->tau += lat->dtau;
-          if (fdtd) lat->live = 1 - lat->live;
+        for (int s = 0; s < k; ++s) lat->tau += lat->dtau;
+        if (fdtd) {
+          lat->live ^= flips & 1;
+          lat->clean = true;
         }
         lat->step += k;
         lat->pending_scale = false;
         done += k;
-        if (snap_every > 0 && lat->step % snap_every == 0) {
-          lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
-          QF_CUDA(lat, cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(),
-                                       (size_t)lat->sites * (lat->c64() ? 8 : 16), cudaMemcpyDeviceToDevice, lat->st));
-          if (lat->snap_count < lat->d.n_snap) lat->snap_count++;
-        }
+        QF_CUDA(lat, take_snapshot(lat, snap_every, lat->st));
       }
     }
   }
@@ -918,6 +1057,7 @@ static qf_status prolong_t(qf_lattice* c, void* cfield, qf_lattice* f) {
   const double scale = 1.0 / ((double)nc * nc * nc);
   QF_CUDA(f, launch(f, K_CONVERT, [&] { return launch_pad_spectrum<R>(pc.data, nc, pf.data, scale, f->st); }));
   f->xfwd_valid = false;
+  f->clean = false;
   for (int ps : {kFftPassZInverse, 3, kFftPassXInverse})
     QF_CUDA(f, launch(f, K_FFT_Y_INV, [&] { return launch_fft_pass<R>(nf, ps, pf, pf.data, f->st, nullptr); }));
   QF_CUDA(f, cudaMemcpyAsync(f->psi(), pf.data, (size_t)f->sites * sizeof(cpx<R>), cudaMemcpyDeviceToDevice, f->st));
@@ -950,6 +1090,7 @@ extern "C" qf_status qf_get_info(qf_lattice* lat, qf_info* out) {
   out->n_snapshots = lat->snap_count;
   out->workspace_bytes = lat->L.total;
   out->launches = lat->launches;
+  out->temporal_block = lat->tblock;
   return QF_OK;
 }
 
@@ -1005,6 +1146,13 @@ extern "C" qf_status qf_use_graphs(qf_lattice* lat, int enable) {
   if (!lat) return QF_EINVAL;
   lat->use_graphs = enable != 0;
   if (!lat->use_graphs) drop_graphs(lat);
+  return QF_OK;
+}
+
+extern "C" qf_status qf_set_temporal_blocking(qf_lattice* lat, int k) {
+  if (!lat) return QF_EINVAL;
+  if (k != 1 && k != 2) return fail(lat, QF_EINVAL, "temporal blocking factor must be 1 or 2");
+  lat->tblock = k;
   return QF_OK;
 }
 

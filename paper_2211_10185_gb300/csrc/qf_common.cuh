@@ -99,6 +99,7 @@ struct StencilArgs {
   R kcoef;                // 1/(2 m a^2)
   R half_dtau;
   R dtau;
+  R kd;                   // dtau * kcoef
   const double* scale;
   double* partials;
   int write_psi;

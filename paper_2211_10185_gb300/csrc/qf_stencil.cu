@@ -11,7 +11,7 @@
 
 #include <mutex>
 
-#include "qf_stencil_tma.cuh"
+#include "qf_stencil_tb.cuh"
 
 namespace qf {
 
@@ -37,9 +37,25 @@ cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Tensor map of an N^3 complex field for the stencil's plane boxes (8-byte elements:
-// one complex FP32 or one FP64 component).
-bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64) {
+cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(stencil_tb_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)stencil_tb_smem());
+    cudaFuncSetAttribute(stencil_tb_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stencil_tb_smem());
+    attr = true;
+  }
+  const int n = g.n;
+  if (g.zc < 1) return cudaErrorInvalidValue;
+  dim3 grid((n + TB_X - 1) / TB_X, (n + TB_Y - 1) / TB_Y, (n + g.zc - 1) / g.zc);
+  if (g.v_real) stencil_tb_kernel<true><<<grid, TB_THREADS, stencil_tb_smem(), st>>>(g);
+  else stencil_tb_kernel<false><<<grid, TB_THREADS, stencil_tb_smem(), st>>>(g);
+  return cudaGetLastError();
+}
+
+// Tensor map of an N^3 complex field for plane boxes of box_w x box_h 8-byte elements
+// (one complex FP32 or one FP64 component).
+static bool encode_field_map(CUtensorMap* map, void* field, int n, bool c64, unsigned box_w, unsigned box_h) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {
@@ -54,13 +70,21 @@ bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64) {
   const cuuint64_t w = c64 ? (cuuint64_t)n : 2 * (cuuint64_t)n;
   const cuuint64_t dims[3] = {w, (cuuint64_t)n, (cuuint64_t)n};
   const cuuint64_t strides[2] = {w * 8, w * 8 * (cuuint64_t)n};
-  const cuuint32_t box[3] = {(cuuint32_t)(c64 ? TmaTile<float>::W : TmaTile<double>::W), (cuuint32_t)(TS_Y + 2), 1};
+  const cuuint32_t box[3] = {box_w, box_h, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = encode(map, c64 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, field,
                             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
+
+// boxes of the single-step kernel: the tile plus a one-site halo (x rounded to 16 bytes)
+bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64) {
+  return encode_field_map(map, field, n, c64, c64 ? TmaTile<float>::W : TmaTile<double>::W, TS_Y + 2);
+}
+
+// boxes of the two-step kernel (complex FP32): the tile plus a two-site halo
+bool encode_tb_map(CUtensorMap* map, void* field, int n) { return encode_field_map(map, field, n, true, TB_W0, TB_H0); }
 
 // Self-test of the bounded waits: an mbarrier that expects bytes nobody sends never
 // completes, so every thread's bounded wait runs out and the block reports it.

@@ -84,6 +84,57 @@ __device__ __forceinline__ void tma_plane(const CUtensorMap* map, unsigned long 
       : "memory");
 }
 
+// ---- the per-site FDTD update, shared by every kernel that computes a site ------------
+// Each operation is rounded explicitly (no contraction left to the compiler), so the
+// single-step kernel and the temporally blocked kernel produce the same bits for a site.
+template <typename R> __device__ __forceinline__ R add_rn(R a, R b);
+template <typename R> __device__ __forceinline__ R mul_rn(R a, R b);
+template <typename R> __device__ __forceinline__ R fma_rn(R a, R b, R c);
+template <typename R> __device__ __forceinline__ R rcp_rn(R a);
+template <> __device__ __forceinline__ float add_rn<float>(float a, float b) { return __fadd_rn(a, b); }
+template <> __device__ __forceinline__ double add_rn<double>(double a, double b) { return __dadd_rn(a, b); }
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <> __device__ __forceinline__ float fma_rn<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fma_rn<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <> __device__ __forceinline__ float rcp_rn<float>(float a) { return __frcp_rn(a); }
+template <> __device__ __forceinline__ double rcp_rn<double>(double a) { return __drcp_rn(a); }
+
+// sum of the six neighbours in the fixed order ((x- + x+) + (y- + y+)) + (z- + z+)
+template <typename R>
+__device__ __forceinline__ cpx<R> six_sum(cpx<R> xm, cpx<R> xp, cpx<R> ym, cpx<R> yp, cpx<R> zm, cpx<R> zp) {
+  return mk<R>(add_rn<R>(add_rn<R>(add_rn<R>(xm.x, xp.x), add_rn<R>(ym.x, yp.x)), add_rn<R>(zm.x, zp.x)),
+               add_rn<R>(add_rn<R>(add_rn<R>(xm.y, xp.y), add_rn<R>(ym.y, yp.y)), add_rn<R>(zm.y, zp.y)));
+}
+
+// lap = sum of neighbours - 6 psi, so that H_K^(0) psi = -kcoef * lap (Eq. HK0)
+template <typename R>
+__device__ __forceinline__ cpx<R> lap_of(cpx<R> c, cpx<R> nbs) {
+  return mk<R>(fma_rn<R>(R(-6), c.x, nbs.x), fma_rn<R>(R(-6), c.y, nbs.y));
+}
+
+// psi' = s (coef_A psi - coef_B dtau H_K psi) with d = 1 + dtau V / 2:
+// psi' = s ((2 - d) psi + kd lap) conj(d) / |d|^2, kd = dtau * kcoef.  For real V,
+// conj(d)/|d|^2 = 1/d.
+template <typename R>
+__device__ __forceinline__ cpx<R> fdtd_update(cpx<R> c, cpx<R> lap, cpx<R> v, bool v_real, R half_dtau, R kd, R sc) {
+  const R dx = fma_rn<R>(half_dtau, v.x, R(1));
+  const R tx = add_rn<R>(R(2), -dx);
+  if (v_real) {
+    const R inv = mul_rn<R>(sc, rcp_rn<R>(dx));
+    return mk<R>(mul_rn<R>(fma_rn<R>(kd, lap.x, mul_rn<R>(tx, c.x)), inv),
+                 mul_rn<R>(fma_rn<R>(kd, lap.y, mul_rn<R>(tx, c.y)), inv));
+  }
+  const R dy = mul_rn<R>(half_dtau, v.y);
+  // (2 - d) psi = (tx - i dy) psi
+  const R ax = fma_rn<R>(tx, c.x, mul_rn<R>(dy, c.y));
+  const R ay = fma_rn<R>(tx, c.y, -mul_rn<R>(dy, c.x));
+  const R nx = fma_rn<R>(kd, lap.x, ax), ny = fma_rn<R>(kd, lap.y, ay);
+  const R inv = mul_rn<R>(sc, rcp_rn<R>(fma_rn<R>(dx, dx, mul_rn<R>(dy, dy))));
+  return mk<R>(mul_rn<R>(fma_rn<R>(nx, dx, mul_rn<R>(ny, dy)), inv),
+               mul_rn<R>(fma_rn<R>(ny, dx, -mul_rn<R>(nx, dy)), inv));
+}
+
 template <typename R>
 __device__ __forceinline__ cpx<R> tile_at(const unsigned long long* buf, int ix, int iy, int x0, int y0) {
   const int row = iy - y0 + 1;
@@ -99,7 +150,7 @@ __device__ __forceinline__ cpx<R> tile_at(const unsigned long long* buf, int ix,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), 3) stencil_tma_kernel(const __grid_constant__ StencilTmaGroup<R> g) {
+__global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), sizeof(R) == 4 ? 3 : 2) stencil_tma_kernel(const __grid_constant__ StencilTmaGroup<R> g) {
   extern __shared__ __align__(128) unsigned long long planes_dyn[];
   unsigned long long(*planes)[TmaTile<R>::STRIDE_WORDS] =
       reinterpret_cast<unsigned long long(*)[TmaTile<R>::STRIDE_WORDS]>(planes_dyn);
@@ -197,16 +248,10 @@ __global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), 3) stencil_tma_kernel(c
           zm = (iz - 1 == 0) ? mk<R>(R(0), R(0)) : tile_at<R>(bm, ix, iy, x0, y0);
           zp = (iz + 1 == n) ? mk<R>(R(0), R(0)) : tile_at<R>(bp, ix, iy, x0, y0);
         }
-        const cpx<R> nbs = ((xm + xp) + (ym + yp)) + (zm + zp);
-        const cpx<R> h = mk<R>(-a.kcoef * (nbs.x - R(6) * c.x), -a.kcoef * (nbs.y - R(6) * c.y));
+        const cpx<R> lap = lap_of<R>(c, six_sum<R>(xm, xp, ym, yp, zm, zp));
         const cpx<R> vv = vcur[k];
-        if (a.reduce) cs.add(c, h, vv);
-        if (a.write_psi) {
-          const cpx<R> d = mk<R>(R(1) + a.half_dtau * vv.x, a.half_dtau * vv.y);
-          const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), c) - cscale<R>(h, a.dtau);
-          const R inv = sc / (d.x * d.x + d.y * d.y);
-          a.out[site] = cscale<R>(cmulc<R>(num, d), inv);
-        }
+        if (a.reduce) cs.add(c, mk<R>(mul_rn<R>(-a.kcoef, lap.x), mul_rn<R>(-a.kcoef, lap.y)), vv);
+        if (a.write_psi) a.out[site] = fdtd_update<R>(c, lap, vv, a.v_real != 0, a.half_dtau, a.kd, sc);
       } else if (a.write_psi) {
         a.out[site] = mk<R>(R(0), R(0));
       }
