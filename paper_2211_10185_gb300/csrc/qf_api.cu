@@ -555,7 +555,7 @@ static qf_status check_device_error(qf_lattice* lat) {
 }
 
 // ---- two FDTD steps per pass (complex FP32) ----------------------------------------------
-static void tb_args(qf_lattice* lat, const double* scale, int zc, StencilTbArgs& g) {
+static void tb_args(qf_lattice* lat, const double* scale, int nzb, StencilTbArgs& g) {
   const double a = lat->d.a, m = lat->mass, dt = lat->dtau;
   g.map = lat->tbmap[lat->live];
   g.out = reinterpret_cast<cpx<float>*>(lat->tmp());
@@ -566,28 +566,42 @@ static void tb_args(qf_lattice* lat, const double* scale, int zc, StencilTbArgs&
   g.kd = (float)(dt / (2.0 * m * a * a));
   g.scale = scale;
   g.n = lat->d.n;
-  g.zc = zc;
+  g.nzb = nzb;
   g.err = &lat->sc()->err[0];
 }
 
-static std::vector<std::pair<long long, int>> g_tuned_tb;  // key n -> zc
+static std::vector<std::pair<long long, int>> g_tuned_tb;  // key n -> z-chunks per tile
 
-// z-chunk of the two-step kernel per N, timed on first use (psi -> scratch; the scratch
-// field is overwritten by the real pass afterwards).  Must not run during a capture.
+// Number of z-chunks per column tile of the two-step kernel, per N, timed on first use
+// (psi -> scratch; the scratch field is overwritten by the real pass afterwards) among
+// chunks of about 64, 32 and 16 planes and the counts that make the grid about 1-4 full
+// waves of two resident blocks per SM.  Must not run during a capture.
 static int tuned_tb_zchunk(qf_lattice* lat) {
-  const long long key = lat->d.n;
+  const int n = lat->d.n;
+  const long long key = n;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     for (auto& kv : g_tuned_tb)
       if (kv.first == key) return kv.second;
   }
-  int best = kTbZChunks[1];
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = ((n + TB_X - 1) / TB_X) * ((n + TB_Y - 1) / TB_Y);
+  std::vector<int> cand = {(n + 63) / 64, (n + 31) / 32, (n + 15) / 16};
+  for (int w = 1; w <= 4; ++w) {
+    cand.push_back(w * 2 * sms / tiles);
+    cand.push_back((w * 2 * sms + tiles - 1) / tiles);
+  }
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  int best = (n + 31) / 32;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return best;
-  for (int zc : kTbZChunks) {
+  for (int nzb : cand) {
+    if (nzb < 1 || nzb > n) continue;
     StencilTbArgs g;
-    tb_args(lat, &lat->sc()->scale[0], zc, g);
+    tb_args(lat, &lat->sc()->scale[0], nzb, g);
     float ms = 0, tot = 0;
     bool ok = launch_stencil_tb(g, lat->st) == cudaSuccess;  // warm-up
     for (int rep = 0; rep < 3 && ok; ++rep) {
@@ -599,7 +613,7 @@ static int tuned_tb_zchunk(qf_lattice* lat) {
     lat->launches += 4;
     if (ok && tot < best_ms) {
       best_ms = tot;
-      best = zc;
+      best = nzb;
     }
   }
   cudaEventDestroy(e0);
@@ -619,9 +633,9 @@ static bool fuse_pair(const qf_lattice* lat, int64_t t, int check_every, int sna
 }
 
 // psi_{t+2} into the scratch field; `scale` renormalises the first of the two steps.
-static cudaError_t fdtd_pair(qf_lattice* lat, const double* scale, int zc) {
+static cudaError_t fdtd_pair(qf_lattice* lat, const double* scale, int nzb) {
   StencilTbArgs g;
-  tb_args(lat, scale, zc, g);
+  tb_args(lat, scale, nzb, g);
   return launch(lat, K_STENCIL_2STEP, [&] { return launch_stencil_tb(g, lat->st); });
 }
 

@@ -46,8 +46,8 @@ cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st) {
     attr = true;
   }
   const int n = g.n;
-  if (g.zc < 1) return cudaErrorInvalidValue;
-  dim3 grid((n + TB_X - 1) / TB_X, (n + TB_Y - 1) / TB_Y, (n + g.zc - 1) / g.zc);
+  if (g.nzb < 1 || g.nzb > n) return cudaErrorInvalidValue;
+  dim3 grid((n + TB_X - 1) / TB_X, (n + TB_Y - 1) / TB_Y, g.nzb);
   if (g.v_real) stencil_tb_kernel<true><<<grid, TB_THREADS, stencil_tb_smem(), st>>>(g);
   else stencil_tb_kernel<false><<<grid, TB_THREADS, stencil_tb_smem(), st>>>(g);
   return cudaGetLastError();

@@ -3,7 +3,8 @@
 //
 // Two consecutive steps read psi_t and V and write psi_{t+2}; the intermediate psi_{t+1}
 // lives only in shared memory.  A block owns a 32 x 32 column tile of the output and
-// marches through a chunk of z.  Three levels are in flight at once:
+// marches through a chunk of z (chunk sizes differ by at most one plane, so the number of
+// chunks can be chosen to fill whole waves of resident blocks).  Three levels are in flight at once:
 //   level 0  psi_t on the tile plus a halo of 2 (36 x 36), streamed plane by plane with
 //            cp.async.bulk.tensor into a ring of six buffers (each with an mbarrier);
 //   level 1  psi_{t+1} on the tile plus a halo of 1 (34 x 34), computed one plane behind
@@ -35,8 +36,6 @@ constexpr int TB_L1_SITES = TB_W1 * TB_H1;           // 1156
 constexpr int TB_L1_STRIDE = (TB_L1_SITES + 15) / 16 * 16;
 constexpr int TB_L1_PER_THREAD = (TB_L1_SITES + TB_THREADS - 1) / TB_THREADS;  // 5
 constexpr unsigned TB_L0_BYTES = TB_L0_WORDS * 8u;
-// z-chunks the autotuner chooses from
-constexpr int kTbZChunks[3] = {16, 32, 64};
 
 struct alignas(64) StencilTbArgs {
   CUtensorMap map;        // input field psi_t, box TB_W0 x TB_H0 x 1 of 8-byte elements
@@ -47,7 +46,7 @@ struct alignas(64) StencilTbArgs {
   float kd;               // dtau / (2 m a^2)
   const double* scale;    // renormalisation applied in the first of the two steps
   int n;
-  int zc;                 // output planes per block
+  int nzb;                // z-chunks per column tile: chunk b holds planes [b n/nzb, (b+1) n/nzb)
   int* err;               // set to 1 when a bounded wait ran out
 };
 
@@ -80,7 +79,7 @@ __global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_
   const long long plane_sites = (long long)n * n;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int x0 = blockIdx.x * TB_X, y0 = blockIdx.y * TB_Y;
-  const int z0 = blockIdx.z * g.zc, z1 = min(n, z0 + g.zc);
+  const int z0 = (int)((long long)blockIdx.z * n / g.nzb), z1 = (int)((long long)(blockIdx.z + 1) * n / g.nzb);
   const int pbase = z0 - 2, last0 = z1 + 1;  // level-0 planes z0-2 .. z1+1
   const float hd = g.half_dtau, kd = g.kd;
   const float sc1 = (float)*g.scale;
@@ -176,18 +175,19 @@ __global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_
       const cpx<float>* ac = l0 + ((p - pbase) % TB_D0) * TB_L0_WORDS;
       const cpx<float>* ap = l0 + ((p + 1 - pbase) % TB_D0) * TB_L0_WORDS;
       cpx<float>* w = l1 + ((p - (z0 - 1)) % TB_D1) * TB_L1_STRIDE;
+      // branch-free: every position is computed (halo and wall positions read zeros or
+      // finite values) and the Dirichlet/outside ones are replaced by 0; only the last
+      // round of the flat index is partial
 #pragma unroll
       for (int q = 0; q < TB_L1_PER_THREAD; ++q) {
-        if (!has1[q]) continue;
-        cpx<float> r = mk<float>(0.f, 0.f);
-        if (zin && in1[q]) {
-          const int o = o0[q];
-          const cpx<float> c = ac[o];
-          const cpx<float> lap =
-              lap_of<float>(c, six_sum<float>(ac[o - 1], ac[o + 1], ac[o - TB_W0], ac[o + TB_W0], am[o], ap[o]));
-          r = fdtd_update<float>(c, lap, v1c[q], VREAL, hd, kd, sc1);
-        }
-        w[o1[q]] = r;
+        if (q == TB_L1_PER_THREAD - 1 && !has1[q]) break;
+        const int o = o0[q];
+        const cpx<float> c = ac[o];
+        const cpx<float> lap =
+            lap_of<float>(c, six_sum<float>(ac[o - 1], ac[o + 1], ac[o - TB_W0], ac[o + TB_W0], am[o], ap[o]));
+        const cpx<float> u = fdtd_update<float>(c, lap, v1c[q], VREAL, hd, kd, sc1);
+        const bool live = zin && in1[q];
+        w[o1[q]] = mk<float>(live ? u.x : 0.f, live ? u.y : 0.f);
       }
     }
     // level 2: psi_{t+2} on plane j-3 (the tile), stored
@@ -202,17 +202,15 @@ __global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_
       cpx<float> col[TB_ROWS + 2];
 #pragma unroll
       for (int k = 0; k < TB_ROWS + 2; ++k) col[k] = bc[base + k * TB_W1];
+      cpx<float>* dst = g.out + (p * (long long)n + oy) * n + ox;
 #pragma unroll
       for (int k = 0; k < TB_ROWS; ++k) {
-        if (!st2[k]) continue;
         const int o = base + (k + 1) * TB_W1;
-        cpx<float> r = mk<float>(0.f, 0.f);
-        if (zin && in2[k]) {
-          const cpx<float> c = col[k + 1];
-          const cpx<float> lap = lap_of<float>(c, six_sum<float>(bc[o - 1], bc[o + 1], col[k], col[k + 2], bm[o], bp[o]));
-          r = fdtd_update<float>(c, lap, v2c[k], VREAL, hd, kd, 1.0f);
-        }
-        g.out[(p * (long long)n + oy + k) * n + ox] = r;
+        const cpx<float> c = col[k + 1];
+        const cpx<float> lap = lap_of<float>(c, six_sum<float>(bc[o - 1], bc[o + 1], col[k], col[k + 2], bm[o], bp[o]));
+        const cpx<float> u = fdtd_update<float>(c, lap, v2c[k], VREAL, hd, kd, 1.0f);
+        const bool live = zin && in2[k];
+        if (st2[k]) dst[(long long)k * n] = mk<float>(live ? u.x : 0.f, live ? u.y : 0.f);
       }
     }
   }
