@@ -36,7 +36,14 @@ from paper_2211_10185_gb300 import inputs as I  # noqa: E402
 CHUNK = 64
 METRIC = "site-updates/s (fused FFT step, N=256)"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic_fft_step_n256.json")
+# per-launch DRAM traffic of one ncu capture per kernel family, with the digest of the
+# sources that family compiles from
+TRAFFIC_FILES = {
+    "fft": (os.path.join(ROOT, "profiles", "ncu_traffic_fft_step_n256.json"),
+            ("qf_fft_impl.cuh", "qf_common.cuh")),
+    "stencil": (os.path.join(ROOT, "profiles", "ncu_traffic_fdtd_step_n256.json"),
+                ("qf_stencil.cu", "qf_stencil_tma.cuh", "qf_stencil_tb.cuh", "qf_common.cuh")),
+}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -231,20 +238,21 @@ def bytes_per_site(kernel, prec, v_real):
     return table.get(kernel)
 
 
-def source_digest():
+def source_digest(files):
     h = hashlib.sha256()
-    for f in ("qf_fft_impl.cuh", "qf_common.cuh", "qf_stencil.cu", "qf_stencil_tma.cuh", "qf_stencil_tb.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2211_10185_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def load_traffic(kernel, n, prec):
+    path, files = TRAFFIC_FILES["stencil" if kernel.startswith("stencil") else "fft"]
     try:
-        rec = json.load(open(TRAFFIC_FILE))
+        rec = json.load(open(path))
     except (OSError, ValueError):
         return None, "no committed ncu traffic summary"
-    if rec.get("source_digest") != source_digest():
+    if rec.get("source_digest") != source_digest(files):
         return None, "kernels changed since the ncu capture"
     k = rec.get("kernels", {}).get(kernel)
     if not k or rec.get("n") != n or rec.get("precision") != prec:
