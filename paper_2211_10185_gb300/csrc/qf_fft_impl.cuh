@@ -276,7 +276,13 @@ __device__ __forceinline__ void run_stages(cpx<R> (&v)[plan_ept(N)], int g, cons
 template <typename R>
 __device__ __forceinline__ R kin_mult(int kinetic, R sxy, R sz, R tcoef, R am2) {
   R s = sxy + sz;
-  if (kinetic == KIN_FFT_REL) return sqrt(s + am2) * tcoef;
+  if (kinetic == KIN_FFT_REL) {
+    // sqrt(u) = u / sqrt(u) for u > 0: FP32 through the hardware reciprocal square root
+    // (a few ulp, no branch; u = 0 only if (am)^2 underflows), FP64 correctly rounded
+    const R u = s + am2;
+    if constexpr (sizeof(R) == 4) return (u > 0.f ? u * rsqrtf(u) : 0.f) * tcoef;
+    else return sqrt(u) * tcoef;
+  }
   return s * tcoef;
 }
 
@@ -481,9 +487,18 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
 // of the same N advanced by one launch (blockIdx.y selects the lattice; the arguments of
 // all members travel in the kernel's parameter space).  Every lattice runs exactly the
 // blocks it would run alone.
+//
+// The x passes that read the inverse-y output walk the lines from the last to the first:
+// the y pass wrote its last z-planes most recently, so they are still in L2 when the
+// reversed pass starts, and the next step's y pass (first to last) starts where this one
+// ended.
+template <int OP>
+__device__ __forceinline__ int x_block(int b) {
+  return (OP == OP_FWD) ? b : (int)gridDim.x - 1 - b;
+}
 template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_kernel(FftPassArgs<R> a) {
-  fft_x_body<R, N, OP, VREAL, NEXT>(a, blockIdx.x);
+  fft_x_body<R, N, OP, VREAL, NEXT>(a, x_block<OP>(blockIdx.x));
 }
 template <typename R, int N, int AXIS, int OP>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArgs<R> a) {
@@ -491,7 +506,7 @@ __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArg
 }
 template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_group_kernel(const __grid_constant__ FftGroup<R> g) {
-  fft_x_body<R, N, OP, VREAL, NEXT>(g.a[blockIdx.y], blockIdx.x);
+  fft_x_body<R, N, OP, VREAL, NEXT>(g.a[blockIdx.y], x_block<OP>(blockIdx.x));
 }
 template <typename R, int N, int AXIS, int OP>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_group_kernel(const __grid_constant__ FftGroup<R> g) {
