@@ -319,7 +319,8 @@ def cufft_comparator(w, v, psi0, steps=10):
 # ---------------------------------------------------------------------------------------
 def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget=170e9, n_cmp=8):
     """Serves a seeded sample of the mixed workload in real time; then, on a subsample of
-    small requests, compares the batched FP32 form with serial per-lattice FP64 solves."""
+    small requests, compares the batched FP32 form with serial per-lattice FP64 solves,
+    and on FFT-term requests with N >= 64, cold solves with warm-started ones."""
     import torch
 
     from paper_2211_10185_gb300 import qfdtd as Q
@@ -353,6 +354,27 @@ def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget
         "requests": len(sub), "fp32_batched_solves_per_s": len(sub) / t32, "fp64_alone_solves_per_s": len(sub) / t64,
         "max_rel_energy_err_fp32_vs_fp64": max(errs) if errs else None,
         "same_status": all(r32[i].status == r64[i].status for i in r64)}
+    # warm start across N: FFT-term requests with N >= 64, all arriving at once, solved cold
+    # and warm (first on the N/2 lattice of the same box, then prolonged)
+    sub = [r for r in reqs if r.kinetic != 0 and r.n >= 64][:n_cmp * 2]
+    runs = {}
+    for warm in (False, True):
+        batch = [dataclasses_replace(r, warm_start=warm) for r in sub]
+        t0 = time.perf_counter()
+        res = Server(int(budget), chunk=CHUNK).run(batch, realtime=False)
+        torch.cuda.synchronize()
+        runs[warm] = (time.perf_counter() - t0, {r.rid: r for r in res})
+    (tc, cold), (tw, warm) = runs[False], runs[True]
+    both = [i for i in cold if cold[i].status == Q.QF_OK and warm[i].status == Q.QF_OK]
+    out["warm_start"] = {
+        "requests": len(sub), "cold_solves_per_s": len(sub) / tc, "warm_solves_per_s": len(sub) / tw,
+        "cold_mean_steps": statistics.mean(r.steps for r in cold.values()) if cold else None,
+        "warm_mean_fine_steps": statistics.mean(r.steps for r in warm.values()) if warm else None,
+        "warm_mean_coarse_steps": statistics.mean(r.coarse_steps for r in warm.values()) if warm else None,
+        "converged_cold": sum(r.status == Q.QF_OK for r in cold.values()),
+        "converged_warm": sum(r.status == Q.QF_OK for r in warm.values()),
+        "max_rel_energy_diff_converged": (max(abs(warm[i].energy - cold[i].energy) / abs(cold[i].energy)
+                                              for i in both) if both else None)}
     return out
 
 
