@@ -102,6 +102,8 @@ typedef struct {
   size_t workspace_bytes;
   int64_t launches;   /* kernels this handle has launched so far                     */
   int temporal_block; /* FDTD steps fused per pass (qf_set_temporal_blocking)         */
+  int fft_passes;     /* HBM passes of a steady-state FFT step: 2 (N = 256 complex
+                         FP32, qf_use_two_pass_fft) or 4; 0 for the FDTD term         */
 } qf_info;
 
 typedef struct {
@@ -186,6 +188,15 @@ qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double* p, double*
  * capture fails, the handle continues with ordinary launches.
  * Changing the potential or the kinetic term drops the captured graphs. */
 qf_status qf_use_graphs(qf_lattice* lat, int enable);
+
+/* Form of the FFT step (no counterpart in the paper; the paper's FFTW transforms are
+ * replaced by GPU passes).  enable != 0, the default: complex-FP32 lattices with N = 256
+ * run a steady-state step in two passes over HBM (the y transform split 16 x 16
+ * four-step fashion between the two passes; the scratch field holds a blocked layout),
+ * other lattices in four.  enable == 0 selects the four-pass form for N = 256 too.  Both
+ * compute the same step to rounding; switching discards the scratch field's contents and
+ * any captured graphs. */
+qf_status qf_use_two_pass_fft(qf_lattice* lat, int enable);
 
 /* Temporal blocking of the FDTD step (the step of Sec. 2 with the Eq. HK0 term; no
  * counterpart in the paper).  k = 2, the default: on complex-FP32 lattices qf_step_n

@@ -21,6 +21,9 @@
 namespace qf {
 bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64);
 bool encode_tb_map(CUtensorMap* map, void* field, int n);
+bool fft2_supported(int n);
+int fft2_final_blocks();
+cudaError_t launch_fft2_group_pass(int pass, const FftGroup<float>& g, cudaStream_t st);
 cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st);
 cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st);
 template <typename R>
@@ -42,12 +45,14 @@ static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Kernel kinds for the per-kernel timing of qf_profile.
 enum KernelKind {
   K_FFT_X_FWD = 0, K_FFT_Y_FWD, K_FFT_Z_MID, K_FFT_Y_INV, K_FFT_X_INV_UPDATE, K_STENCIL, K_FINISH, K_GS_DOTS,
-  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_FFT_X_INV_SUMS, K_STENCIL_SUMS, K_STENCIL_2STEP, K_NUM_KINDS
+  K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_FFT_X_INV_SUMS, K_STENCIL_SUMS, K_STENCIL_2STEP, K_FFT2_XY_FWD,
+  K_FFT2_YZ_MID, K_FFT2_XY_INV_UPDATE, K_FFT2_XY_INV_SUMS, K_NUM_KINDS
 };
 static const char* kKindNames[K_NUM_KINDS] = {"fft_x_fwd", "fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
                                                "fft_x_inv_update", "stencil_step", "finish_sums", "gs_dots",
                                                "gs_axpy", "scale_copy", "parity", "convert", "fft_x_inv_sums",
-                                               "stencil_sums", "stencil_2step"};
+                                               "stencil_sums", "stencil_2step", "fft2_xy_fwd", "fft2_yz_mid_T",
+                                               "fft2_xy_inv_update", "fft2_xy_inv_sums"};
 static const int kEventPool = 4096;
 
 struct Layout {
@@ -139,6 +144,9 @@ struct qf_lattice {
   // the Dirichlet planes (it is after any FDTD step), which the two-step kernel needs
   int tblock = 2;
   bool clean = false;
+  // N = 256 complex-FP32 FFT steps in two passes over HBM (qf_fft2.cuh) instead of four;
+  // the scratch field then holds the four-step layout, so switching drops xfwd_valid
+  bool two_pass = true;
   std::string err;
   // launch accounting and optional CUDA-event timing per kernel kind
   int64_t launches = 0;
@@ -162,6 +170,11 @@ struct qf_lattice {
   double* stage() const { return reinterpret_cast<double*>(ws + L.stage); }
   bool c64() const { return d.prec == QF_PREC_C64; }
 };
+
+// The FFT step of this lattice runs the two-pass kernels.
+static bool uses_fft2(const qf_lattice* lat) {
+  return lat->two_pass && lat->c64() && lat->kinetic != QF_KIN_FDTD && fft2_supported(lat->d.n);
+}
 
 static void drop_graphs(qf_lattice* lat) {
   for (auto& g : lat->graphs) cudaGraphExecDestroy(g.exec);
@@ -663,6 +676,24 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
   const bool live = write && in == lat->psi();
   const int first = (live && lat->xfwd_valid) ? 1 : 0;
   lat->xfwd_valid = false;
+  if (uses_fft2(lat)) {
+    // two-pass step: A (natural -> scratch; skipped when the previous step emitted it),
+    // B, C; every launch a group of one
+    FftGroup<float> g;
+    g.count = 1;
+    g.a[0] = fft_args<float>(lat, in, write, reduce, scale);
+    g.a[0].emit_next = live ? 1 : 0;
+    if (nblocks) *nblocks = fft2_final_blocks();
+    for (int ps = first; ps < 3; ++ps) {
+      g.a[0].src = ps == 0 ? reinterpret_cast<const cpx<float>*>(in) : nullptr;
+      const int kind = ps == 0 ? K_FFT2_XY_FWD : ps == 1 ? K_FFT2_YZ_MID : write ? K_FFT2_XY_INV_UPDATE
+                                                                                  : K_FFT2_XY_INV_SUMS;
+      cudaError_t e = launch(lat, kind, [&] { return launch_fft2_group_pass(ps, g, lat->st); });
+      if (e != cudaSuccess) return e;
+    }
+    lat->xfwd_valid = live;
+    return cudaSuccess;
+  }
   if (lat->c64()) {
     FftPassArgs<float> p = fft_args<float>(lat, in, write, reduce, scale);
     p.emit_next = live ? 1 : 0;
@@ -1105,6 +1136,7 @@ extern "C" qf_status qf_get_info(qf_lattice* lat, qf_info* out) {
   out->workspace_bytes = lat->L.total;
   out->launches = lat->launches;
   out->temporal_block = lat->tblock;
+  out->fft_passes = lat->kinetic == QF_KIN_FDTD ? 0 : uses_fft2(lat) ? 2 : 4;
   return QF_OK;
 }
 
@@ -1160,6 +1192,16 @@ extern "C" qf_status qf_use_graphs(qf_lattice* lat, int enable) {
   if (!lat) return QF_EINVAL;
   lat->use_graphs = enable != 0;
   if (!lat->use_graphs) drop_graphs(lat);
+  return QF_OK;
+}
+
+extern "C" qf_status qf_use_two_pass_fft(qf_lattice* lat, int enable) {
+  if (!lat) return QF_EINVAL;
+  if (lat->two_pass != (enable != 0)) {
+    lat->two_pass = enable != 0;
+    lat->xfwd_valid = false;  // the scratch layouts of the two step forms differ
+    drop_graphs(lat);
+  }
   return QF_OK;
 }
 
@@ -1312,8 +1354,9 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
       const bool fdtd = L->kinetic == QF_KIN_FDTD;
       if (!L->c64()) {
         void* in = L->psi();
+        const int64_t l0 = L->launches;
         QF_BCUDA(b, kinetic_pass(L, in, fdtd ? L->tmp() : in, true, chk[k], sk, &nblk[k]));
-        b->launches += fdtd ? 1 : kFftPasses;
+        b->launches += L->launches - l0;
         done[k] = 1;
         continue;
       }
@@ -1322,7 +1365,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
         if (done[q]) continue;
         qf_lattice* M = b->m[run[q]].lat;
         if (!M->c64() || M->d.n != L->d.n || (M->kinetic == QF_KIN_FDTD) != fdtd) continue;
-        if (!fdtd && (M->v_real != L->v_real || chk[q] != chk[k])) continue;
+        if (!fdtd && (M->v_real != L->v_real || chk[q] != chk[k] || uses_fft2(M) != uses_fft2(L))) continue;
         g.push_back(q);
         done[q] = 1;
       }
@@ -1345,6 +1388,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
           QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
           b->launches += 1;
         } else {
+          const bool two = uses_fft2(L);
           FftGroup<float> fg, f0;
           fg.count = cnt;
           f0.count = 0;
@@ -1354,7 +1398,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
             const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
             fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
             fg.a[j].emit_next = 1;
-            nblk[q] = fft_final_blocks<float>(n);
+            nblk[q] = two ? fft2_final_blocks() : fft_final_blocks<float>(n);
             if (!M->xfwd_valid) {
               f0.a[f0.count] = fg.a[j];
               f0.a[f0.count].src = fg.a[j].psi;
@@ -1363,12 +1407,12 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
             M->xfwd_valid = true;
           }
           if (f0.count > 0) {
-            QF_BCUDA(b, launch_fft_group_pass<float>(n, 0, f0, st));
+            QF_BCUDA(b, two ? launch_fft2_group_pass(0, f0, st) : launch_fft_group_pass<float>(n, 0, f0, st));
             b->launches += 1;
           }
-          for (int ps = 1; ps < kFftPasses; ++ps) {
-            for (int j = 0; j < cnt; ++j) fg.a[j].src = nullptr;
-            QF_BCUDA(b, launch_fft_group_pass<float>(n, ps, fg, st));
+          for (int j = 0; j < cnt; ++j) fg.a[j].src = nullptr;
+          for (int ps = 1; ps < (two ? 3 : kFftPasses); ++ps) {
+            QF_BCUDA(b, two ? launch_fft2_group_pass(ps, fg, st) : launch_fft_group_pass<float>(n, ps, fg, st));
             b->launches += 1;
           }
         }

@@ -1,0 +1,327 @@
+// Two-pass imaginary-time FFT step for N = 256 complex-FP32 lattices (Eqs. HK1-HK3 and
+// the update of Sec. 2), sm_103a.
+//
+// The 3D transform is reorganised so that a steady-state step reads and writes HBM in two
+// passes instead of four.  The y transform of length 256 is split four-step fashion,
+// y = y_lo + 16 y_hi and k_y = k_lo + 16 k_hi:
+//   Y(k_lo + 16 k_hi) = sum_{y_lo} w16^{y_lo k_hi} [ w256^{y_lo k_lo}
+//                        sum_{y_hi} w16^{y_hi k_lo} f(y_lo + 16 y_hi) ],
+// and each half is attached to a pass that already holds the needed elements:
+//   pass A  x forward + the inner 16-point DFTs over y_hi (+ twiddle), from a field in
+//           natural order, into the scratch field S;
+//   pass B  the outer 16-point DFTs over y_lo, z forward, T(k), z inverse, the outer
+//           inverse DFTs, S in place;
+//   pass C  the inner inverse DFTs (+ conjugate twiddle), x inverse, the update of psi
+//           (and the FP64 check sums), then pass A on psi_{t+1} for the next step.
+// Steady state: B + C = 16 + (8 + 8 + 4 + 8 + 8) B per site (real V) instead of 84.
+//
+// S layout (the scratch field, 2^24 elements): [kx_hi 128][k_lo 16][z 256][y_lo 16][kx_lo 2]
+// with kx = 2 kx_hi + kx_lo.  A pass-B block owns one (kx_hi, k_lo): 8192 contiguous
+// elements.  A pass-A/C block owns YL consecutive y_lo of one z: 16 YL lines
+// y = y_lo + 16 y_hi of the natural field, and in S 16 YL bytes per (kx_hi, k_lo).
+//
+// Shared-memory layouts are padded for conflict-free access: the A/C line tile has pitch
+// 280 (line YL y_hi + s, one pad element per 16), the B tile pitch 33 per z row plus one
+// element of skew per 16 rows.
+#pragma once
+#include "qf_fft_impl.cuh"
+
+namespace qf {
+
+constexpr int F2_N = 256;
+constexpr int F2_THREADS = 512;                       // pass B block
+constexpr int F2_BLOCKS = 2048;                       // pass B blocks per lattice
+constexpr int F2_PL = 280;                            // A/C tile line pitch
+constexpr int F2_BP = 33;                             // B tile row pitch
+constexpr int F2_TW = plan_tw_size(F2_N);             // 255 per-stage twiddles
+constexpr int F2_TW1 = plan_tw_off(F2_N, 1);          // stage-1 block: w256^{k r}
+constexpr int F2_TWB = (F2_TW * 8 + 15) / 16 * 16;    // twiddle bytes in shared memory
+constexpr int F2_BTILE = F2_N * F2_BP + F2_N / 16;    // B tile elements (with the row skew)
+constexpr size_t F2_SMEM_B = F2_TWB + F2_N * 4 + (size_t)F2_BTILE * 8;
+constexpr long long F2_SKLO = (long long)F2_N * 32;   // S stride of k_lo
+
+// pass A / C geometry for YL y_lo per block
+template <int YL>
+struct F2AC {
+  static constexpr int THREADS = 256 * YL;
+  static constexpr int LINES = 16 * YL;
+  static constexpr int BLOCKS = 4096 / YL;
+  static constexpr size_t SMEM = F2_TWB + (size_t)LINES * F2_PL * 8 + 32 * kNumSums * 8;
+};
+
+// w256^{y_lo k_lo} (forward) from the stage-1 twiddle block
+__device__ __forceinline__ cpx<float> f2_tw(const cpx<float>* tw_s, int ylo, int klo) {
+  return klo == 0 ? mk<float>(1.f, 0.f) : tw_s[F2_TW1 + ylo * 15 + klo - 1];
+}
+
+__device__ __forceinline__ int f2_tile(int line, int e) { return line * F2_PL + e + (e >> 4); }
+// B tile: row z (odd pitch) plus one element of skew per 16 rows, so rows 16 apart (the
+// Stockham exchange) fall in different banks as well as consecutive rows
+__device__ __forceinline__ int f2_b(int row, int col) { return row * F2_BP + col + (row >> 4); }
+
+// Blocks are dispatched roughly in index order, two per SM at a time, so block b + 2 x
+// (SM count) runs about one wave after block b: passes A and B pull that block's inputs
+// into L2 while they work, and the next wave finds them there instead of waiting on HBM.
+__device__ __forceinline__ int f2_next_wave_block() {
+  unsigned nsm;
+  asm("mov.u32 %0, %%nsmid;" : "=r"(nsm));
+  return (int)blockIdx.x + 2 * (int)nsm;
+}
+__device__ __forceinline__ void f2_prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Offset of line `line` of pass-A/C block blk in a natural-order field.
+template <int YL>
+__device__ __forceinline__ long long f2_row(int blk, int line) {
+  const int z = blk / (16 / YL), y0 = (blk % (16 / YL)) * YL;
+  return ((long long)z * F2_N + y0 + (line % YL) + 16 * (line / YL)) * F2_N;
+}
+
+// x transform of the 16 elements v[r] = line element g + 16 r of this thread's line
+// (positions g + 16 r in and out), through the line tile for the stage exchange.  A line
+// belongs to 16 lanes of one warp and its tile row to those lanes alone (callers
+// separate block-wide tile use with __syncthreads), so the exchange needs only warp
+// synchronisation.
+template <bool INV>
+__device__ __forceinline__ void f2_x_transform(cpx<float> (&v)[16], int line, int g, cpx<float>* tile,
+                                               const cpx<float>* tw_s) {
+  stage_compute<float, F2_N, 0, INV>(v, g, tw_s);
+  __syncwarp();  // the line's earlier reads of its tile row are done
+#pragma unroll
+  for (int r = 0; r < 16; ++r) tile[f2_tile(line, 16 * g + r)] = v[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = tile[f2_tile(line, g + 16 * r)];
+  stage_compute<float, F2_N, 1, INV>(v, g, tw_s);
+}
+
+// Thread roles in a pass-A/C block (YL consecutive y_lo of one z).
+template <int YL>
+struct F2Roles {
+  int z, y0;              // first y_lo of the block
+  int line, g;            // x role: line YL y_hi + s, element group g
+  int kx, s, ylo;         // cross role: column kx of the lines with y_lo = y0 + s
+  long long row;          // natural offset of line `line`
+  long long sbase;        // S offset of (kx_hi, k_lo = 0, z, y_lo, kx_lo)
+  __device__ __forceinline__ F2Roles(int blk) {
+    z = blk / (16 / YL);
+    y0 = (blk % (16 / YL)) * YL;
+    const int tid = threadIdx.x;
+    line = tid >> 4;
+    g = tid & 15;
+    row = f2_row<YL>(blk, line);
+    const int kxlo = tid & 1;
+    s = YL == 1 ? 0 : (tid >> 1) & (YL - 1);
+    const int kxhi = tid >> (YL == 1 ? 1 : 2);
+    kx = 2 * kxhi + kxlo;
+    ylo = y0 + s;
+    sbase = ((long long)kxhi * 16 * F2_N + z) * 32 + 2 * ylo + kxlo;
+  }
+};
+
+// Cross stage forward: line tile (x-transformed) -> 16-point DFTs over y_hi, twiddle,
+// store into S.
+template <int YL>
+__device__ __forceinline__ void f2_cross_fwd(const F2Roles<YL>& q, const cpx<float>* tile, const cpx<float>* tw_s,
+                                             cpx<float>* S) {
+  cpx<float> u[16];
+#pragma unroll
+  for (int yh = 0; yh < 16; ++yh) u[yh] = tile[f2_tile(YL * yh + q.s, q.kx)];
+  dft16<float, false>(u);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) S[q.sbase + k * F2_SKLO] = cmul<float>(u[k], f2_tw(tw_s, q.ylo, k));
+}
+
+// Pass A: field `src` (natural order) -> S.
+template <int YL>
+__global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_a_kernel(const __grid_constant__ FftGroup<float> gr) {
+  const FftPassArgs<float>& a = gr.a[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char f2_smem[];
+  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
+  cpx<float>* tile = reinterpret_cast<cpx<float>*>(f2_smem + F2_TWB);
+  const F2Roles<YL> q(blockIdx.x);
+  const cpx<float>* __restrict__ src = a.src ? a.src : a.psi;
+  cpx<float> v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = src[q.row + q.g + 16 * r];
+  {
+    const int nb = f2_next_wave_block();
+    if (nb < (int)gridDim.x && threadIdx.x < F2AC<YL>::LINES)
+      f2_prefetch_l2(src + f2_row<YL>(nb, threadIdx.x), F2_N * 8);
+  }
+  for (int i = threadIdx.x; i < F2_TW; i += F2AC<YL>::THREADS) tw_s[i] = a.twiddle[i];
+  __syncthreads();
+  f2_x_transform<false>(v, q.line, q.g, tile, tw_s);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) tile[f2_tile(q.line, q.g + 16 * r)] = v[r];
+  __syncthreads();
+  f2_cross_fwd<YL>(q, tile, tw_s, a.data);
+}
+
+// Pass B: S in place (one (kx_hi, k_lo) block of 8192 contiguous elements).
+__global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_constant__ FftGroup<float> gr) {
+  const FftPassArgs<float>& a = gr.a[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char f2_smem[];
+  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
+  float* sym_s = reinterpret_cast<float*>(f2_smem + F2_TWB);
+  cpx<float>* tile = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(sym_s) + F2_N * 4);
+  const int blk = blockIdx.x, kxhi = blk >> 4, klo = blk & 15;
+  const int tid = threadIdx.x;
+  const float4* S4 = reinterpret_cast<const float4*>(a.data + (long long)blk * 8192);
+  float4* D4 = reinterpret_cast<float4*>(a.data + (long long)blk * 8192);
+  {
+    const int nb = f2_next_wave_block();
+    if (nb < (int)gridDim.x && tid < 4) f2_prefetch_l2(a.data + (long long)nb * 8192 + tid * 2048, 2048 * 8);
+  }
+  // coalesced load: element e = 2 i (+1) -> row z = e >> 5, column e & 31
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int i = tid + F2_THREADS * j, e = 2 * i;
+    const float4 w = S4[i];
+    cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
+    t[0] = mk<float>(w.x, w.y);
+    t[1] = mk<float>(w.z, w.w);
+  }
+  for (int i = tid; i < F2_TW; i += F2_THREADS) tw_s[i] = a.twiddle[i];
+  for (int i = tid; i < F2_N; i += F2_THREADS) sym_s[i] = a.symbol[i];
+  __syncthreads();
+  // outer y DFTs over y_lo for each (z, kx_lo): natural-order k_hi in place (a half-warp
+  // holds 16 consecutive z of one kx_lo)
+  const int kxl = (tid >> 4) & 1, zr = (tid & 15) + 16 * (tid >> 5);
+  {
+    cpx<float> u[16];
+#pragma unroll
+    for (int y = 0; y < 16; ++y) u[y] = tile[f2_b(zr, 2 * y + kxl)];
+    dft16<float, false>(u);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) tile[f2_b(zr, 2 * k + kxl)] = u[k];
+  }
+  __syncthreads();
+  // z transforms of the 32 columns c = 2 k_hi + kx_lo: a warp owns two whole columns
+  // (lanes = 16 element groups g x 2 columns), so the stage exchange is warp-local
+  const int c = 2 * (tid >> 5) + ((tid >> 4) & 1), g = tid & 15;
+  cpx<float> v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
+  stage_compute<float, F2_N, 0, false>(v, g, tw_s);
+  __syncwarp();  // (the column's own lanes are its only readers)
+#pragma unroll
+  for (int r = 0; r < 16; ++r) tile[f2_b(16 * g + r, c)] = v[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
+  stage_compute<float, F2_N, 1, false>(v, g, tw_s);
+  // natural-order kz = g + 16 r; T(kx, ky, kz)/N^3
+  {
+    const int kx = 2 * kxhi + (c & 1), ky = klo + 16 * (c >> 1);
+    const float sxy = sym_s[kx] + sym_s[ky];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+      v[r] = cscale<float>(v[r], kin_mult<float>(a.kinetic, sxy, sym_s[g + 16 * r], a.tcoef, a.am2));
+  }
+  stage_compute<float, F2_N, 0, true>(v, g, tw_s);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) tile[f2_b(16 * g + r, c)] = v[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
+  stage_compute<float, F2_N, 1, true>(v, g, tw_s);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) tile[f2_b(g + 16 * r, c)] = v[r];
+  __syncthreads();
+  // outer inverse y DFTs over k_hi: natural-order y_lo in place
+  {
+    cpx<float> u[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) u[k] = tile[f2_b(zr, 2 * k + kxl)];
+    dft16<float, true>(u);
+#pragma unroll
+    for (int y = 0; y < 16; ++y) tile[f2_b(zr, 2 * y + kxl)] = u[y];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int i = tid + F2_THREADS * j, e = 2 * i;
+    const cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
+    D4[i] = make_float4(t[0].x, t[0].y, t[1].x, t[1].y);
+  }
+}
+
+// Pass C: S -> inverse inner y DFTs, x inverse -> H_K psi; update / sums; with NEXT, pass A
+// on psi_{t+1} into S.  OP: OP_FINAL (write), OP_FINAL_SUMS (write + sums), OP_SUMS.
+template <int YL, int OP, bool VREAL, bool NEXT>
+__global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const __grid_constant__ FftGroup<float> gr) {
+  constexpr bool WRITE = (OP == OP_FINAL || OP == OP_FINAL_SUMS);
+  constexpr bool SUMS = (OP == OP_FINAL_SUMS || OP == OP_SUMS);
+  constexpr int LINES = F2AC<YL>::LINES;
+  const FftPassArgs<float>& a = gr.a[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char f2_smem[];
+  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
+  cpx<float>* tile = reinterpret_cast<cpx<float>*>(f2_smem + F2_TWB);
+  double* red_s = reinterpret_cast<double*>(tile + LINES * F2_PL);
+  const F2Roles<YL> q(blockIdx.x);
+  // psi and V of the output rows are needed only after the transforms: start pulling them
+  // into L2 now, one bulk prefetch per row.  (Prefetching the next wave's rows or scratch
+  // sectors here as well measured slower: this pass already moves 36 B per site.)
+  if (threadIdx.x < 2 * LINES) {
+    const long long row = f2_row<YL>(blockIdx.x, threadIdx.x % LINES);
+    if (threadIdx.x < LINES) f2_prefetch_l2(a.psi + row, F2_N * 8);
+    else if (VREAL) f2_prefetch_l2(reinterpret_cast<const float*>(a.v) + row, F2_N * 4);
+    else f2_prefetch_l2(reinterpret_cast<const cpx<float>*>(a.v) + row, F2_N * 8);
+  }
+  for (int i = threadIdx.x; i < F2_TW; i += F2AC<YL>::THREADS) tw_s[i] = a.twiddle[i];
+  cpx<float> u[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) u[k] = a.data[q.sbase + k * F2_SKLO];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 16; ++k) u[k] = cmulc<float>(u[k], f2_tw(tw_s, q.ylo, k));
+  dft16<float, true>(u);
+#pragma unroll
+  for (int yh = 0; yh < 16; ++yh) tile[f2_tile(YL * yh + q.s, q.kx)] = u[yh];
+  __syncthreads();
+  cpx<float> v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = tile[f2_tile(q.line, q.g + 16 * r)];
+  f2_x_transform<true>(v, q.line, q.g, tile, tw_s);
+  // v[r] = H_K psi at x = g + 16 r of row `row` (1/N^3 inside T); psi and V are read
+  // site by site (registers are the limit)
+  CheckSums<float> cs;
+  const float sc = WRITE ? float(*a.scale) : 1.f;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const long long site = q.row + q.g + 16 * r;
+    const cpx<float> pv = a.psi[site];
+    cpx<float> vi;
+    if constexpr (VREAL) vi = mk<float>(reinterpret_cast<const float*>(a.v)[site], 0.f);
+    else vi = reinterpret_cast<const cpx<float>*>(a.v)[site];
+    if constexpr (SUMS) cs.add(pv, v[r], vi);
+    if constexpr (WRITE) {
+      // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d
+      const cpx<float> d = mk<float>(1.f + a.half_dtau * vi.x, a.half_dtau * vi.y);
+      const cpx<float> num = cmul<float>(mk<float>(2.f - d.x, -d.y), pv) - cscale<float>(v[r], a.dtau);
+      const float inv = __fdividef(sc, d.x * d.x + d.y * d.y);
+      v[r] = cscale<float>(cmulc<float>(num, d), inv);  // psi_{t+1}
+      a.psi[site] = v[r];
+    }
+  }
+  if constexpr (SUMS) {
+    double acc[kNumSums];
+    cs.to(acc);
+    block_sum_store<kNumSums>(acc, red_s, a.partials + ((long long)blockIdx.x) * kPartialStride);
+  }
+  if constexpr (WRITE && NEXT) {
+    f2_x_transform<false>(v, q.line, q.g, tile, tw_s);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) tile[f2_tile(q.line, q.g + 16 * r)] = v[r];
+    __syncthreads();
+    f2_cross_fwd<YL>(q, tile, tw_s, a.data);
+  }
+}
+
+}  // namespace qf

@@ -127,10 +127,15 @@ class Lattice:
         i = Q.qf_info()
         _check(self.h, self.lib.qf_get_info(self.h, C.byref(i)), "qf_get_info")
         return dict(dtau=i.dtau, step=i.step, tau=i.tau, kinetic=i.kinetic, n_snapshots=i.n_snapshots,
-                    workspace_bytes=i.workspace_bytes, launches=i.launches, temporal_block=i.temporal_block)
+                    workspace_bytes=i.workspace_bytes, launches=i.launches, temporal_block=i.temporal_block,
+                    fft_passes=i.fft_passes)
 
     def use_graphs(self, enable: bool = True):
         _check(self.h, self.lib.qf_use_graphs(self.h, int(bool(enable))), "qf_use_graphs")
+
+    def use_two_pass_fft(self, enable: bool = True):
+        """Two HBM passes per FFT step for N = 256 complex FP32 (default) or four."""
+        _check(self.h, self.lib.qf_use_two_pass_fft(self.h, int(bool(enable))), "qf_use_two_pass_fft")
 
     def set_temporal_blocking(self, k: int):
         """FDTD steps per pass over HBM (1 or 2; complex FP32 only)."""

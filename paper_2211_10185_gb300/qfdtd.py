@@ -36,7 +36,7 @@ class qf_energy(C.Structure):
 class qf_info(C.Structure):
     _fields_ = [("dtau", C.c_double), ("step", C.c_int64), ("tau", C.c_double), ("kinetic", C.c_int),
                 ("n_snapshots", C.c_int), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64),
-                ("temporal_block", C.c_int)]
+                ("temporal_block", C.c_int), ("fft_passes", C.c_int)]
 
 
 class qf_kernel_stat(C.Structure):
@@ -77,6 +77,7 @@ SIGNATURES = {
     "qf_selftest_bounded_wait": (C.c_int, [_P]),
     "qf_use_graphs": (C.c_int, [_P, C.c_int]),
     "qf_set_temporal_blocking": (C.c_int, [_P, C.c_int]),
+    "qf_use_two_pass_fft": (C.c_int, [_P, C.c_int]),
     "qf_last_error": (C.c_char_p, [_P]),
     "qf_version": (C.c_char_p, []),
 }

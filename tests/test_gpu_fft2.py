@@ -1,0 +1,136 @@
+"""The two-pass FFT step (N = 256, complex FP32) against the oracle and the four-pass step.
+
+The two-pass form splits the y transform 16 x 16 between its passes and keeps the
+scratch field in a blocked layout; it must compute the same step as the four-pass form
+to FP32 rounding, match the FP64 oracle to the usual c64 tolerance, and run bitwise the
+same alone and inside a batch (both launch the same grouped kernels).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qfdtd_oracle as O
+from paper_2211_10185_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+N, A = 256, 0.05
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10185_gb300 import build
+
+    build.build()
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
+
+
+def _potential(cplx):
+    v = I.cornell(N, A, 0.4, 0.2)
+    return v - 0.04j * np.abs(v) if cplx else v
+
+
+def _dtau(kind):
+    # a/4 for the relativistic term (the bench workload); the stable default otherwise
+    return A / 4 if kind == I.FFT_REL else None
+
+
+def _lat(kind, v, psi0, two_pass=True, m=0.3):
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    lat = Lattice(N, A, precision="c64")
+    lat.set_potential(v)
+    lat.set_kinetic(kind, m, _dtau(kind))
+    lat.set_wavefunction(psi0)
+    lat.use_two_pass_fft(two_pass)
+    return lat
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("kind", [I.FFT_NAIVE, I.FFT_SYMANZIK, I.FFT_REL])
+def test_two_pass_step_matches_oracle_every_site(kind, cplx):
+    v = _potential(cplx)
+    psi0 = I.gaussian_field(N, 11 + kind)
+    gpu = _lat(kind, v, psi0)
+    assert gpu.info()["fft_passes"] == 2
+    ref = O.Lattice(N, A)
+    if cplx:
+        ref.set_potential(v.real, v.imag)
+    else:
+        ref.set_potential(v)
+    ref.set_kinetic(kind, 0.3, _dtau(kind))
+    ref.set_wavefunction(psi0)
+    # step 0 with a check (sums), step 1 plain with the renormalisation (the first step
+    # starts from the natural-order pass, the second from the emitted scratch field)
+    for _ in range(2):
+        ref.step_n(1, check_every=2)
+        gpu.step_n(1, tol=0.0, check_every=2)
+    tol = 2e-6 * (1 + math.log2(N))
+    assert _rel(gpu.get_wavefunction(), ref.psi) < tol
+    e_ref, e_gpu = ref.energies(), gpu.energies()
+    assert abs(e_gpu["e"] - e_ref["e"]) < 1e-5 * abs(e_ref["e"])
+    assert e_gpu["norm"] == pytest.approx(e_ref["norm"], rel=1e-5)
+
+
+@pytest.mark.parametrize("kind", [I.FFT_SYMANZIK, I.FFT_REL])
+def test_two_pass_and_four_pass_agree_over_many_steps(kind):
+    v = _potential(True)
+    psi0 = I.gaussian_field(N, 3)
+    two = _lat(kind, v, psi0, True)
+    four = _lat(kind, v, psi0, False)
+    assert four.info()["fft_passes"] == 4
+    for lat in (two, four):
+        lat.step_n(193, tol=0.0, check_every=64, snap_every=64)
+    assert _rel(two.get_wavefunction(), four.get_wavefunction()) < 2e-5
+    e2, e4 = two.energies(), four.energies()
+    assert e2["step"] == e4["step"] == 192
+    assert abs(e2["e"] - e4["e"]) < 1e-5 * abs(e4["e"])
+    # excited states through the measure passes (pass A from a state slot, sums-only C)
+    x2, x4 = two.project_excited(3), four.project_excited(3)
+    for a, b in zip(x2, x4):
+        assert abs(a["e"] - b["e"]) < 1e-4 * abs(b["e"])
+    # fewer launches per steady-state step
+    assert two.info()["launches"] < four.info()["launches"]
+
+
+def test_switching_forms_mid_run_keeps_the_step():
+    v = _potential(False)
+    psi0 = I.gaussian_field(N, 5)
+    ref = _lat(I.FFT_REL, v, psi0, True)
+    mix = _lat(I.FFT_REL, v, psi0, True)
+    ref.step_n(6, tol=0.0, check_every=3)
+    mix.step_n(3, tol=0.0, check_every=3)
+    mix.use_two_pass_fft(False)   # the scratch field's blocked layout is discarded
+    mix.step_n(2, tol=0.0, check_every=3)
+    mix.use_two_pass_fft(True)
+    mix.step_n(1, tol=0.0, check_every=3)
+    assert _rel(mix.get_wavefunction(), ref.get_wavefunction()) < 1e-5
+
+
+def test_two_pass_batch_members_match_alone_bitwise():
+    from paper_2211_10185_gb300.serve import Batch
+
+    specs = [(I.FFT_REL, False, 1), (I.FFT_NAIVE, True, 2), (I.FFT_SYMANZIK, False, 3)]
+    alone, mixed = [], []
+    for kind, cplx, seed in specs:
+        v = _potential(cplx)
+        psi0 = I.gaussian_field(N, seed)
+        alone.append(_lat(kind, v, psi0))
+        mixed.append(_lat(kind, v, psi0))
+    for lat in alone:
+        lat.step_n(70, tol=0.0, check_every=32, snap_every=32)
+    b = Batch()
+    for lat in mixed:
+        b.add(lat, 70, 0.0)
+    while b.step(35, check_every=32) > 0:
+        pass
+    for la, lm in zip(alone, mixed):
+        assert np.array_equal(la.get_wavefunction(), lm.get_wavefunction())
+        assert la.energies()["e"] == lm.energies()["e"]
