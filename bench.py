@@ -40,7 +40,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # sources that family compiles from
 TRAFFIC_FILES = {
     "fft": (os.path.join(ROOT, "profiles", "ncu_traffic_fft_step_n256.json"),
-            ("qf_fft_impl.cuh", "qf_common.cuh")),
+            ("qf_fft_impl.cuh", "qf_common.cuh", "qf_fft2.cuh")),
     "stencil": (os.path.join(ROOT, "profiles", "ncu_traffic_fdtd_step_n256.json"),
                 ("qf_stencil.cu", "qf_stencil_tma.cuh", "qf_stencil_tb.cuh", "qf_common.cuh")),
 }
@@ -234,6 +234,9 @@ def bytes_per_site(kernel, prec, v_real):
         "stencil_step": 2 * c + vb,
         # two steps per launch: read psi_t and V, write psi_{t+2}
         "stencil_2step": 2 * c + vb,
+        # two-pass FFT step (N=256 c64): y/z pass in place; x/y pass reading the scratch
+        # field, psi and V, writing psi' and the next step's scratch field
+        "fft2_xy_fwd": 2 * c, "fft2_yz_mid_T": 2 * c, "fft2_xy_inv_update": 4 * c + vb,
     }
     return table.get(kernel)
 
