@@ -160,7 +160,11 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_a_kernel(const
   f2_cross_fwd<YL>(q, tile, tw_s, a.data);
 }
 
-// Pass B: S in place (one (kx_hi, k_lo) block of 8192 contiguous elements).
+// Pass B: S in place (one (kx_hi, k_lo) block of 8192 contiguous elements).  The outer y
+// DFTs read their 16 inputs straight from global memory (L1 serves the neighbouring
+// elements of each sector) and the inverse ones write straight back, so the tile carries
+// only the z transforms.
+constexpr bool kF2BDirect = true;
 __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_constant__ FftGroup<float> gr) {
   const FftPassArgs<float>& a = gr.a[blockIdx.y];
   extern __shared__ __align__(16) unsigned char f2_smem[];
@@ -175,29 +179,36 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
     const int nb = f2_next_wave_block();
     if (nb < (int)gridDim.x && tid < 4) f2_prefetch_l2(a.data + (long long)nb * 8192 + tid * 2048, 2048 * 8);
   }
-  // coalesced load: element e = 2 i (+1) -> row z = e >> 5, column e & 31
+  // outer y DFTs over y_lo for each (z, kx_lo): natural-order k_hi (a half-warp holds 16
+  // consecutive z of one kx_lo)
+  const int kxl = (tid >> 4) & 1, zr = (tid & 15) + 16 * (tid >> 5);
+  const cpx<float>* Sblk = a.data + (long long)blk * 8192;
+  if constexpr (!kF2BDirect) {
+    // coalesced load: element e = 2 i (+1) -> row z = e >> 5, column e & 31
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int i = tid + F2_THREADS * j, e = 2 * i;
-    const float4 w = S4[i];
-    cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
-    t[0] = mk<float>(w.x, w.y);
-    t[1] = mk<float>(w.z, w.w);
+    for (int j = 0; j < 8; ++j) {
+      const int i = tid + F2_THREADS * j, e = 2 * i;
+      const float4 w = S4[i];
+      cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
+      t[0] = mk<float>(w.x, w.y);
+      t[1] = mk<float>(w.z, w.w);
+    }
+  }
+  cpx<float> u[16];
+  if constexpr (kF2BDirect) {
+#pragma unroll
+    for (int y = 0; y < 16; ++y) u[y] = Sblk[zr * 32 + 2 * y + kxl];
   }
   for (int i = tid; i < F2_TW; i += F2_THREADS) tw_s[i] = a.twiddle[i];
   for (int i = tid; i < F2_N; i += F2_THREADS) sym_s[i] = a.symbol[i];
-  __syncthreads();
-  // outer y DFTs over y_lo for each (z, kx_lo): natural-order k_hi in place (a half-warp
-  // holds 16 consecutive z of one kx_lo)
-  const int kxl = (tid >> 4) & 1, zr = (tid & 15) + 16 * (tid >> 5);
-  {
-    cpx<float> u[16];
+  if constexpr (!kF2BDirect) {
+    __syncthreads();
 #pragma unroll
     for (int y = 0; y < 16; ++y) u[y] = tile[f2_b(zr, 2 * y + kxl)];
-    dft16<float, false>(u);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) tile[f2_b(zr, 2 * k + kxl)] = u[k];
   }
+  dft16<float, false>(u);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) tile[f2_b(zr, 2 * k + kxl)] = u[k];
   __syncthreads();
   // z transforms of the 32 columns c = 2 k_hi + kx_lo: a warp owns two whole columns
   // (lanes = 16 element groups g x 2 columns), so the stage exchange is warp-local
@@ -233,21 +244,24 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
 #pragma unroll
   for (int r = 0; r < 16; ++r) tile[f2_b(g + 16 * r, c)] = v[r];
   __syncthreads();
-  // outer inverse y DFTs over k_hi: natural-order y_lo in place
-  {
-    cpx<float> u[16];
+  // outer inverse y DFTs over k_hi: natural-order y_lo
 #pragma unroll
-    for (int k = 0; k < 16; ++k) u[k] = tile[f2_b(zr, 2 * k + kxl)];
-    dft16<float, true>(u);
+  for (int k = 0; k < 16; ++k) u[k] = tile[f2_b(zr, 2 * k + kxl)];
+  dft16<float, true>(u);
+  if constexpr (kF2BDirect) {
+    cpx<float>* Dblk = a.data + (long long)blk * 8192;
+#pragma unroll
+    for (int y = 0; y < 16; ++y) Dblk[zr * 32 + 2 * y + kxl] = u[y];
+  } else {
 #pragma unroll
     for (int y = 0; y < 16; ++y) tile[f2_b(zr, 2 * y + kxl)] = u[y];
-  }
-  __syncthreads();
+    __syncthreads();
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int i = tid + F2_THREADS * j, e = 2 * i;
-    const cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
-    D4[i] = make_float4(t[0].x, t[0].y, t[1].x, t[1].y);
+    for (int j = 0; j < 8; ++j) {
+      const int i = tid + F2_THREADS * j, e = 2 * i;
+      const cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
+      D4[i] = make_float4(t[0].x, t[0].y, t[1].x, t[1].y);
+    }
   }
 }
 
@@ -302,10 +316,16 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const
     if constexpr (SUMS) cs.add(pv, v[r], vi);
     if constexpr (WRITE) {
       // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d
-      const cpx<float> d = mk<float>(1.f + a.half_dtau * vi.x, a.half_dtau * vi.y);
-      const cpx<float> num = cmul<float>(mk<float>(2.f - d.x, -d.y), pv) - cscale<float>(v[r], a.dtau);
-      const float inv = __fdividef(sc, d.x * d.x + d.y * d.y);
-      v[r] = cscale<float>(cmulc<float>(num, d), inv);  // psi_{t+1}
+      if constexpr (VREAL) {
+        const float d = 1.f + a.half_dtau * vi.x;
+        const cpx<float> num = cscale<float>(pv, 2.f - d) - cscale<float>(v[r], a.dtau);
+        v[r] = cscale<float>(num, __fdividef(sc, d));  // psi_{t+1}
+      } else {
+        const cpx<float> d = mk<float>(1.f + a.half_dtau * vi.x, a.half_dtau * vi.y);
+        const cpx<float> num = cmul<float>(mk<float>(2.f - d.x, -d.y), pv) - cscale<float>(v[r], a.dtau);
+        const float inv = __fdividef(sc, d.x * d.x + d.y * d.y);
+        v[r] = cscale<float>(cmulc<float>(num, d), inv);  // psi_{t+1}
+      }
       a.psi[site] = v[r];
     }
   }
