@@ -160,11 +160,9 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_a_kernel(const
   f2_cross_fwd<YL>(q, tile, tw_s, a.data);
 }
 
-// Pass B: S in place (one (kx_hi, k_lo) block of 8192 contiguous elements).  The outer y
-// DFTs read their 16 inputs straight from global memory (L1 serves the neighbouring
-// elements of each sector) and the inverse ones write straight back, so the tile carries
-// only the z transforms.
-constexpr bool kF2BDirect = true;
+// Pass B: S in place (one (kx_hi, k_lo) block of 8192 contiguous elements), staged
+// through shared memory with coalesced 16-byte accesses.  (Reading the outer y DFTs'
+// strided inputs straight from global memory measured 1.8x slower.)
 __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_constant__ FftGroup<float> gr) {
   const FftPassArgs<float>& a = gr.a[blockIdx.y];
   extern __shared__ __align__(16) unsigned char f2_smem[];
@@ -182,30 +180,21 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
   // outer y DFTs over y_lo for each (z, kx_lo): natural-order k_hi (a half-warp holds 16
   // consecutive z of one kx_lo)
   const int kxl = (tid >> 4) & 1, zr = (tid & 15) + 16 * (tid >> 5);
-  const cpx<float>* Sblk = a.data + (long long)blk * 8192;
-  if constexpr (!kF2BDirect) {
-    // coalesced load: element e = 2 i (+1) -> row z = e >> 5, column e & 31
+  // coalesced load: element e = 2 i (+1) -> row z = e >> 5, column e & 31
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = tid + F2_THREADS * j, e = 2 * i;
-      const float4 w = S4[i];
-      cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
-      t[0] = mk<float>(w.x, w.y);
-      t[1] = mk<float>(w.z, w.w);
-    }
-  }
-  cpx<float> u[16];
-  if constexpr (kF2BDirect) {
-#pragma unroll
-    for (int y = 0; y < 16; ++y) u[y] = Sblk[zr * 32 + 2 * y + kxl];
+  for (int j = 0; j < 8; ++j) {
+    const int i = tid + F2_THREADS * j, e = 2 * i;
+    const float4 w = S4[i];
+    cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
+    t[0] = mk<float>(w.x, w.y);
+    t[1] = mk<float>(w.z, w.w);
   }
   for (int i = tid; i < F2_TW; i += F2_THREADS) tw_s[i] = a.twiddle[i];
   for (int i = tid; i < F2_N; i += F2_THREADS) sym_s[i] = a.symbol[i];
-  if constexpr (!kF2BDirect) {
-    __syncthreads();
+  __syncthreads();
+  cpx<float> u[16];
 #pragma unroll
-    for (int y = 0; y < 16; ++y) u[y] = tile[f2_b(zr, 2 * y + kxl)];
-  }
+  for (int y = 0; y < 16; ++y) u[y] = tile[f2_b(zr, 2 * y + kxl)];
   dft16<float, false>(u);
 #pragma unroll
   for (int k = 0; k < 16; ++k) tile[f2_b(zr, 2 * k + kxl)] = u[k];
@@ -248,20 +237,14 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
 #pragma unroll
   for (int k = 0; k < 16; ++k) u[k] = tile[f2_b(zr, 2 * k + kxl)];
   dft16<float, true>(u);
-  if constexpr (kF2BDirect) {
-    cpx<float>* Dblk = a.data + (long long)blk * 8192;
 #pragma unroll
-    for (int y = 0; y < 16; ++y) Dblk[zr * 32 + 2 * y + kxl] = u[y];
-  } else {
+  for (int y = 0; y < 16; ++y) tile[f2_b(zr, 2 * y + kxl)] = u[y];
+  __syncthreads();
 #pragma unroll
-    for (int y = 0; y < 16; ++y) tile[f2_b(zr, 2 * y + kxl)] = u[y];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int i = tid + F2_THREADS * j, e = 2 * i;
-      const cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
-      D4[i] = make_float4(t[0].x, t[0].y, t[1].x, t[1].y);
-    }
+  for (int j = 0; j < 8; ++j) {
+    const int i = tid + F2_THREADS * j, e = 2 * i;
+    const cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
+    D4[i] = make_float4(t[0].x, t[0].y, t[1].x, t[1].y);
   }
 }
 
