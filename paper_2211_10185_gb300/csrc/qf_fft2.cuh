@@ -285,43 +285,31 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = tile[f2_tile(q.line, q.g + 16 * r)];
   f2_x_transform<true>(v, q.line, q.g, tile, tw_s);
-  // v[r] = H_K psi at x = g + 16 r of row `row` (1/N^3 inside T).  psi and V are read in
-  // groups of four sites, all loads of a group issued before any store (registers are the
-  // limit at 64 per thread, and a store to psi must not wait behind later psi loads)
+  // v[r] = H_K psi at x = g + 16 r of row `row` (1/N^3 inside T); psi and V are read
+  // site by site (registers are the limit)
   CheckSums<float> cs;
   const float sc = WRITE ? float(*a.scale) : 1.f;
-  constexpr int GRP = 4;
 #pragma unroll
-  for (int r0 = 0; r0 < 16; r0 += GRP) {
-    cpx<float> pv[GRP], vi[GRP];
-#pragma unroll
-    for (int j = 0; j < GRP; ++j) {
-      const long long site = q.row + q.g + 16 * (r0 + j);
-      pv[j] = a.psi[site];
-      if constexpr (VREAL) vi[j] = mk<float>(reinterpret_cast<const float*>(a.v)[site], 0.f);
-      else vi[j] = reinterpret_cast<const cpx<float>*>(a.v)[site];
-    }
-#pragma unroll
-    for (int j = 0; j < GRP; ++j) {
-      const int r = r0 + j;
-      if constexpr (SUMS) cs.add(pv[j], v[r], vi[j]);
-      if constexpr (WRITE) {
-        // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d
-        if constexpr (VREAL) {
-          const float d = 1.f + a.half_dtau * vi[j].x;
-          const cpx<float> num = cscale<float>(pv[j], 2.f - d) - cscale<float>(v[r], a.dtau);
-          v[r] = cscale<float>(num, __fdividef(sc, d));  // psi_{t+1}
-        } else {
-          const cpx<float> d = mk<float>(1.f + a.half_dtau * vi[j].x, a.half_dtau * vi[j].y);
-          const cpx<float> num = cmul<float>(mk<float>(2.f - d.x, -d.y), pv[j]) - cscale<float>(v[r], a.dtau);
-          const float inv = __fdividef(sc, d.x * d.x + d.y * d.y);
-          v[r] = cscale<float>(cmulc<float>(num, d), inv);  // psi_{t+1}
-        }
-      }
-    }
+  for (int r = 0; r < 16; ++r) {
+    const long long site = q.row + q.g + 16 * r;
+    const cpx<float> pv = a.psi[site];
+    cpx<float> vi;
+    if constexpr (VREAL) vi = mk<float>(reinterpret_cast<const float*>(a.v)[site], 0.f);
+    else vi = reinterpret_cast<const cpx<float>*>(a.v)[site];
+    if constexpr (SUMS) cs.add(pv, v[r], vi);
     if constexpr (WRITE) {
-#pragma unroll
-      for (int j = 0; j < GRP; ++j) a.psi[q.row + q.g + 16 * (r0 + j)] = v[r0 + j];
+      // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d
+      if constexpr (VREAL) {
+        const float d = 1.f + a.half_dtau * vi.x;
+        const cpx<float> num = cscale<float>(pv, 2.f - d) - cscale<float>(v[r], a.dtau);
+        v[r] = cscale<float>(num, __fdividef(sc, d));  // psi_{t+1}
+      } else {
+        const cpx<float> d = mk<float>(1.f + a.half_dtau * vi.x, a.half_dtau * vi.y);
+        const cpx<float> num = cmul<float>(mk<float>(2.f - d.x, -d.y), pv) - cscale<float>(v[r], a.dtau);
+        const float inv = __fdividef(sc, d.x * d.x + d.y * d.y);
+        v[r] = cscale<float>(cmulc<float>(num, d), inv);  // psi_{t+1}
+      }
+      a.psi[site] = v[r];
     }
   }
   if constexpr (SUMS) {
