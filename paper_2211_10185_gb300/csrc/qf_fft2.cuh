@@ -250,31 +250,13 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
 
 // Pass C: S -> inverse inner y DFTs, x inverse -> H_K psi; update / sums; with NEXT, pass A
 // on psi_{t+1} into S.  OP: OP_FINAL (write), OP_FINAL_SUMS (write + sums), OP_SUMS.
+// Everything of pass C after the scratch values u (this thread's 16 k_lo values of its
+// cross-role column) are in registers: block `item`.
 template <int YL, int OP, bool VREAL, bool NEXT>
-__global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const __grid_constant__ FftGroup<float> gr) {
+__device__ __forceinline__ void f2_c_body(const FftPassArgs<float>& a, const F2Roles<YL>& q, cpx<float> (&u)[16],
+                                          cpx<float>* tile, const cpx<float>* tw_s, double* red_s, int item) {
   constexpr bool WRITE = (OP == OP_FINAL || OP == OP_FINAL_SUMS);
   constexpr bool SUMS = (OP == OP_FINAL_SUMS || OP == OP_SUMS);
-  constexpr int LINES = F2AC<YL>::LINES;
-  const FftPassArgs<float>& a = gr.a[blockIdx.y];
-  extern __shared__ __align__(16) unsigned char f2_smem[];
-  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
-  cpx<float>* tile = reinterpret_cast<cpx<float>*>(f2_smem + F2_TWB);
-  double* red_s = reinterpret_cast<double*>(tile + LINES * F2_PL);
-  const F2Roles<YL> q(blockIdx.x);
-  // psi and V of the output rows are needed only after the transforms: start pulling them
-  // into L2 now, one bulk prefetch per row.  (Prefetching the next wave's rows or scratch
-  // sectors here as well measured slower: this pass already moves 36 B per site.)
-  if (threadIdx.x < 2 * LINES) {
-    const long long row = f2_row<YL>(blockIdx.x, threadIdx.x % LINES);
-    if (threadIdx.x < LINES) f2_prefetch_l2(a.psi + row, F2_N * 8);
-    else if (VREAL) f2_prefetch_l2(reinterpret_cast<const float*>(a.v) + row, F2_N * 4);
-    else f2_prefetch_l2(reinterpret_cast<const cpx<float>*>(a.v) + row, F2_N * 8);
-  }
-  for (int i = threadIdx.x; i < F2_TW; i += F2AC<YL>::THREADS) tw_s[i] = a.twiddle[i];
-  cpx<float> u[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) u[k] = a.data[q.sbase + k * F2_SKLO];
-  __syncthreads();
 #pragma unroll
   for (int k = 0; k < 16; ++k) u[k] = cmulc<float>(u[k], f2_tw(tw_s, q.ylo, k));
   dft16<float, true>(u);
@@ -315,7 +297,7 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const
   if constexpr (SUMS) {
     double acc[kNumSums];
     cs.to(acc);
-    block_sum_store<kNumSums>(acc, red_s, a.partials + ((long long)blockIdx.x) * kPartialStride);
+    block_sum_store<kNumSums>(acc, red_s, a.partials + ((long long)item) * kPartialStride);
   }
   if constexpr (WRITE && NEXT) {
     f2_x_transform<false>(v, q.line, q.g, tile, tw_s);
@@ -324,6 +306,93 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const
     for (int r = 0; r < 16; ++r) tile[f2_tile(q.line, q.g + 16 * r)] = v[r];
     __syncthreads();
     f2_cross_fwd<YL>(q, tile, tw_s, a.data);
+  }
+}
+
+// L2 prefetch of psi and V of the output rows of pass-C block `item` (threads < 4 YL 16).
+template <int YL, bool VREAL>
+__device__ __forceinline__ void f2_prefetch_psi_v(const FftPassArgs<float>& a, int item) {
+  constexpr int LINES = F2AC<YL>::LINES;
+  if (threadIdx.x < 2 * LINES) {
+    const long long row = f2_row<YL>(item, threadIdx.x % LINES);
+    if (threadIdx.x < LINES) f2_prefetch_l2(a.psi + row, F2_N * 8);
+    else if (VREAL) f2_prefetch_l2(reinterpret_cast<const float*>(a.v) + row, F2_N * 4);
+    else f2_prefetch_l2(reinterpret_cast<const cpx<float>*>(a.v) + row, F2_N * 8);
+  }
+}
+
+template <int YL, int OP, bool VREAL, bool NEXT>
+__global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const __grid_constant__ FftGroup<float> gr) {
+  constexpr int LINES = F2AC<YL>::LINES;
+  const FftPassArgs<float>& a = gr.a[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char f2_smem[];
+  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
+  cpx<float>* tile = reinterpret_cast<cpx<float>*>(f2_smem + F2_TWB);
+  double* red_s = reinterpret_cast<double*>(tile + LINES * F2_PL);
+  const F2Roles<YL> q(blockIdx.x);
+  // psi and V of the output rows are needed only after the transforms: start pulling them
+  // into L2 now, one bulk prefetch per row.  (Prefetching the next wave's rows or scratch
+  // sectors here as well measured slower: this pass already moves 36 B per site.)
+  f2_prefetch_psi_v<YL, VREAL>(a, blockIdx.x);
+  for (int i = threadIdx.x; i < F2_TW; i += F2AC<YL>::THREADS) tw_s[i] = a.twiddle[i];
+  cpx<float> u[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) u[k] = a.data[q.sbase + k * F2_SKLO];
+  __syncthreads();
+  f2_c_body<YL, OP, VREAL, NEXT>(a, q, u, tile, tw_s, red_s, blockIdx.x);
+}
+
+// Persistent form of pass C (two y_lo per item, one 512-thread block per SM): while an
+// item is computed, the next item's scratch sectors stream into a staging buffer with
+// cp.async (16-byte copies, no registers) and its psi and V rows into L2, so no item
+// starts by waiting on HBM.  Staging layout: row = kx_hi 16 + k_lo, 4 elements
+// (2 y_lo x 2 kx_lo) each, plus 4 elements of skew per 16 rows (conflict-free reads).
+constexpr int F2P_STAGE = 2048 * 4 + 128 * 4;
+constexpr size_t F2P_SMEM = F2_TWB + (size_t)32 * F2_PL * 8 + (size_t)F2P_STAGE * 8 + 32 * kNumSums * 8;
+__device__ __forceinline__ int f2p_stage(int row, int e) { return row * 4 + (row >> 4) * 4 + e; }
+
+__device__ __forceinline__ void f2p_issue(const cpx<float>* S, cpx<float>* stage, int item) {
+  const int z = item >> 3, p = item & 7;
+  for (int i = threadIdx.x; i < 4096; i += F2_THREADS) {
+    const int row = i >> 1, half = i & 1;
+    const cpx<float>* src = S + ((long long)row * F2_N + z) * 32 + 4 * p + 2 * half;
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(stage + f2p_stage(row, 2 * half));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int OP, bool VREAL, bool NEXT>
+__global__ void __launch_bounds__(F2_THREADS, 1) fft2_cp_kernel(const __grid_constant__ FftGroup<float> gr) {
+  const FftPassArgs<float>& a = gr.a[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char f2_smem[];
+  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
+  cpx<float>* tile = reinterpret_cast<cpx<float>*>(f2_smem + F2_TWB);
+  cpx<float>* stage = tile + 32 * F2_PL;
+  double* red_s = reinterpret_cast<double*>(stage + F2P_STAGE);
+  constexpr int ITEMS = F2AC<2>::BLOCKS;
+  int item = blockIdx.x;
+  if (item < ITEMS) {
+    f2p_issue(a.data, stage, item);
+    f2_prefetch_psi_v<2, VREAL>(a, item);
+  }
+  for (int i = threadIdx.x; i < F2_TW; i += F2_THREADS) tw_s[i] = a.twiddle[i];
+  for (; item < ITEMS; item += gridDim.x) {
+    const F2Roles<2> q(item);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();  // this item's sectors (and the twiddles) are visible to every thread
+    const int kxhi = threadIdx.x >> 2, e = 2 * q.s + (threadIdx.x & 1);
+    cpx<float> u[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) u[k] = stage[f2p_stage(kxhi * 16 + k, e)];
+    __syncthreads();  // staging free
+    const int nxt = item + gridDim.x;
+    if (nxt < ITEMS) {
+      f2p_issue(a.data, stage, nxt);
+      f2_prefetch_psi_v<2, VREAL>(a, nxt);
+    }
+    f2_c_body<2, OP, VREAL, NEXT>(a, q, u, tile, tw_s, red_s, item);
+    __syncthreads();  // the tile is free for the next item
   }
 }
 
