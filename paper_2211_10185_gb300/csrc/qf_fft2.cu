@@ -9,9 +9,6 @@ namespace qf {
 // sectors (1 measured 12 % slower per step)
 constexpr int kF2YL = 2;
 
-// pass C as a persistent kernel (one block per SM, next item staged while computing)
-constexpr bool kF2Persistent = true;
-
 bool fft2_supported(int n) { return n == F2_N; }
 int fft2_final_blocks() { return F2AC<kF2YL>::BLOCKS; }
 
@@ -19,7 +16,6 @@ template <int OP, bool VREAL, bool NEXT>
 static void f2_attr_c() {
   cudaFuncSetAttribute(fft2_c_kernel<kF2YL, OP, VREAL, NEXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)F2AC<kF2YL>::SMEM);
-  cudaFuncSetAttribute(fft2_cp_kernel<OP, VREAL, NEXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F2P_SMEM);
 }
 
 // pass 0: natural field -> S (members' src); 1: S in place; 2: S -> update / sums (+ the
@@ -43,24 +39,14 @@ cudaError_t launch_fft2_group_pass(int pass, const FftGroup<float>& g, cudaStrea
     attr_done = true;
   }
   if (g.count < 1 || g.count > kGroupMax) return cudaErrorInvalidValue;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      sms = 148;
-  }
-  const dim3 grid_b(F2_BLOCKS, g.count), grid_ac(AC::BLOCKS, g.count), grid_p(sms, g.count);
+  const dim3 grid_b(F2_BLOCKS, g.count), grid_ac(AC::BLOCKS, g.count);
   const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0, write = g.a[0].write_psi != 0;
   const bool next = write && g.a[0].emit_next != 0;
   switch (pass) {
     case 0: fft2_a_kernel<kF2YL><<<grid_ac, AC::THREADS, AC::SMEM, st>>>(g); break;
     case 1: fft2_b_kernel<<<grid_b, F2_THREADS, F2_SMEM_B, st>>>(g); break;
     case 2:
-#define F2_C(OP, VR, NX)                                                              \
-  do {                                                                                \
-    if (kF2Persistent) fft2_cp_kernel<OP, VR, NX><<<grid_p, F2_THREADS, F2P_SMEM, st>>>(g); \
-    else fft2_c_kernel<kF2YL, OP, VR, NX><<<grid_ac, AC::THREADS, AC::SMEM, st>>>(g);         \
-  } while (0)
+#define F2_C(OP, VR, NX) fft2_c_kernel<kF2YL, OP, VR, NX><<<grid_ac, AC::THREADS, AC::SMEM, st>>>(g)
       if (!write) {
         if (vreal) F2_C(OP_SUMS, true, false);
         else F2_C(OP_SUMS, false, false);

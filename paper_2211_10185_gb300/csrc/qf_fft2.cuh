@@ -331,8 +331,10 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const
   double* red_s = reinterpret_cast<double*>(tile + LINES * F2_PL);
   const F2Roles<YL> q(blockIdx.x);
   // psi and V of the output rows are needed only after the transforms: start pulling them
-  // into L2 now, one bulk prefetch per row.  (Prefetching the next wave's rows or scratch
-  // sectors here as well measured slower: this pass already moves 36 B per site.)
+  // into L2 now, one bulk prefetch per row.  (Measured slower: prefetching the next
+  // wave's rows or scratch sectors here as well, this pass already moving 36 B per site;
+  // and a persistent form with one block per SM that stages the next item's sectors with
+  // cp.async while computing, 16 warps per SM being too few for the transforms.)
   f2_prefetch_psi_v<YL, VREAL>(a, blockIdx.x);
   for (int i = threadIdx.x; i < F2_TW; i += F2AC<YL>::THREADS) tw_s[i] = a.twiddle[i];
   cpx<float> u[16];
@@ -340,60 +342,6 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_c_kernel(const
   for (int k = 0; k < 16; ++k) u[k] = a.data[q.sbase + k * F2_SKLO];
   __syncthreads();
   f2_c_body<YL, OP, VREAL, NEXT>(a, q, u, tile, tw_s, red_s, blockIdx.x);
-}
-
-// Persistent form of pass C (two y_lo per item, one 512-thread block per SM): while an
-// item is computed, the next item's scratch sectors stream into a staging buffer with
-// cp.async (16-byte copies, no registers) and its psi and V rows into L2, so no item
-// starts by waiting on HBM.  Staging layout: row = kx_hi 16 + k_lo, 4 elements
-// (2 y_lo x 2 kx_lo) each, plus 4 elements of skew per 16 rows (conflict-free reads).
-constexpr int F2P_STAGE = 2048 * 4 + 128 * 4;
-constexpr size_t F2P_SMEM = F2_TWB + (size_t)32 * F2_PL * 8 + (size_t)F2P_STAGE * 8 + 32 * kNumSums * 8;
-__device__ __forceinline__ int f2p_stage(int row, int e) { return row * 4 + (row >> 4) * 4 + e; }
-
-__device__ __forceinline__ void f2p_issue(const cpx<float>* S, cpx<float>* stage, int item) {
-  const int z = item >> 3, p = item & 7;
-  for (int i = threadIdx.x; i < 4096; i += F2_THREADS) {
-    const int row = i >> 1, half = i & 1;
-    const cpx<float>* src = S + ((long long)row * F2_N + z) * 32 + 4 * p + 2 * half;
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(stage + f2p_stage(row, 2 * half));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-template <int OP, bool VREAL, bool NEXT>
-__global__ void __launch_bounds__(F2_THREADS, 1) fft2_cp_kernel(const __grid_constant__ FftGroup<float> gr) {
-  const FftPassArgs<float>& a = gr.a[blockIdx.y];
-  extern __shared__ __align__(16) unsigned char f2_smem[];
-  cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
-  cpx<float>* tile = reinterpret_cast<cpx<float>*>(f2_smem + F2_TWB);
-  cpx<float>* stage = tile + 32 * F2_PL;
-  double* red_s = reinterpret_cast<double*>(stage + F2P_STAGE);
-  constexpr int ITEMS = F2AC<2>::BLOCKS;
-  int item = blockIdx.x;
-  if (item < ITEMS) {
-    f2p_issue(a.data, stage, item);
-    f2_prefetch_psi_v<2, VREAL>(a, item);
-  }
-  for (int i = threadIdx.x; i < F2_TW; i += F2_THREADS) tw_s[i] = a.twiddle[i];
-  for (; item < ITEMS; item += gridDim.x) {
-    const F2Roles<2> q(item);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();  // this item's sectors (and the twiddles) are visible to every thread
-    const int kxhi = threadIdx.x >> 2, e = 2 * q.s + (threadIdx.x & 1);
-    cpx<float> u[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) u[k] = stage[f2p_stage(kxhi * 16 + k, e)];
-    __syncthreads();  // staging free
-    const int nxt = item + gridDim.x;
-    if (nxt < ITEMS) {
-      f2p_issue(a.data, stage, nxt);
-      f2_prefetch_psi_v<2, VREAL>(a, nxt);
-    }
-    f2_c_body<2, OP, VREAL, NEXT>(a, q, u, tile, tw_s, red_s, item);
-    __syncthreads();  // the tile is free for the next item
-  }
 }
 
 }  // namespace qf
