@@ -62,10 +62,11 @@ __device__ __forceinline__ void tb_plane(const CUtensorMap* map, unsigned long l
       : "memory");
 }
 
+// V at offset `off` of plane p (the plane's base address computed once per plane)
 template <bool VREAL>
-__device__ __forceinline__ cpx<float> tb_v(const StencilTbArgs& g, long long site) {
-  if constexpr (VREAL) return mk<float>(reinterpret_cast<const float*>(g.v)[site], 0.f);
-  else return reinterpret_cast<const cpx<float>*>(g.v)[site];
+__device__ __forceinline__ cpx<float> tb_v(const StencilTbArgs& g, long long plane_off, int off) {
+  if constexpr (VREAL) return mk<float>((reinterpret_cast<const float*>(g.v) + plane_off)[off], 0.f);
+  else return (reinterpret_cast<const cpx<float>*>(g.v) + plane_off)[off];
 }
 
 // VREAL: the potential is real (g.v holds floats)
@@ -106,17 +107,20 @@ __global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_
     st2[k] = ox < n && oy + k < n;
     in2[k] = st2[k] && ox >= 1 && oy + k >= 1;
   }
+  const int o2 = oy * n + ox;  // in-plane offset of this thread's first output row
   auto load_v1 = [&](int p, cpx<float>(&v)[TB_L1_PER_THREAD]) {
     const bool zin = p >= 1 && p < n;
+    const long long po = zin ? p * plane_sites : 0;
 #pragma unroll
     for (int q = 0; q < TB_L1_PER_THREAD; ++q)
-      v[q] = (zin && in1[q]) ? tb_v<VREAL>(g, p * plane_sites + gs[q]) : mk<float>(0.f, 0.f);
+      v[q] = (zin && in1[q]) ? tb_v<VREAL>(g, po, gs[q]) : mk<float>(0.f, 0.f);
   };
   auto load_v2 = [&](int p, cpx<float>(&v)[TB_ROWS]) {
     const bool zin = p >= 1 && p < n;
+    const long long po = zin ? p * plane_sites : 0;
 #pragma unroll
     for (int k = 0; k < TB_ROWS; ++k)
-      v[k] = (zin && in2[k]) ? tb_v<VREAL>(g, (p * (long long)n + oy + k) * n + ox) : mk<float>(0.f, 0.f);
+      v[k] = (zin && in2[k]) ? tb_v<VREAL>(g, po, o2 + k * n) : mk<float>(0.f, 0.f);
   };
 
   if (tid == 0) {
