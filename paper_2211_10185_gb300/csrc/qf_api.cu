@@ -1,7 +1,9 @@
 // C ABI of libqfdtd (declared in include/qfdtd.h): lattice handles over a caller-owned
 // device workspace, the step loop with its checks and snapshots, Gram-Schmidt excited
 // states and parity projection.  Every arithmetic step on fields runs in the kernels of
-// qf_fft.cu, qf_stencil.cu and qf_fields.cu; this file only sequences them.
+// qf_fft_impl.cuh (four-pass FFT step), qf_fft2.cuh (two-pass N = 256 step),
+// qf_stencil_tma.cuh / qf_stencil_tb.cuh (FDTD steps) and qf_fields.cu; this file only
+// sequences them.
 #include <math.h>
 
 #include <cmath>
