@@ -378,12 +378,22 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int i = b * RL + r;
-          // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d
+          // d = 1 + dtau V/2; coef_B = 1/d; coef_A = (2 - d)/d (FP32: the fast hardware
+          // division, a few ulp; FP64: correctly rounded)
           const cpx<R> vi = vat(i);
-          const cpx<R> d = mk<R>(R(1) + a.half_dtau * vi.x, a.half_dtau * vi.y);
-          const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), pv[i]) - cscale<R>(v[i], a.dtau);
-          const R inv = sc / (d.x * d.x + d.y * d.y);
-          v[i] = cscale<R>(cmulc<R>(num, d), inv);  // psi_{t+1}
+          if constexpr (VREAL) {
+            const R d = R(1) + a.half_dtau * vi.x;
+            const cpx<R> num = cscale<R>(pv[i], R(2) - d) - cscale<R>(v[i], a.dtau);
+            if constexpr (sizeof(R) == 4) v[i] = cscale<R>(num, __fdividef(sc, d));
+            else v[i] = cscale<R>(num, sc / d);
+          } else {
+            const cpx<R> d = mk<R>(R(1) + a.half_dtau * vi.x, a.half_dtau * vi.y);
+            const cpx<R> num = cmul<R>(mk<R>(R(2) - d.x, -d.y), pv[i]) - cscale<R>(v[i], a.dtau);
+            R inv;
+            if constexpr (sizeof(R) == 4) inv = __fdividef(sc, d.x * d.x + d.y * d.y);
+            else inv = sc / (d.x * d.x + d.y * d.y);
+            v[i] = cscale<R>(cmulc<R>(num, d), inv);
+          }  // v[i] = psi_{t+1}
           a.psi[base + e_out<N, S - 1>(g, b, r)] = v[i];
         }
       if constexpr (NEXT) {
