@@ -1,0 +1,96 @@
+"""Degenerate inputs and a closed form at the bench size, through the C ABI.
+
+* an empty run (max_steps = 0) changes nothing;
+* the zero wavefunction stays zero (norm 0: the renormalisation falls back to 1, the
+  energy is NaN) for every kinetic form, as the oracle's field does;
+* a plane wave under a constant potential is an eigenvector of every step: after n steps
+  it is multiplied by lambda^n, lambda = (1 - dtau V/2 - dtau T(k)) / (1 + dtau V/2), with
+  T(k) the kinetic symbol (Eqs. HK1-HK3) -- checked on the N=256 two-pass and four-pass
+  FFT steps without the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qfdtd_oracle as O
+from paper_2211_10185_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10185_gb300 import build
+
+    build.build()
+
+
+def _lat(n, a, kind, m, v, psi, prec="c64", dtau=None):
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    lat = Lattice(n, a, precision=prec)
+    lat.set_potential(v)
+    lat.set_kinetic(kind, m, dtau)
+    lat.set_wavefunction(psi)
+    return lat
+
+
+def test_empty_run_changes_nothing():
+    from paper_2211_10185_gb300 import qfdtd as Q
+
+    n, a = 16, 0.3
+    psi = I.gaussian_field(n, 1)
+    lat = _lat(n, a, I.FFT_SYMANZIK, 1.0, I.harmonic(n, a), psi)
+    st, done = lat.step_n(0, tol=0.0, check_every=4)
+    assert (st, done) == (Q.QF_ENOTCONV, 0)
+    assert lat.info()["step"] == 0
+    assert np.allclose(lat.get_wavefunction(), psi, rtol=0, atol=1e-6 * np.abs(psi).max())
+
+
+@pytest.mark.parametrize("kind,n", [(I.FDTD, 24), (I.FFT_NAIVE, 16), (I.FFT_REL, 256)])
+def test_zero_wavefunction_stays_zero(kind, n):
+    a = 6.0 / n
+    lat = _lat(n, a, kind, 1.0, I.cornell(n, a, 0.4, 0.2), np.zeros((n, n, n), complex))
+    lat.step_n(9, tol=0.0, check_every=4)
+    assert not lat.get_wavefunction().any()
+    e = lat.energies()
+    assert e["norm"] == 0.0 and math.isnan(e["e"].real)
+    ref = O.Lattice(n, a)
+    ref.set_potential(I.cornell(n, a, 0.4, 0.2))
+    ref.set_kinetic(kind, 1.0)
+    ref.set_wavefunction(np.zeros((n, n, n), complex))
+    ref.step_n(9, check_every=0)   # (the oracle leaves the energy of a zero field undefined)
+    assert not ref.psi.any()
+
+
+def _symbol(kind, k, a, m):
+    s2 = 4 * np.sum(np.sin(np.asarray(k) / 2) ** 2)
+    if kind == I.FFT_NAIVE:
+        return float(np.sum(np.asarray(k) ** 2)) / (2 * m * a * a)
+    if kind == I.FFT_SYMANZIK:
+        return s2 / (2 * m * a * a)
+    return math.sqrt(s2 + (a * m) ** 2) / a
+
+
+@pytest.mark.parametrize("two_pass", [True, False])
+@pytest.mark.parametrize("kind", [I.FFT_NAIVE, I.FFT_SYMANZIK, I.FFT_REL])
+def test_plane_wave_closed_form_at_n256(kind, two_pass):
+    n, a, m, v0 = 256, 0.05, 0.3, 0.7
+    nvec = (3, -5, 7)                       # momentum index per axis (x, y, z)
+    k = [2 * math.pi * j / n for j in nvec]
+    idx = np.arange(n)
+    # psi[z, y, x] = exp(i (kx x + ky y + kz z)) on the lattice indices
+    psi = np.exp(1j * (k[0] * idx[None, None, :] + k[1] * idx[None, :, None] + k[2] * idx[:, None, None]))
+    lat = _lat(n, a, kind, m, np.full((n, n, n), v0), psi)
+    lat.use_two_pass_fft(two_pass)
+    dtau = lat.info()["dtau"]
+    steps = 5
+    lat.step_n(steps, tol=0.0, check_every=0, snap_every=0)
+    lam = (1 - dtau * v0 / 2 - dtau * _symbol(kind, k, a, m)) / (1 + dtau * v0 / 2)
+    got = lat.get_wavefunction()
+    want = lam ** steps * psi
+    assert np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel()) < 2e-6 * steps * math.log2(n)
