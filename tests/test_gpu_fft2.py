@@ -134,3 +134,26 @@ def test_two_pass_batch_members_match_alone_bitwise():
     for la, lm in zip(alone, mixed):
         assert np.array_equal(la.get_wavefunction(), lm.get_wavefunction())
         assert la.energies()["e"] == lm.energies()["e"]
+
+
+def test_batch_keeps_two_and_four_pass_members_apart():
+    """Members of one size that run different step forms launch separately, and each
+    matches its own form alone bitwise."""
+    from paper_2211_10185_gb300.serve import Batch
+
+    v = _potential(False)
+    alone, mixed = [], []
+    for seed, two in ((7, True), (8, False), (9, True)):
+        psi0 = I.gaussian_field(N, seed)
+        alone.append(_lat(I.FFT_REL, v, psi0, two))
+        mixed.append(_lat(I.FFT_REL, v, psi0, two))
+    for lat in alone:
+        lat.step_n(40, tol=0.0, check_every=16, snap_every=16)
+    b = Batch()
+    for lat in mixed:
+        b.add(lat, 40, 0.0)
+    while b.step(20, check_every=16) > 0:
+        pass
+    for la, lm in zip(alone, mixed):
+        assert lm.info()["fft_passes"] == la.info()["fft_passes"]
+        assert np.array_equal(la.get_wavefunction(), lm.get_wavefunction())
