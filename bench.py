@@ -136,6 +136,34 @@ def oracle_rate(w, v, psi0, seconds, min_steps=2):
     return n ** 3 * steps / el, steps, el
 
 
+def size_sweep(name, prec, sizes=(32, 128), gpu_steps=640, cpu_seconds=2.0):
+    """The same workload at smaller N: GPU site-updates/s over ``gpu_steps`` imaginary-time
+    steps (checks every 64) against the FP64 oracle on one host core for ~``cpu_seconds``."""
+    import torch
+
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    res = {}
+    for n in sizes:
+        w = I.workload(name, n)
+        v, psi0 = make_inputs(w)
+        lat = Lattice(n, w["a"], precision=prec)
+        lat.set_potential(v)
+        lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+        lat.set_wavefunction(psi0)
+        lat.step_n(2 * CHUNK, tol=0.0, check_every=CHUNK)  # warm-up (plans, graphs, autotuning)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.step_n(gpu_steps, tol=0.0, check_every=CHUNK)
+        torch.cuda.synchronize()
+        gpu = n ** 3 * gpu_steps / (time.perf_counter() - t0)
+        lat.close()
+        cpu, steps, el = oracle_rate(w, v, psi0, cpu_seconds)
+        res[str(n)] = {"gpu_site_updates_per_s": gpu, "oracle_site_updates_per_s": cpu, "oracle_steps": steps,
+                       "oracle_cores": 1}
+    return res
+
+
 def run_reference(args):
     """The FP64 oracle as it stands, on the host cores; one bench step = one oracle
     imaginary-time step of the same workload (a check step every 64)."""
@@ -558,6 +586,11 @@ def run_ours(args):
         out["cpu_baseline"] = {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
                                "sample": f"{steps} FP64 oracle imaginary-time steps of the same N={n} workload "
                                          f"({el:.1f} s, numpy FFT, one thread)"}
+    if out is not None and world == 1 and not args.no_cpu_baseline:
+        try:
+            out["by_size"] = size_sweep(args.workload, prec)
+        except Exception as exc:
+            out["by_size"] = {"error": str(exc)[:300]}
     if out is not None:
         print(json.dumps(out), flush=True)
     lat.close()
