@@ -78,24 +78,6 @@ __device__ __forceinline__ long long f2_row(int blk, int line) {
   return ((long long)z * F2_N + y0 + (line % YL) + 16 * (line / YL)) * F2_N;
 }
 
-// x transform of the 16 elements v[r] = line element g + 16 r of this thread's line
-// (positions g + 16 r in and out), through the line tile for the stage exchange.  A line
-// belongs to 16 lanes of one warp and its tile row to those lanes alone (callers
-// separate block-wide tile use with __syncthreads), so the exchange needs only warp
-// synchronisation.
-template <bool INV>
-__device__ __forceinline__ void f2_x_transform(cpx<float> (&v)[16], int line, int g, cpx<float>* tile,
-                                               const cpx<float>* tw_s) {
-  stage_compute<float, F2_N, 0, INV>(v, g, tw_s);
-  __syncwarp();  // the line's earlier reads of its tile row are done
-#pragma unroll
-  for (int r = 0; r < 16; ++r) tile[f2_tile(line, 16 * g + r)] = v[r];
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = tile[f2_tile(line, g + 16 * r)];
-  stage_compute<float, F2_N, 1, INV>(v, g, tw_s);
-}
-
 // Second radix-16 stage of a 256-point transform for element group g (the Stockham stage
 // of stage_compute with its 15 twiddles w256^{g r}): two twiddles are read (r = 1, 8) and
 // the others formed by multiplying up by w256^g (at most six products deep, a few ulp),
@@ -111,6 +93,24 @@ __device__ __forceinline__ void f2_stage1(cpx<float> (&v)[16], int g, const cpx<
     v[r] = INV ? cmulc<float>(v[r], w) : cmul<float>(v[r], w);
   }
   dft16<float, INV>(v);
+}
+
+// x transform of the 16 elements v[r] = line element g + 16 r of this thread's line
+// (positions g + 16 r in and out), through the line tile for the stage exchange.  A line
+// belongs to 16 lanes of one warp and its tile row to those lanes alone (callers
+// separate block-wide tile use with __syncthreads), so the exchange needs only warp
+// synchronisation.
+template <bool INV>
+__device__ __forceinline__ void f2_x_transform(cpx<float> (&v)[16], int line, int g, cpx<float>* tile,
+                                               const cpx<float>* tw_s) {
+  stage_compute<float, F2_N, 0, INV>(v, g, tw_s);
+  __syncwarp();  // the line's earlier reads of its tile row are done
+#pragma unroll
+  for (int r = 0; r < 16; ++r) tile[f2_tile(line, 16 * g + r)] = v[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = tile[f2_tile(line, g + 16 * r)];
+  f2_stage1<INV>(v, g, tw_s);
 }
 
 // Thread roles in a pass-A/C block (YL consecutive y_lo of one z).
