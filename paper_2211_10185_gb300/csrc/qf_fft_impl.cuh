@@ -207,10 +207,24 @@ __device__ __forceinline__ void stage_compute(cpx<R> (&v)[plan_ept(N)], int g, c
       const int j = g + b * TL;
       const int k = j % NS;
       const cpx<R>* t = tw_s + OFF + k * (RAD - 1);
+      if constexpr (sizeof(R) == 4 && RAD >= 8) {
+        // complex FP32, radix 8 / 16: w^r formed by multiplying up from w = t[0], restarting
+        // from the table at r = 8 (at most six products deep, a few ulp), so a butterfly
+        // reads 1-2 twiddles from shared memory instead of RAD - 1
+        const cpx<R> w1 = t[0];
+        cpx<R> w = w1;
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) {
-        cpx<R> w = t[r - 1];
-        v[b * RAD + r] = INV ? cmulc<R>(v[b * RAD + r], w) : cmul<R>(v[b * RAD + r], w);
+        for (int r = 1; r < RAD; ++r) {
+          if (r == 8) w = t[7];
+          else if (r > 1) w = cmul<R>(w, w1);
+          v[b * RAD + r] = INV ? cmulc<R>(v[b * RAD + r], w) : cmul<R>(v[b * RAD + r], w);
+        }
+      } else {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) {
+          cpx<R> w = t[r - 1];
+          v[b * RAD + r] = INV ? cmulc<R>(v[b * RAD + r], w) : cmul<R>(v[b * RAD + r], w);
+        }
       }
     }
     dft<R, RAD, INV>(&v[b * RAD]);
