@@ -78,23 +78,6 @@ __device__ __forceinline__ long long f2_row(int blk, int line) {
   return ((long long)z * F2_N + y0 + (line % YL) + 16 * (line / YL)) * F2_N;
 }
 
-// Second radix-16 stage of a 256-point transform for element group g (the Stockham stage
-// of stage_compute with its 15 twiddles w256^{g r}): two twiddles are read (r = 1, 8) and
-// the others formed by multiplying up by w256^g (at most six products deep, a few ulp),
-// which spares the shared-memory pipe 13 loads per thread -- the pass-B limit.
-template <bool INV>
-__device__ __forceinline__ void f2_stage1(cpx<float> (&v)[16], int g, const cpx<float>* tw_s) {
-  const cpx<float> w1 = tw_s[F2_TW1 + g * 15], w8 = tw_s[F2_TW1 + g * 15 + 7];
-  cpx<float> w = w1;
-#pragma unroll
-  for (int r = 1; r < 16; ++r) {
-    if (r == 8) w = w8;
-    else if (r > 1) w = cmul<float>(w, w1);
-    v[r] = INV ? cmulc<float>(v[r], w) : cmul<float>(v[r], w);
-  }
-  dft16<float, INV>(v);
-}
-
 // x transform of the 16 elements v[r] = line element g + 16 r of this thread's line
 // (positions g + 16 r in and out), through the line tile for the stage exchange.  A line
 // belongs to 16 lanes of one warp and its tile row to those lanes alone (callers
@@ -110,7 +93,7 @@ __device__ __forceinline__ void f2_x_transform(cpx<float> (&v)[16], int line, in
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = tile[f2_tile(line, g + 16 * r)];
-  f2_stage1<INV>(v, g, tw_s);
+  stage_compute<float, F2_N, 1, INV>(v, g, tw_s);
 }
 
 // Thread roles in a pass-A/C block (YL consecutive y_lo of one z).
@@ -229,7 +212,7 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
-  f2_stage1<false>(v, g, tw_s);
+  stage_compute<float, F2_N, 1, false>(v, g, tw_s);
   // natural-order kz = g + 16 r; T(kx, ky, kz)/N^3
   {
     const int kx = 2 * kxhi + (c & 1), ky = klo + 16 * (c >> 1);
@@ -245,7 +228,7 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
-  f2_stage1<true>(v, g, tw_s);
+  stage_compute<float, F2_N, 1, true>(v, g, tw_s);
   __syncwarp();
 #pragma unroll
   for (int r = 0; r < 16; ++r) tile[f2_b(g + 16 * r, c)] = v[r];
