@@ -49,20 +49,9 @@ struct F2AC {
   static constexpr size_t SMEM = F2_TWB + (size_t)LINES * F2_PL * 8 + 32 * kNumSums * 8;
 };
 
-// u[k] times w256^{y_lo k} (forward) or its conjugate, k = 0..15: the stage-1 twiddle
-// block holds w256^{y_lo r}; like the transform stages, two entries are read (r = 1, 8)
-// and the rest formed by multiplying up (at most six products deep)
-template <bool CONJ>
-__device__ __forceinline__ void f2_twiddle_row(cpx<float> (&u)[16], const cpx<float>* tw_s, int ylo) {
-  const cpx<float>* t = tw_s + F2_TW1 + ylo * 15;
-  const cpx<float> w1 = t[0];
-  cpx<float> w = w1;
-#pragma unroll
-  for (int k = 1; k < 16; ++k) {
-    if (k == 8) w = t[7];
-    else if (k > 1) w = cmul<float>(w, w1);
-    u[k] = CONJ ? cmulc<float>(u[k], w) : cmul<float>(u[k], w);
-  }
+// w256^{y_lo k_lo} (forward) from the stage-1 twiddle block
+__device__ __forceinline__ cpx<float> f2_tw(const cpx<float>* tw_s, int ylo, int klo) {
+  return klo == 0 ? mk<float>(1.f, 0.f) : tw_s[F2_TW1 + ylo * 15 + klo - 1];
 }
 
 __device__ __forceinline__ int f2_tile(int line, int e) { return line * F2_PL + e + (e >> 4); }
@@ -140,9 +129,8 @@ __device__ __forceinline__ void f2_cross_fwd(const F2Roles<YL>& q, const cpx<flo
 #pragma unroll
   for (int yh = 0; yh < 16; ++yh) u[yh] = tile[f2_tile(YL * yh + q.s, q.kx)];
   dft16<float, false>(u);
-  f2_twiddle_row<false>(u, tw_s, q.ylo);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) S[q.sbase + k * F2_SKLO] = u[k];
+  for (int k = 0; k < 16; ++k) S[q.sbase + k * F2_SKLO] = cmul<float>(u[k], f2_tw(tw_s, q.ylo, k));
 }
 
 // Pass A: field `src` (natural order) -> S.
@@ -269,7 +257,8 @@ __device__ __forceinline__ void f2_c_body(const FftPassArgs<float>& a, const F2R
                                           cpx<float>* tile, const cpx<float>* tw_s, double* red_s, int item) {
   constexpr bool WRITE = (OP == OP_FINAL || OP == OP_FINAL_SUMS);
   constexpr bool SUMS = (OP == OP_FINAL_SUMS || OP == OP_SUMS);
-  f2_twiddle_row<true>(u, tw_s, q.ylo);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) u[k] = cmulc<float>(u[k], f2_tw(tw_s, q.ylo, k));
   dft16<float, true>(u);
 #pragma unroll
   for (int yh = 0; yh < 16; ++yh) tile[f2_tile(YL * yh + q.s, q.kx)] = u[yh];
