@@ -157,3 +157,50 @@ def test_batch_keeps_two_and_four_pass_members_apart():
     for la, lm in zip(alone, mixed):
         assert lm.info()["fft_passes"] == la.info()["fft_passes"]
         assert np.array_equal(la.get_wavefunction(), lm.get_wavefunction())
+
+
+def test_side_operations_between_two_pass_steps_leave_the_solve_unchanged():
+    """Momentum output, parity projection of a state slot and excited-state extraction
+    overwrite the scratch field; the next two-pass step must start again from natural
+    order and give the same field as a lattice that did none of them."""
+    v = _potential(False)
+    psi0 = I.gaussian_field(N, 21)
+    plain = _lat(I.FFT_REL, v, psi0)
+    busy = _lat(I.FFT_REL, v, psi0)
+    for lat in (plain, busy):
+        lat.step_n(193, tol=0.0, check_every=64, snap_every=64)
+    busy.momentum_distribution()
+    busy.project_excited(3)
+    busy.parity_project(O.P_MINUS, 3, 1)   # on state 1, not the live field
+    for lat in (plain, busy):
+        lat.step_n(70, tol=0.0, check_every=64, snap_every=64)
+    # (the busy lattice restarts with pass A from natural order, the other reuses the
+    # emitted scratch field: the same arithmetic in two kernels, equal to rounding)
+    assert _rel(busy.get_wavefunction(), plain.get_wavefunction()) < 1e-6
+    assert abs(busy.energies()["e"] - plain.energies()["e"]) < 1e-6 * abs(plain.energies()["e"])
+
+
+def test_prolongation_onto_a_two_pass_lattice():
+    """Warm start N=128 -> 256: the prolonged field keeps the coarse values on coincident
+    sites, and the two-pass steps from it match the four-pass steps."""
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    nc, ac = N // 2, 2 * A
+    coarse = Lattice(nc, ac, precision="c64")
+    coarse.set_potential(I.cornell(nc, ac, 0.4, 0.2))
+    coarse.set_kinetic(I.FFT_REL, 0.3, A / 4)
+    coarse.set_wavefunction(I.gaussian_field(nc, 4))
+    coarse.step_n(64, tol=0.0, check_every=32)
+    psi_c = coarse.get_wavefunction()
+    fines = []
+    for two in (True, False):
+        fine = _lat(I.FFT_REL, _potential(False), np.zeros((N, N, N), complex), two)
+        fine.prolong_from(coarse)
+        fines.append(fine)
+    got = fines[0].get_wavefunction()
+    # coincident sites carry the coarse values (exact up to the FP32 transforms)
+    assert np.abs(got[::2, ::2, ::2] - psi_c).max() < 1e-5 * np.abs(psi_c).max()
+    assert np.array_equal(got, fines[1].get_wavefunction())
+    for f in fines:
+        f.step_n(20, tol=0.0, check_every=10)
+    assert _rel(fines[0].get_wavefunction(), fines[1].get_wavefunction()) < 1e-5
