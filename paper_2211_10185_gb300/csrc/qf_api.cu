@@ -308,6 +308,16 @@ extern "C" qf_status qf_destroy_lattice(qf_lattice* lat) {
 // after each chunk.
 template <typename F>
 static qf_status staged_upload(qf_lattice* lat, const double* host, long long n, long long per_item, F fn) {
+  // page-locked host memory is read by the conversion kernel itself over the host link,
+  // in one launch (no staging copies, one synchronisation)
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, host) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+      attr.devicePointer != nullptr) {
+    QF_CUDA(lat, launch(lat, K_CONVERT, [&] { return fn(reinterpret_cast<double*>(attr.devicePointer), 0, n); }));
+    QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+    return QF_OK;
+  }
+  cudaGetLastError();  // (a pageable pointer is not an error)
   const long long chunk = (long long)(lat->L.stage_bytes / sizeof(double)) / per_item;
   for (long long first = 0; first < n; first += chunk) {
     const long long cnt = (n - first < chunk) ? n - first : chunk;

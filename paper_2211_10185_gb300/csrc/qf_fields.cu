@@ -279,11 +279,22 @@ cudaError_t launch_parity(cpx<R>* dst, const cpx<R>* src, int n, int which, int 
 // ------------------------------------------------------------------------------------
 // Precision conversion at the host boundary
 // ------------------------------------------------------------------------------------
+// src may be device memory (the staging area) or page-locked host memory read over the
+// host link, where 16-byte loads (when src is 16-byte aligned) move twice the data per
+// request
 template <typename R>
 __global__ void from_f64_kernel(cpx<R>* dst, const double* __restrict__ src, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    dst[i] = mk<R>(R(src[2 * i]), R(src[2 * i + 1]));
+  if ((reinterpret_cast<unsigned long long>(src) & 15) == 0) {
+    const double2* __restrict__ s2 = reinterpret_cast<const double2*>(src);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const double2 w = s2[i];
+      dst[i] = mk<R>(R(w.x), R(w.y));
+    }
+  } else {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+      dst[i] = mk<R>(R(src[2 * i]), R(src[2 * i + 1]));
+  }
 }
 template <typename R>
 cudaError_t launch_from_f64(cpx<R>* dst, const double* src, long long n, cudaStream_t st) {
