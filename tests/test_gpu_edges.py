@@ -94,3 +94,22 @@ def test_plane_wave_closed_form_at_n256(kind, two_pass):
     got = lat.get_wavefunction()
     want = lam ** steps * psi
     assert np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel()) < 2e-6 * steps * math.log2(n)
+
+
+@pytest.mark.parametrize("prec,offset", [("c64", 0), ("c128", 0), ("c64", 1)])
+def test_upload_from_page_locked_memory_matches_pageable(prec, offset):
+    """qf_set_wavefunction reads page-locked host buffers directly from the GPU; the field
+    must equal the one uploaded from ordinary (pageable) memory, also for a buffer that is
+    only 8-byte aligned."""
+    import torch
+
+    n, a = 24, 0.3
+    psi = I.gaussian_field(n, 3)
+    flat = np.ascontiguousarray(psi.reshape(-1)).view(np.float64)
+    pinned = torch.empty(2 * n ** 3 + 1, dtype=torch.float64, pin_memory=True)
+    view = pinned.numpy()[offset:offset + 2 * n ** 3]
+    view[:] = flat
+    one = _lat(n, a, I.FFT_SYMANZIK, 1.0, I.harmonic(n, a), psi, prec)
+    two = _lat(n, a, I.FFT_SYMANZIK, 1.0, I.harmonic(n, a), np.zeros_like(psi), prec)
+    two.set_wavefunction_raw(view)
+    assert np.array_equal(one.get_wavefunction(), two.get_wavefunction())
