@@ -518,8 +518,15 @@ def run_ours(args):
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
                 "traffic_source": tsrc}
-    step_bytes = (3 * (8 if prec == "c64" else 16) + ((4 if prec == "c64" else 8) if v_real else (8 if prec == "c64" else 16)))
+    # minimum bytes of one step: read psi and V, write psi'
+    c = 8 if prec == "c64" else 16
+    step_bytes = 2 * c + ((c // 2) if v_real else c)
     step_frac = step_bytes * units_per_rank / (ms_total * 1e-3) / 1e9 / peak
+    # design bytes of a steady-state step: the per-launch bytes of the kernels one step
+    # launches (from the live profile: launches per step of each kernel kind)
+    steps_timed = CHUNK * args.steps
+    design = sum(bytes_per_site(k, prec, v_real) * cnt / steps_timed
+                 for k, (cnt, _) in prof.items() if bytes_per_site(k, prec, v_real))
 
     out = None
     if rank == 0:
@@ -535,7 +542,11 @@ def run_ours(args):
             "profiled_region_ms_per_step": ms_prof / args.steps,
             "step_algorithmic_hbm": {"bytes_per_site_update": step_bytes,
                                      "frac_of_peak": step_frac,
-                                     "note": "minimum bytes of one step (read psi, V; write psi') / step time"},
+                                     "design_bytes_per_site_update": design,
+                                     "field_passes_per_step": design / c,
+                                     "note": "minimum bytes of one step (read psi, V; write psi') / bench-step "
+                                             "time; design bytes: the step's kernels (GS and parity passes "
+                                             "excluded), averaged over the timed steps"},
             "gpu_launches": launches,
             "clocks": clk,
             "energies_last_step": [e["e"].real for e in ex],
