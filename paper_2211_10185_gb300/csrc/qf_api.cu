@@ -25,6 +25,7 @@ bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64);
 bool encode_tb_map(CUtensorMap* map, void* field, int n);
 bool fft2_supported(int n);
 int fft2_final_blocks();
+int fft2_measure_blocks();
 cudaError_t launch_fft2_group_pass(int pass, const FftGroup<float>& g, cudaStream_t st);
 cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st);
 cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st);
@@ -48,13 +49,14 @@ static size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 enum KernelKind {
   K_FFT_X_FWD = 0, K_FFT_Y_FWD, K_FFT_Z_MID, K_FFT_Y_INV, K_FFT_X_INV_UPDATE, K_STENCIL, K_FINISH, K_GS_DOTS,
   K_GS_AXPY, K_SCALE_COPY, K_PARITY, K_CONVERT, K_FFT_X_INV_SUMS, K_STENCIL_SUMS, K_STENCIL_2STEP, K_FFT2_XY_FWD,
-  K_FFT2_YZ_MID, K_FFT2_XY_INV_UPDATE, K_FFT2_XY_INV_SUMS, K_NUM_KINDS
+  K_FFT2_YZ_MID, K_FFT2_XY_INV_UPDATE, K_FFT2_XY_INV_SUMS, K_FFT2_XY_FWD_SUMS, K_FFT2_YZ_SUMS, K_NUM_KINDS
 };
 static const char* kKindNames[K_NUM_KINDS] = {"fft_x_fwd", "fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
                                                "fft_x_inv_update", "stencil_step", "finish_sums", "gs_dots",
                                                "gs_axpy", "scale_copy", "parity", "convert", "fft_x_inv_sums",
                                                "stencil_sums", "stencil_2step", "fft2_xy_fwd", "fft2_yz_mid_T",
-                                               "fft2_xy_inv_update", "fft2_xy_inv_sums"};
+                                               "fft2_xy_inv_update", "fft2_xy_inv_sums", "fft2_xy_fwd_sums",
+                                               "fft2_yz_sums"};
 static const int kEventPool = 4096;
 
 struct Layout {
@@ -688,6 +690,19 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
   const bool live = write && in == lat->psi();
   const int first = (live && lat->xfwd_valid) ? 1 : 0;
   lat->xfwd_valid = false;
+  if (uses_fft2(lat) && !write) {
+    // energy of a field that is not stepped: <v|v> and <v|V v> in pass A, <v|H_K v> in
+    // k-space (Parseval) in the forward half of pass B; no inverse transforms
+    FftGroup<float> g;
+    g.count = 1;
+    g.a[0] = fft_args<float>(lat, in, false, true, scale);
+    g.a[0].src = reinterpret_cast<const cpx<float>*>(in);
+    if (nblocks) *nblocks = fft2_measure_blocks();
+    cudaError_t e = launch(lat, K_FFT2_XY_FWD_SUMS, [&] { return launch_fft2_group_pass(3, g, lat->st); });
+    if (e != cudaSuccess) return e;
+    g.a[0].src = nullptr;
+    return launch(lat, K_FFT2_YZ_SUMS, [&] { return launch_fft2_group_pass(4, g, lat->st); });
+  }
   if (uses_fft2(lat)) {
     // two-pass step: A (natural -> scratch; skipped when the previous step emitted it),
     // B, C; every launch a group of one

@@ -11,6 +11,8 @@ constexpr int kF2YL = 2;
 
 bool fft2_supported(int n) { return n == F2_N; }
 int fft2_final_blocks() { return F2AC<kF2YL>::BLOCKS; }
+// partial rows of a measure (passes 3 and 4): pass A rows, then pass B rows
+int fft2_measure_blocks() { return F2AC<kF2YL>::BLOCKS + F2_BLOCKS; }
 
 template <int OP, bool VREAL, bool NEXT>
 static void f2_attr_c() {
@@ -19,13 +21,17 @@ static void f2_attr_c() {
 }
 
 // pass 0: natural field -> S (members' src); 1: S in place; 2: S -> update / sums (+ the
-// next step's pass 0 when emit_next).  The pass-2 variant follows member 0.
+// next step's pass 0 when emit_next).  The pass-2 variant follows member 0.  Energy of a
+// field that is not stepped: 3 = pass 0 with <v|v>, <v|V v> sums, 4 = forward half of
+// pass 1 with the k-space <v|H_K v> sums (nothing written back).
 cudaError_t launch_fft2_group_pass(int pass, const FftGroup<float>& g, cudaStream_t st) {
   using AC = F2AC<kF2YL>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(fft2_a_kernel<kF2YL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AC::SMEM);
-    cudaFuncSetAttribute(fft2_b_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F2_SMEM_B);
+    cudaFuncSetAttribute(fft2_a_kernel<kF2YL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AC::SMEM);
+    cudaFuncSetAttribute(fft2_a_kernel<kF2YL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AC::SMEM);
+    cudaFuncSetAttribute(fft2_b_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F2_SMEM_B);
+    cudaFuncSetAttribute(fft2_b_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)F2_SMEM_B);
     f2_attr_c<OP_FINAL, true, true>();
     f2_attr_c<OP_FINAL, true, false>();
     f2_attr_c<OP_FINAL, false, true>();
@@ -43,8 +49,10 @@ cudaError_t launch_fft2_group_pass(int pass, const FftGroup<float>& g, cudaStrea
   const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0, write = g.a[0].write_psi != 0;
   const bool next = write && g.a[0].emit_next != 0;
   switch (pass) {
-    case 0: fft2_a_kernel<kF2YL><<<grid_ac, AC::THREADS, AC::SMEM, st>>>(g); break;
-    case 1: fft2_b_kernel<<<grid_b, F2_THREADS, F2_SMEM_B, st>>>(g); break;
+    case 0: fft2_a_kernel<kF2YL, false><<<grid_ac, AC::THREADS, AC::SMEM, st>>>(g); break;
+    case 1: fft2_b_kernel<false><<<grid_b, F2_THREADS, F2_SMEM_B, st>>>(g, 0); break;
+    case 3: fft2_a_kernel<kF2YL, true><<<grid_ac, AC::THREADS, AC::SMEM, st>>>(g); break;
+    case 4: fft2_b_kernel<true><<<grid_b, F2_THREADS, F2_SMEM_B, st>>>(g, AC::BLOCKS); break;
     case 2:
 #define F2_C(OP, VR, NX) fft2_c_kernel<kF2YL, OP, VR, NX><<<grid_ac, AC::THREADS, AC::SMEM, st>>>(g)
       if (!write) {

@@ -37,7 +37,7 @@ constexpr int F2_TW = plan_tw_size(F2_N);             // 255 per-stage twiddles
 constexpr int F2_TW1 = plan_tw_off(F2_N, 1);          // stage-1 block: w256^{k r}
 constexpr int F2_TWB = (F2_TW * 8 + 15) / 16 * 16;    // twiddle bytes in shared memory
 constexpr int F2_BTILE = F2_N * F2_BP + F2_N / 16;    // B tile elements (with the row skew)
-constexpr size_t F2_SMEM_B = F2_TWB + F2_N * 4 + (size_t)F2_BTILE * 8;
+constexpr size_t F2_SMEM_B = F2_TWB + F2_N * 4 + (size_t)F2_BTILE * 8 + 32 * kNumSums * 8;
 constexpr long long F2_SKLO = (long long)F2_N * 32;   // S stride of k_lo
 
 // pass A / C geometry for YL y_lo per block
@@ -133,8 +133,10 @@ __device__ __forceinline__ void f2_cross_fwd(const F2Roles<YL>& q, const cpx<flo
   for (int k = 0; k < 16; ++k) S[q.sbase + k * F2_SKLO] = cmul<float>(u[k], f2_tw(tw_s, q.ylo, k));
 }
 
-// Pass A: field `src` (natural order) -> S.
-template <int YL>
+// Pass A: field `src` (natural order) -> S.  With SUMS (energy of a field that is not
+// stepped): also <src|src> and <src|V src> of its sites into partial row blockIdx.x; the
+// kinetic part comes from pass B in k-space.
+template <int YL, bool SUMS = false>
 __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_a_kernel(const __grid_constant__ FftGroup<float> gr) {
   const FftPassArgs<float>& a = gr.a[blockIdx.y];
   extern __shared__ __align__(16) unsigned char f2_smem[];
@@ -145,6 +147,16 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_a_kernel(const
   cpx<float> v[16];
 #pragma unroll
   for (int r = 0; r < 16; ++r) v[r] = src[q.row + q.g + 16 * r];
+  CheckSums<float> cs;
+  if constexpr (SUMS) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const long long site = q.row + q.g + 16 * r;
+      const cpx<float> vi = a.v_real ? mk<float>(reinterpret_cast<const float*>(a.v)[site], 0.f)
+                                     : reinterpret_cast<const cpx<float>*>(a.v)[site];
+      cs.add(v[r], mk<float>(0.f, 0.f), vi);
+    }
+  }
   {
     const int nb = f2_next_wave_block();
     if (nb < (int)gridDim.x && threadIdx.x < F2AC<YL>::LINES)
@@ -158,12 +170,23 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_a_kernel(const
   for (int r = 0; r < 16; ++r) tile[f2_tile(q.line, q.g + 16 * r)] = v[r];
   __syncthreads();
   f2_cross_fwd<YL>(q, tile, tw_s, a.data);
+  if constexpr (SUMS) {
+    double acc[kNumSums];
+    cs.to(acc);
+    block_sum_store<kNumSums>(acc, reinterpret_cast<double*>(tile + F2AC<YL>::LINES * F2_PL),
+                              a.partials + (long long)blockIdx.x * kPartialStride);
+  }
 }
 
 // Pass B: S in place (one (kx_hi, k_lo) block of 8192 contiguous elements), staged
 // through shared memory with coalesced 16-byte accesses.  (Reading the outer y DFTs'
 // strided inputs straight from global memory measured 1.8x slower.)
-__global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_constant__ FftGroup<float> gr) {
+// With SUMS (energy of a field that is not stepped): after the forward transforms,
+// <v|H_K v> = sum_k T(k)/N^3 |v^(k)|^2 (Parseval) into partial row row0 + blockIdx.x, and
+// nothing is written back.
+template <bool SUMS = false>
+__global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_constant__ FftGroup<float> gr,
+                                                               int row0 = 0) {
   const FftPassArgs<float>& a = gr.a[blockIdx.y];
   extern __shared__ __align__(16) unsigned char f2_smem[];
   cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
@@ -217,6 +240,19 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
   {
     const int kx = 2 * kxhi + (c & 1), ky = klo + 16 * (c >> 1);
     const float sxy = sym_s[kx] + sym_s[ky];
+    if constexpr (SUMS) {
+      CheckSums<float> cs;
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        cs.add(v[r], cscale<float>(v[r], kin_mult<float>(a.kinetic, sxy, sym_s[g + 16 * r], a.tcoef, a.am2)),
+               mk<float>(0.f, 0.f));
+      double acc[kNumSums];
+      cs.to(acc);
+      acc[0] = acc[3] = acc[4] = 0.0;  // norm and potential terms come from pass A
+      block_sum_store<kNumSums>(acc, reinterpret_cast<double*>(tile + F2_BTILE),
+                                a.partials + (long long)(row0 + blockIdx.x) * kPartialStride);
+      return;
+    }
 #pragma unroll
     for (int r = 0; r < 16; ++r)
       v[r] = cscale<float>(v[r], kin_mult<float>(a.kinetic, sxy, sym_s[g + 16 * r], a.tcoef, a.am2));
