@@ -538,3 +538,29 @@ def test_prolongation_keeps_coarse_values_and_band_limited_functions():
     fny = O.prolong(nyq + 0j)
     assert np.max(np.abs(fny.imag)) < 1e-13
     assert np.max(np.abs(fny[::2, ::2, ::2] - nyq)) < 1e-13
+
+
+@pytest.mark.parametrize("kind", [O.FFT_NAIVE, O.FFT_SYMANZIK, O.FFT_REL])
+def test_kinetic_energy_in_k_space_equals_real_space(kind):
+    """Parseval: <v|H_K v> computed in position space (inverse transform, then the
+    Hermitian inner product) equals sum_k T(k) |v^(k)|^2 / N^3 with the unnormalised
+    forward DFT -- the identity the GPU uses for the energies of excited states.  A
+    dropped 1/N^3, a conjugate or a symbol on the wrong axis order fails it."""
+    rng = np.random.default_rng(11)
+    for n in (8, 12):
+        a, m = 0.3, 0.7
+        v = rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))
+        real_space = np.vdot(v, O.apply_kinetic_fft(v, kind, a, m))
+        k_space = np.sum(O.kinetic_symbol(kind, n, a, m) * np.abs(np.fft.fftn(v)) ** 2) / n ** 3
+        assert abs(real_space.imag) < 1e-10 * abs(real_space)
+        assert abs(real_space.real - k_space) < 1e-12 * abs(k_space)
+    # a plane wave with a different momentum on each axis: the energy is the symbol at
+    # exactly that (kx, ky, kz), written out here from Eqs. HK1-HK3
+    j = np.arange(16)
+    kx, ky, kz = 2 * np.pi * np.array([1, 2, 3]) / 16
+    pw = np.exp(1j * (kx * j[None, None, :] + ky * j[None, :, None] + kz * j[:, None, None]))
+    e = np.vdot(pw, O.apply_kinetic_fft(pw, kind, 0.3, 0.7)).real / np.vdot(pw, pw).real
+    sym = {O.FFT_NAIVE: (kx ** 2 + ky ** 2 + kz ** 2) / (2 * 0.09 * 0.7),
+           O.FFT_SYMANZIK: 4 * (np.sin(kx / 2) ** 2 + np.sin(ky / 2) ** 2 + np.sin(kz / 2) ** 2) / (2 * 0.09 * 0.7),
+           O.FFT_REL: np.sqrt(4 * (np.sin(kx / 2) ** 2 + np.sin(ky / 2) ** 2 + np.sin(kz / 2) ** 2) + 0.21 ** 2) / 0.3}
+    assert abs(e - sym[kind]) < 1e-10 * sym[kind]
