@@ -33,6 +33,10 @@ Readings of points the paper leaves open (each marked "reading" below):
     step is multiplied by 1/sqrt(n_t).  The map is linear, so this only rescales.
   * Excited states (Sec. 1, "nearby temporal snapshots ... orthogonal projection"):
     classical Gram-Schmidt, latest snapshot first, with one re-orthogonalisation pass.
+  * Which tau to report an excited-state energy at (Sec. 4 asks for the saddle point of
+    E_i(tau)): E_i is recorded at a sequence of snapshot sets j, and the reported value
+    is E_i(tau_j) at the j >= 1 that minimises |E_i(tau_j) - E_i(tau_{j-1})| (the
+    earliest such j on ties), chosen for each state i separately.
   * P^-_{p_k} (Sec. 3) is used with the factor 1/4 and renormalised afterwards; the
     other axes than k flip together.
   * Default dtau = 0.75 / T_max with T_max = 6/(m a^2) (HK0, HK2), 3 pi^2/(2 m a^2)
@@ -224,6 +228,17 @@ def gram_schmidt(vectors):
     return basis
 
 
+def plateau_index(energies) -> int | None:
+    """Index j >= 1 of the sequence E(tau_0), E(tau_1), ... that minimises
+    |E(tau_j) - E(tau_{j-1})| (the earliest on ties); None for fewer than two values."""
+    best, best_j = math.inf, None
+    for j in range(1, len(energies)):
+        d = abs(energies[j] - energies[j - 1])
+        if d < best:
+            best, best_j = d, j
+    return best_j
+
+
 # --------------------------------------------------------------------------------------
 # The solver state machine (what the C ABI exposes), Sec. 2
 # --------------------------------------------------------------------------------------
@@ -249,6 +264,8 @@ class Lattice:
         self.states = [None, None, None]
         self.state_energies = [None, None, None]
         self.history = []           # every check record
+        self.excited_history = []   # one record per track_excited(): step, tau, [E_i]
+        self.plateau = [None, None, None]   # per state: chosen record, energy, state
 
     # -- set-up ------------------------------------------------------------------------
     def set_potential(self, v_re, v_im=None):
@@ -341,6 +358,36 @@ class Lattice:
             self.state_energies[i] = rec
             out.append(rec)
         return OK, out
+
+    # -- plateau of E_i(tau) (Sec. 4: the saddle point of the excited-state energies) ----
+    def track_excited(self, n_states: int):
+        """Gram-Schmidt of the latest ``n_states`` snapshots now (``project_excited``) and
+        one record E_i(tau_j) appended to ``excited_history``.  For each state i the
+        running choice is updated: record j >= 1 replaces the current choice when
+        |E_i(tau_j) - E_i(tau_{j-1})| is strictly smaller than the choice's difference
+        (so the earliest minimiser wins), and the state v_i of record j is kept with it."""
+        st, out = self.project_excited(n_states)
+        if st != OK:
+            return st, None
+        rec = dict(step=self.step, tau=self.tau, e=[r["e"] for r in out])
+        self.excited_history.append(rec)
+        j = len(self.excited_history) - 1
+        if j >= 1:
+            prev = self.excited_history[j - 1]["e"]
+            for i in range(n_states):
+                if i >= len(prev):
+                    continue
+                d = abs(rec["e"][i] - prev[i])
+                best = self.plateau[i]
+                if best is None or d < best["de"]:
+                    self.plateau[i] = dict(index=j, step=rec["step"], tau=rec["tau"], e=rec["e"][i], de=d,
+                                           state=self.states[i].copy())
+        return OK, out
+
+    def excited_plateau(self, n_states: int):
+        """Per state i < n_states, the record chosen by ``track_excited``: dict(index,
+        step, tau, e, de, state); None for a state with fewer than two records."""
+        return [self.plateau[i] for i in range(n_states)]
 
     # -- parity ------------------------------------------------------------------------
     def parity_project(self, which: int, axis: int = 3, target: int = -1):

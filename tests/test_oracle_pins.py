@@ -564,3 +564,62 @@ def test_kinetic_energy_in_k_space_equals_real_space(kind):
            O.FFT_SYMANZIK: 4 * (np.sin(kx / 2) ** 2 + np.sin(ky / 2) ** 2 + np.sin(kz / 2) ** 2) / (2 * 0.09 * 0.7),
            O.FFT_REL: np.sqrt(4 * (np.sin(kx / 2) ** 2 + np.sin(ky / 2) ** 2 + np.sin(kz / 2) ** 2) + 0.21 ** 2) / 0.3}
     assert abs(e - sym[kind]) < 1e-10 * sym[kind]
+
+
+# ----------------------------------------------------------------------------------
+# The plateau ("saddle point") of E_i(tau), Sec. 4: the reported excited-state energy
+# ----------------------------------------------------------------------------------
+
+def test_plateau_index_on_hand_made_sequences():
+    # differences 2, .5, .1, .05, 6.55: the flattest step ends at index 4
+    assert O.plateau_index([5.0, 3.0, 2.5, 2.4, 2.45, 9.0]) == 4
+    # ties: the earliest minimiser; complex values by modulus
+    assert O.plateau_index([1.0, 1.0, 1.0]) == 1
+    assert O.plateau_index([1 + 1j, 1 + 0.5j, 1 + 0.6j, 2 + 0j]) == 2
+    assert O.plateau_index([1.0]) is None and O.plateau_index([]) is None
+
+
+def test_plateau_picks_the_exact_first_excited_level_of_the_oscillator():
+    """Snapshots every 64 steps (delta (E1 - E0) ~ 0.7) of the Dirichlet oscillator up to
+    tau ~ 43: early records carry the higher states, late ones have lost Psi_1 below FP64
+    rounding (weight e^-tau).  The chosen E_1 must be the fixed point of the step for a
+    first excited state (the self-consistent dense 1D eigensolve) to 1e-9, where neither
+    the earliest nor the latest record is within 1e-3."""
+    n, a, m = 16, 0.3, 1.0
+    dtau = a * a / 8
+    lat = O.Lattice(n, a)
+    lat.set_potential(I.harmonic(n, a))
+    lat.set_kinetic(O.FDTD, m, dtau)
+    lat.set_wavefunction(I.gaussian_field(n, 0))
+    for j in range(60):
+        lat.step_n(64, check_every=64, snap_every=64)
+        if j >= 2:
+            assert lat.track_excited(3)[0] == O.OK
+    rq0, _ = _fixed_point_rq(n, a, m, dtau, (0, 0, 0))
+    rq1, _ = _fixed_point_rq(n, a, m, dtau, (0, 0, 1))
+    hist = lat.excited_history
+    e1 = [r["e"][1] for r in hist]
+    p0, p1, p2 = lat.excited_plateau(3)
+    assert abs(p0["e"] - rq0) < 1e-12
+    assert abs(p1["e"] - rq1) < 1e-9
+    assert abs(e1[0] - rq1) > 1e-3 and abs(e1[-1] - rq1) > 1e-3
+    # the running choice equals the plain argmin over the recorded sequence
+    assert p1["index"] == O.plateau_index(e1)
+    assert p1["e"] == e1[p1["index"]] and p1["step"] == hist[p1["index"]]["step"]
+    # the kept state is the Gram-Schmidt state of that record: an eigenvector of the step
+    # map psi -> coef_A psi - coef_B dtau H_K psi (written out here from Eq. HK0's stencil)
+    v = p1["state"]
+    pad = np.pad(v, 1)
+    lap = sum(np.roll(pad, s, axis=ax) for ax in range(3) for s in (1, -1))[1:-1, 1:-1, 1:-1] - 6 * v
+    mask = O.dirichlet_mask(n)
+    hk = -lap / (2 * m * a * a) * mask
+    d = 1 + dtau * lat.v / 2
+    mv = ((2 - d) * v - dtau * hk) / d * mask
+    lam = np.vdot(v, mv) / np.vdot(v, v)
+    assert np.linalg.norm((mv - lam * v).ravel()) / np.linalg.norm(v.ravel()) < 1e-7
+    # E_2 lies in the (lattice-split) n = 2 band of the oscillator
+    x = (np.arange(1, n) - n // 2) * a
+    T = (2 * np.eye(n - 1) - np.eye(n - 1, k=1) - np.eye(n - 1, k=-1)) / (2 * m * a * a)
+    w = np.linalg.eigvalsh(T + np.diag(0.5 * x * x))
+    band = sorted([2 * w[0] + w[2], w[0] + 2 * w[1]])
+    assert band[0] - 0.02 < p2["e"].real < band[1] + 0.02
