@@ -29,6 +29,11 @@ Readings of points the paper leaves open (each marked "reading" below):
   * Energies are Rayleigh quotients <psi|H|psi>/<psi|psi> (complex for complex V),
     measured every ``check_every`` steps on the step's input psi; the convergence test
     is |E_t - E_{t-check_every}| < tol (complex modulus).
+  * A second stopping rule for solves served in batches ("extrapolated"): the check
+    energies approach their limit geometrically, so with d = |E_t - E_{t-check_every}|,
+    the previous check's d_prev > d and rho = d / d_prev, the distance left is about
+    d rho / (1 - rho); converged when max(d, d rho / (1 - rho)) < tol (d = 0 counts as
+    converged; never while d >= d_prev).
   * Renormalisation: after a check on psi_t with norm n_t the output of the following
     step is multiplied by 1/sqrt(n_t).  The map is linear, so this only rescales.
   * Excited states (Sec. 1, "nearby temporal snapshots ... orthogonal projection"):
@@ -156,6 +161,22 @@ def energy(psi, v, kind, a, m):
     return (ek + ev) / norm, norm
 
 
+def check_converged(rule: str, d: float, d_prev: float, tol: float) -> bool:
+    """Stopping test of a check with energy difference d (previous check's d_prev):
+    "difference": d < tol; "extrapolated": max(d, d rho/(1 - rho)) < tol with
+    rho = d / d_prev while d < d_prev (d = 0 converged), else not converged."""
+    if not math.isfinite(d):
+        return False
+    if rule == "difference":
+        return d < tol
+    if d == 0.0:
+        return True
+    if not math.isfinite(d_prev) or not d < d_prev:
+        return False
+    rho = d / d_prev
+    return max(d, d * rho / (1.0 - rho)) < tol
+
+
 # --------------------------------------------------------------------------------------
 # Parity projectors, Sec. 3
 # --------------------------------------------------------------------------------------
@@ -260,6 +281,7 @@ class Lattice:
         self.pending_scale = None
         self.last = None            # last check: dict(e, norm, de, step, tau)
         self.prev_e = None
+        self.prev_de = math.inf     # energy difference at the previous check
         self.snaps = []             # latest first
         self.states = [None, None, None]
         self.state_energies = [None, None, None]
@@ -289,14 +311,15 @@ class Lattice:
         return apply_kinetic(psi, self.kind, self.a, self.m)
 
     def step_n(self, max_steps: int, tol: float = 0.0, check_every: int = 64,
-               snap_every: int | None = None):
+               snap_every: int | None = None, tol_rel: float = 0.0, rule: str = "difference"):
         """Advance up to ``max_steps`` steps; returns (status, steps_done).
 
         Step t (0-based, counted over the lattice's life) maps psi_t to
         psi_{t+1} = coef_A psi_t - coef_B dtau H_K psi_t.  When t % check_every == 0 the
-        energy of psi_t is measured first; the run stops with OK after a check whose
-        |E_t - E_{t-check_every}| < tol.  After step t, when (t+1) % snap_every == 0,
-        psi_{t+1} is pushed into the snapshot ring (latest first).
+        energy of psi_t is measured first; the run stops with OK after a check that meets
+        ``check_converged(rule, |E_t - E_{t-check_every}|, previous difference,
+        tol + tol_rel |E_t|)``.  After step t, when (t+1) % snap_every == 0, psi_{t+1} is
+        pushed into the snapshot ring (latest first).
         """
         if self.v is None or self.kind is None or self.psi is None:
             return ESTATE, 0
@@ -334,8 +357,9 @@ class Lattice:
                 self.snaps.insert(0, self.psi.copy())
                 del self.snaps[self.n_snap:]
             if check:
-                converged = self.prev_e is not None and de < tol
+                converged = check_converged(rule, de, self.prev_de, tol + tol_rel * abs(e))
                 self.prev_e = e
+                self.prev_de = de
                 if converged:
                     status = OK
                     break

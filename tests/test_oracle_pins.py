@@ -623,3 +623,59 @@ def test_plateau_picks_the_exact_first_excited_level_of_the_oscillator():
     w = np.linalg.eigvalsh(T + np.diag(0.5 * x * x))
     band = sorted([2 * w[0] + w[2], w[0] + 2 * w[1]])
     assert band[0] - 0.02 < p2["e"].real < band[1] + 0.02
+
+
+# ----------------------------------------------------------------------------------
+# Stopping rules (the paper has none; readings): difference and extrapolated
+# ----------------------------------------------------------------------------------
+
+def _stop_index(rule, energies, tol):
+    d_prev, prev = math.inf, None
+    for j, e in enumerate(energies):
+        d = abs(e - prev) if prev is not None else math.inf
+        if O.check_converged(rule, d, d_prev, tol):
+            return j
+        prev, d_prev = e, d
+    return None
+
+
+def test_extrapolated_rule_bounds_the_distance_to_the_limit():
+    # a slowly contracting sequence E_j = 1 + 0.01 * 0.99^j: the difference rule stops
+    # where the distance left is ~99 x tol; the extrapolated rule within tol
+    tol = 1e-6
+    seq = [1.0 + 0.01 * 0.99 ** j for j in range(3000)]
+    jd = _stop_index("difference", seq, tol)
+    je = _stop_index("extrapolated", seq, tol)
+    assert seq[jd] - 1.0 > 50 * tol
+    assert seq[je] - 1.0 < tol and je > jd
+    # a fast one (rho = 0.1): both stop right away, at the same check
+    fast = [2.0 + 0.5 * 0.1 ** j for j in range(40)]
+    assert _stop_index("extrapolated", fast, tol) == _stop_index("difference", fast, tol)
+    # an exact repeat converges; a growing difference never does
+    assert O.check_converged("extrapolated", 0.0, math.inf, tol)
+    assert not O.check_converged("extrapolated", 1e-9, 1e-10, tol)
+    assert not O.check_converged("extrapolated", 1e-9, math.inf, tol)
+
+
+def test_extrapolated_rule_in_a_solve_stops_near_the_converged_energy():
+    n, a, m = 16, 0.3, 1.0
+    dtau = a * a / 8
+    ref = O.Lattice(n, a)
+    ref.set_potential(I.harmonic(n, a))
+    ref.set_kinetic(O.FDTD, m, dtau)
+    ref.set_wavefunction(I.gaussian_field(n, 0))
+    ref.step_n(40 * 64, tol=1e-14, check_every=64)
+    e_inf = ref.energies()["e"].real
+    for rule in ("difference", "extrapolated"):
+        lat = O.Lattice(n, a)
+        lat.set_potential(I.harmonic(n, a))
+        lat.set_kinetic(O.FDTD, m, dtau)
+        lat.set_wavefunction(I.gaussian_field(n, 0))
+        # check every 8 steps: slow contraction per check (rho ~ exp(-8 dtau (E1 - E0)))
+        st, done = lat.step_n(40000, tol=0.0, tol_rel=1e-6, check_every=8, rule=rule)
+        assert st == O.OK
+        err = abs(lat.energies()["e"].real - e_inf) / e_inf
+        if rule == "difference":
+            assert err > 2e-6   # several times the tolerance
+        else:
+            assert err < 1e-6
