@@ -64,6 +64,27 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
+// Per-call tables, passed by value in the kernel's parameter space and written into the
+// scratch array on the device: no host buffer has to outlive the call.
+struct StaticTables {
+  float tw[2 * kStaticMaxN];  // per-stage twiddles (re, im), fft_twiddle_count(n) pairs
+  float sym[kStaticMaxN];     // per-axis kinetic symbol
+  double out_scale;
+  int tw_count, n;
+};
+
+__global__ void static_tables_kernel(const __grid_constant__ StaticTables t, float* tw, float* sym,
+                                     DevScalars* sc) {
+  for (int i = threadIdx.x; i < 2 * t.tw_count; i += blockDim.x) tw[i] = t.tw[i];
+  for (int i = threadIdx.x; i < t.n; i += blockDim.x) sym[i] = t.sym[i];
+  if (threadIdx.x == 0) {
+    DevScalars z{};
+    z.scale[0] = t.out_scale;
+    z.scale[1] = t.out_scale;
+    *sc = z;
+  }
+}
+
 }  // namespace
 }  // namespace qf
 
@@ -81,23 +102,25 @@ extern "C" qf_status qf_fft_step_static(int n, double a, int kinetic, double mas
   char* base = static_cast<char*>(base_v);
 
   // tables of this call (the array holds the previous call's): per-stage twiddles, the
-  // per-axis symbol, and the output scale
+  // per-axis symbol and the output scale, written on the device by the first launch
+  StaticTables tab{};
   double twd[2 * kStaticMaxN];
-  float tw[2 * kStaticMaxN], sym[kStaticMaxN];
   const int cnt = fft_twiddle_count(n);
   fft_twiddles(n, twd);
-  for (int i = 0; i < 2 * cnt; ++i) tw[i] = (float)twd[i];
+  for (int i = 0; i < 2 * cnt; ++i) tab.tw[i] = (float)twd[i];
   for (int j = 0; j < n; ++j) {
     const double k = 2.0 * M_PI * (double)(j <= n / 2 ? j : j - n) / (double)n;
-    sym[j] = (float)(kinetic == QF_KIN_FFT_NAIVE ? k * k : 4.0 * sin(0.5 * k) * sin(0.5 * k));
+    tab.sym[j] = (float)(kinetic == QF_KIN_FFT_NAIVE ? k * k : 4.0 * sin(0.5 * k) * sin(0.5 * k));
   }
-  DevScalars sc{};
-  sc.scale[0] = out_scale;
-  sc.scale[1] = out_scale;
-  // pageable sources: each copy has read its host buffer when the call returns
-  if (cudaMemcpyAsync(base + kStaticTwOff, tw, sizeof(float) * 2 * cnt, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(base + kStaticSymOff, sym, sizeof(float) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(base + kStaticScOff, &sc, sizeof(sc), cudaMemcpyHostToDevice, st) != cudaSuccess)
+  tab.out_scale = out_scale;
+  tab.tw_count = cnt;
+  tab.n = n;
+  float* tw_dev = reinterpret_cast<float*>(base + kStaticTwOff);
+  float* sym_dev = reinterpret_cast<float*>(base + kStaticSymOff);
+  DevScalars* sc_dev = reinterpret_cast<DevScalars*>(base + kStaticScOff);
+  void* targs[] = {&tab, &tw_dev, &sym_dev, &sc_dev};
+  // (cudaLaunchKernel returns this launch's own status, not an earlier error of the thread)
+  if (cudaLaunchKernel((const void*)static_tables_kernel, dim3(1), dim3(128), targs, 0, st) != cudaSuccess)
     return QF_ECUDA;
 
   DevScalars* dsc = reinterpret_cast<DevScalars*>(base + kStaticScOff);
@@ -127,5 +150,5 @@ extern "C" qf_status qf_fft_step_static(int n, double a, int kinetic, double mas
     if (cudaMemcpyAsync(sums, dsc->sums, kNumSums * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return QF_ECUDA;
   }
-  return cudaGetLastError() == cudaSuccess ? QF_OK : QF_ECUDA;
+  return QF_OK;
 }
