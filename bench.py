@@ -95,7 +95,7 @@ def workload_config(w, prec):
                      f"dtau={'a/4' if w['dtau'] else 'default'} seed={w['seed']} {prec}"),
         "n": w["n"], "a": w["a"], "kinetic": kin, "mass": w["m"], "precision": prec,
         "chunk_steps": CHUNK, "check_every": CHUNK, "snap_every": CHUNK,
-        "per_step": "64 steps + check + snapshot + 3-state Gram-Schmidt + energies + parity",
+        "per_step": "64 steps + check + snapshot + 3-state Gram-Schmidt + energies (plateau record) + parity",
         "l2": "no flush: inputs larger than L2 (3 fields of 8 N^3 bytes per step)",
     }
 
@@ -164,15 +164,12 @@ def size_sweep(name, prec, sizes=(32, 128), gpu_steps=640, cpu_seconds=2.0):
     return res
 
 
-def run_reference(args):
-    """The FP64 oracle as it stands, on the host cores; one bench step = one oracle
-    imaginary-time step of the same workload (a check step every 64)."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
+def _oracle_worker(conn, name, n):
+    """One host core's oracle lattice of the workload: builds it, then advances it one
+    imaginary-time step (a check every 64) per message until it receives None."""
     from oracle import qfdtd_oracle as O
 
-    w = I.workload(args.workload, args.n)
+    w = I.workload(name, n)
     v, psi0 = make_inputs(w)
     lat = O.Lattice(w["n"], w["a"])
     if np.iscomplexobj(v):
@@ -181,22 +178,93 @@ def run_reference(args):
         lat.set_potential(v)
     lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
     lat.set_wavefunction(psi0)
-    for _ in range(args.warmup):
+    conn.send("ready")
+    while conn.recv() is not None:
         lat.step_n(1, check_every=CHUNK)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        lat.step_n(1, check_every=CHUNK)
-    el = time.perf_counter() - t0
-    rate = w["n"] ** 3 * args.steps / el
+        conn.send("done")
+
+
+class OracleCores:
+    """The FP64 oracle as it stands on ``procs`` host cores: one independent lattice of
+    the workload per core (spawned processes; numpy's FFT runs on one thread each), all
+    stepped together.  ``step()`` advances every lattice by one imaginary-time step."""
+
+    def __init__(self, name, n, procs):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        self.procs, self.conns = [], []
+        for _ in range(procs):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, name, n), daemon=True)
+            p.start()
+            self.procs.append(p)
+            self.conns.append(a)
+        for c in self.conns:
+            c.recv()
+
+    def step(self):
+        for c in self.conns:
+            c.send(1)
+        for c in self.conns:
+            c.recv()
+
+    def close(self):
+        for c in self.conns:
+            c.send(None)
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+def oracle_rate_cores(name, n, seconds, procs, min_steps=2):
+    """Whole-host oracle throughput: ``procs`` lattices stepped together for about
+    ``seconds``; returns (site-updates/s, steps per lattice, seconds)."""
+    pool = OracleCores(name, n, procs)
+    try:
+        pool.step()  # warm-up
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            pool.step()
+            steps += 1
+            el = time.perf_counter() - t0
+            if steps >= min_steps and el >= seconds:
+                break
+    finally:
+        pool.close()
+    return procs * n ** 3 * steps / el, steps, el
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, on all host cores (one lattice of the workload per
+    core); one bench step = one oracle imaginary-time step of every lattice (a check step
+    every 64)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = I.workload(args.workload, args.n)
+    n = w["n"]
+    cores = os.cpu_count() or 1
+    pool = OracleCores(args.workload, args.n, cores)
+    try:
+        for _ in range(args.warmup):
+            pool.step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.step()
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
+    rate = cores * n ** 3 * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "site-updates/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded SplitMix64/Box-Muller psi0, analytic potential)",
         "config": workload_config(w, "c128 (FP64 oracle)"),
-        "cpu_baseline": {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} oracle imaginary-time steps of the N={w['n']} workload "
-                                   f"({el:.1f} s; numpy FFT, one thread)"},
+        "cpu_baseline": {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} oracle imaginary-time steps of {cores} independent N={n} "
+                                   f"lattices, one per host core ({el:.1f} s; numpy FFT, one thread each)"},
         "e2e": {"value": rate, "unit": "site-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -251,7 +319,21 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # Roofline bookkeeping
 # ---------------------------------------------------------------------------------------
-def bytes_per_site(kernel, prec, v_real):
+def algorithmic_bytes_per_site_update(prec, v_real):
+    """The floor of one imaginary-time step: read psi and V, write psi' (8 + 4 + 8 B per
+    site for complex FP32 with a real V; V complex: 8 B; FP64 doubles every term)."""
+    c = 8 if prec == "c64" else 16
+    return 2 * c + ((c // 2) if v_real else c)
+
+
+# site-updates one launch of a kernel kind carries (per lattice site): the step's kernels
+# advance every site by one step, the two-step stencil by two
+UPDATES_PER_LAUNCH = {"stencil_2step": 2}
+
+
+def design_bytes_per_site(kernel, prec, v_real):
+    """Bytes a launch of this kernel kind moves per lattice site by its design (every
+    field it reads or writes once): the counted traffic of the kernel, not the floor."""
     c = 8 if prec == "c64" else 16
     r = c // 2
     vb = r if v_real else c
@@ -267,6 +349,11 @@ def bytes_per_site(kernel, prec, v_real):
         "fft2_xy_fwd": 2 * c, "fft2_yz_mid_T": 2 * c, "fft2_xy_inv_update": 4 * c + vb,
     }
     return table.get(kernel)
+
+
+def step_kernel(kernel):
+    """Kernel kinds that advance psi by a step (the roofline candidates)."""
+    return kernel in ("fft_x_inv_update", "fft2_xy_inv_update", "stencil_step", "stencil_2step")
 
 
 def source_digest(files):
@@ -346,6 +433,64 @@ def cufft_comparator(w, v, psi0, steps=10):
 
 
 # ---------------------------------------------------------------------------------------
+# The complex-FP64 arm of the same bench step, and the FP64 rate it runs against
+# ---------------------------------------------------------------------------------------
+def c128_arm(w, v, psi0, bench_steps=2):
+    """The bench step with complex-FP64 fields (qf precision c128): 64 steps + check +
+    snapshot + Gram-Schmidt energies + parity, timed with CUDA events on the lattice's
+    stream; returns its rate and energies beside the complex-FP32 ones."""
+    import torch
+
+    from paper_2211_10185_gb300 import qfdtd as Q
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    n = w["n"]
+    lat = Lattice(n, w["a"], precision="c128")
+    lat.set_potential(v)
+    lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+    lat.set_wavefunction(psi0)
+    lat.step_n(3 * CHUNK, tol=0.0, check_every=CHUNK, snap_every=CHUNK)
+
+    def one():
+        lat.step_n(CHUNK, tol=0.0, check_every=CHUNK, snap_every=CHUNK)
+        ex = lat.project_excited(3)
+        lat.parity_project(Q.QF_P_MINUS_PK, 3, 1)
+        return ex
+
+    one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    for _ in range(bench_steps):
+        ex = one()
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / bench_steps
+    lat.close()
+    return {"precision": "c128", "bench_steps": bench_steps, "ms_per_bench_step": ms,
+            "site_updates_per_s": n ** 3 * CHUNK / (ms * 1e-3), "energies": [e["e"].real for e in ex]}
+
+
+def fp64_peak(size=4096, reps=3):
+    """Dense FP64 rate of this GPU (cuBLAS DGEMM through torch.matmul, best of reps)."""
+    import torch
+
+    a = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    b = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return {"tflops": 2 * size ** 3 / best / 1e12, "how": f"torch.matmul float64 {size}^3, best of {reps}"}
+
+
+# ---------------------------------------------------------------------------------------
 # Served mix: Poisson arrivals of Cornell solves, continuous batching
 # ---------------------------------------------------------------------------------------
 def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget=170e9, n_cmp=8):
@@ -363,7 +508,7 @@ def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget
     torch.cuda.synchronize()
     out = dict(srv.metrics())
     out.update({"requests": n_req, "arrival_rate_per_s": rate, "sizes": list(sizes), "step_cap": cap,
-                "tolerance": "|dE| < 1e-7 (1 + |E|)", "hbm_budget_bytes": int(budget), "realtime": True})
+                "tolerance": "extrapolated distance to the converged energy < 1e-7 + 1e-6 |E| (QF_STOP_EXTRAPOLATED)", "hbm_budget_bytes": int(budget), "realtime": True})
     # comparator: the same small requests, all arriving at once, FP32 batched vs FP64 alone
     sub = [r for r in reqs if r.n <= 64][:n_cmp]
     t0 = time.perf_counter()
@@ -450,7 +595,7 @@ def run_ours(args):
 
     def bench_step():
         lat.step_n(CHUNK, tol=0.0, check_every=CHUNK, snap_every=CHUNK)
-        ex = lat.project_excited(3)
+        ex = lat.track_excited(3)
         lat.parity_project(Q.QF_P_MINUS_PK, 3, 1)
         return ex
 
@@ -500,10 +645,14 @@ def run_ours(args):
     value = aggregate_rate(units_per_rank, world, ms_total * 1e-3)
     ms_per_step = ms_total / args.steps
 
-    # roofline of the dominant kernel (largest share of the timed device time)
+    # roofline of the dominant kernel: the largest share of the timed device time among the
+    # kernels that advance psi.  achieved = algorithmic bytes per launch (the step's floor,
+    # read psi and V and write psi', times the site-updates one launch carries) / the
+    # launch's average CUDA-event duration; the design bytes (every field the kernel moves)
+    # give design_frac beside it.
     peak, peak_src = hbm_peak()
-    dom = max(((k, v_) for k, v_ in prof.items() if bytes_per_site(k, prec, v_real)),
-              key=lambda kv: kv[1][1], default=None)
+    alg_site = algorithmic_bytes_per_site_update(prec, v_real)
+    dom = max(((k, v_) for k, v_ in prof.items() if step_kernel(k)), key=lambda kv: kv[1][1], default=None)
     roof = None
     kernels = {}
     for k, (cnt, tot) in prof.items():
@@ -511,22 +660,25 @@ def run_ours(args):
     if dom:
         k, (cnt, tot) = dom
         avg_s = tot / cnt * 1e-3
-        alg = bytes_per_site(k, prec, v_real) * n ** 3
+        alg = alg_site * UPDATES_PER_LAUNCH.get(k, 1) * n ** 3
+        design_b = design_bytes_per_site(k, prec, v_real) * n ** 3
         achieved = alg / avg_s / 1e9
         traffic, tsrc = load_traffic(k, n, prec)
         roof = {"bound": "hbm", "kernel": k, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg, "avg_launch_us": avg_s * 1e6,
-                "traffic_source": tsrc}
-    # minimum bytes of one step: read psi and V, write psi'
+                "algorithmic_bytes_per_launch": alg,
+                "algorithmic_bytes_per_site_update": alg_site,
+                "design_bytes_per_launch": design_b, "design_frac": design_b / avg_s / 1e9 / peak,
+                "dram_frac": (traffic / avg_s / 1e9 / peak) if traffic else None,
+                "avg_launch_us": avg_s * 1e6, "traffic_source": tsrc}
+    # whole step on the floor bytes
     c = 8 if prec == "c64" else 16
-    step_bytes = 2 * c + ((c // 2) if v_real else c)
-    step_frac = step_bytes * units_per_rank / (ms_total * 1e-3) / 1e9 / peak
+    step_frac = alg_site * units_per_rank / (ms_total * 1e-3) / 1e9 / peak
     # design bytes of a steady-state step: the per-launch bytes of the kernels one step
     # launches (from the live profile: launches per step of each kernel kind)
     steps_timed = CHUNK * args.steps
-    design = sum(bytes_per_site(k, prec, v_real) * cnt / steps_timed
-                 for k, (cnt, _) in prof.items() if bytes_per_site(k, prec, v_real))
+    design = sum(design_bytes_per_site(k, prec, v_real) * cnt / steps_timed
+                 for k, (cnt, _) in prof.items() if design_bytes_per_site(k, prec, v_real))
 
     out = None
     if rank == 0:
@@ -540,7 +692,7 @@ def run_ours(args):
             "roofline": roof,
             "kernels": kernels,
             "profiled_region_ms_per_step": ms_prof / args.steps,
-            "step_algorithmic_hbm": {"bytes_per_site_update": step_bytes,
+            "step_algorithmic_hbm": {"bytes_per_site_update": alg_site,
                                      "frac_of_peak": step_frac,
                                      "design_bytes_per_site_update": design,
                                      "field_passes_per_step": design / c,
@@ -585,6 +737,12 @@ def run_ours(args):
             out["comparator_cufft"] = cufft_comparator(w, v, psi0)
         except Exception as exc:  # context only
             out["comparator_cufft"] = {"error": str(exc)[:200]}
+    if out is not None and world == 1 and not args.no_comparator:
+        try:
+            out["c128_arm"] = c128_arm(w, v, psi0)
+            out["fp64_peak"] = fp64_peak()
+        except Exception as exc:  # context only
+            out["c128_arm"] = {"error": str(exc)[:200]}
     if out is not None and not args.no_served:
         lat.close()
         torch.cuda.synchronize()
@@ -593,10 +751,16 @@ def run_ours(args):
         except Exception as exc:
             out["served"] = {"error": str(exc)[:300]}
     if out is not None and world == 1 and not args.no_cpu_baseline:
-        rate, steps, el = oracle_rate(w, v, psi0, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": rate, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
-                               "sample": f"{steps} FP64 oracle imaginary-time steps of the same N={n} workload "
-                                         f"({el:.1f} s, numpy FFT, one thread)"}
+        cores = os.cpu_count() or 1
+        rate, steps, el = oracle_rate_cores(args.workload, args.n, args.cpu_seconds, cores)
+        out["cpu_baseline"] = {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{steps} FP64 oracle imaginary-time steps of each of {cores} independent "
+                                         f"N={n} lattices of the same workload, one per host core ({el:.1f} s; "
+                                         f"numpy FFT, one thread each)"}
+        rate1, steps1, el1 = oracle_rate(w, v, psi0, args.cpu_seconds / 2)
+        out["cpu_baseline_one_core"] = {"value": rate1, "unit": "site-updates/s", "cores": 1, "kind": "oracle",
+                                        "sample": f"{steps1} FP64 oracle steps of the same N={n} workload "
+                                                  f"({el1:.1f} s, one thread)"}
     if out is not None and world == 1 and not args.no_cpu_baseline:
         try:
             out["by_size"] = size_sweep(args.workload, prec)

@@ -65,14 +65,22 @@ def test_roofline_byte_model():
     for prec, c in (("c64", 8), ("c128", 16)):
         for v_real in (True, False):
             vb = c // 2 if v_real else c
-            assert bench.bytes_per_site("fft_y_fwd", prec, v_real) == 2 * c
-            assert bench.bytes_per_site("fft_x_inv_update", prec, v_real) == 4 * c + vb
-            assert bench.bytes_per_site("fft2_yz_mid_T", prec, v_real) == 2 * c
+            assert bench.design_bytes_per_site("fft_y_fwd", prec, v_real) == 2 * c
+            assert bench.design_bytes_per_site("fft_x_inv_update", prec, v_real) == 4 * c + vb
+            assert bench.design_bytes_per_site("fft2_yz_mid_T", prec, v_real) == 2 * c
             # two-pass steady state: 16 + 36 B per site (real V, c64) instead of 84
-            assert bench.bytes_per_site("fft2_xy_inv_update", prec, v_real) == 4 * c + vb
-            assert bench.bytes_per_site("stencil_2step", prec, v_real) == 2 * c + vb
-            assert bench.bytes_per_site("gs_dots", prec, v_real) is None
-    two = bench.bytes_per_site("fft2_yz_mid_T", "c64", True) + bench.bytes_per_site("fft2_xy_inv_update", "c64", True)
-    four = sum(bench.bytes_per_site(k, "c64", True) for k in ("fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
+            assert bench.design_bytes_per_site("fft2_xy_inv_update", prec, v_real) == 4 * c + vb
+            assert bench.design_bytes_per_site("stencil_2step", prec, v_real) == 2 * c + vb
+            assert bench.design_bytes_per_site("gs_dots", prec, v_real) is None
+    two = bench.design_bytes_per_site("fft2_yz_mid_T", "c64", True) + bench.design_bytes_per_site("fft2_xy_inv_update", "c64", True)
+    four = sum(bench.design_bytes_per_site(k, "c64", True) for k in ("fft_y_fwd", "fft_z_mid_T", "fft_y_inv",
                                                                 "fft_x_inv_update"))
     assert (two, four) == (52, 84)
+    # the floor of a step (read psi and V, write psi'): 20 / 24 B per site-update in complex
+    # FP32, 40 / 48 in FP64; a two-step stencil launch carries two updates per site
+    assert bench.algorithmic_bytes_per_site_update("c64", True) == 20
+    assert bench.algorithmic_bytes_per_site_update("c64", False) == 24
+    assert bench.algorithmic_bytes_per_site_update("c128", True) == 40
+    assert bench.algorithmic_bytes_per_site_update("c128", False) == 48
+    assert bench.UPDATES_PER_LAUNCH.get("stencil_2step") == 2 and bench.UPDATES_PER_LAUNCH.get("fft2_xy_inv_update", 1) == 1
+    assert bench.step_kernel("fft2_xy_inv_update") and not bench.step_kernel("fft2_yz_mid_T")
