@@ -83,6 +83,8 @@ typedef struct {
   double a;           /* lattice spacing (the paper's A), > 0                      */
   int prec;           /* qf_precision                                              */
   int n_snap;         /* snapshot ring length, 1..3 (Gram-Schmidt uses up to 3)    */
+  int plateau_slots;  /* 0..3 fields kept for the states at the plateau of E_i(tau)
+                         (qf_track_excited); 0 keeps the energies only              */
 } qf_lattice_desc;
 
 typedef struct {
@@ -104,6 +106,8 @@ typedef struct {
   int temporal_block; /* FDTD steps fused per pass (qf_set_temporal_blocking)         */
   int fft_passes;     /* HBM passes of a steady-state FFT step: 2 (N = 256 complex
                          FP32, qf_use_two_pass_fft) or 4; 0 for the FDTD term         */
+  int64_t field_exp2; /* the stored live field is 2^field_exp2 times the one
+                         qf_get_wavefunction returns (see qf_step_n)                  */
 } qf_info;
 
 typedef struct {
@@ -140,7 +144,8 @@ qf_status qf_set_kinetic(qf_lattice* lat, int kinetic, double mass, double dtau)
 qf_status qf_set_wavefunction(qf_lattice* lat, const double* re_im);
 
 /* Copies a field to a host array of 2 N^3 doubles.  slot -1: live psi as stored;
- * 0..2: Gram-Schmidt state i; 100 + j: snapshot j (0 = latest). */
+ * 0..2: Gram-Schmidt state i; 100 + j: snapshot j (0 = latest); 200 + i: the state i
+ * kept at its plateau by qf_track_excited (needs plateau_slots > i). */
 qf_status qf_get_wavefunction(qf_lattice* lat, int slot, double* re_im);
 
 /* Advances up to max_steps steps.  Step t maps psi_t to psi_{t+1}.  When
@@ -148,7 +153,14 @@ qf_status qf_get_wavefunction(qf_lattice* lat, int slot, double* re_im);
  * pass (FP64 sums), and the output of step t+1 is scaled by 1/sqrt(<psi_t|psi_t>).  The
  * call returns QF_OK right after a check with |E_t - E_{t-check_every}| < tol_abs, else
  * QF_ENOTCONV after max_steps.  After step t, when (t+1) % snap_every == 0
- * (snap_every > 0), psi_{t+1} enters the snapshot ring.  steps_done may be NULL. */
+ * (snap_every > 0), psi_{t+1} enters the snapshot ring.  steps_done may be NULL.
+ * Between checks psi shrinks by about the ground state's step multiplier per step (a
+ * heavy relativistic term can take it below the complex-FP32 range within one check
+ * interval); each step therefore also multiplies its output by an exact power of two 2^k,
+ * k estimated at every check from the measured decay.  The library tracks the
+ * accumulated power and removes it from every field it returns (qf_get_wavefunction,
+ * norms in qf_energy), so results are those of the unscaled iteration; only the raw
+ * device data of qf_field_pointer carries it (qf_info.field_exp2 for the live field). */
 qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_abs, int check_every, int snap_every,
                     int64_t* steps_done);
 
@@ -161,11 +173,28 @@ qf_status qf_energies(qf_lattice* lat, qf_energy* out);
  * min(3, n_snap); QF_ESTATE when fewer snapshots are held. */
 qf_status qf_project_excited(qf_lattice* lat, int n_states, qf_energy* out);
 
+/* Plateau of the excited-state energies (Sec. 4: the saddle point of E_i(tau), made
+ * automatic).  Runs qf_project_excited(lat, n_states, out) on the latest snapshots and
+ * appends E_0..E_{n_states-1} to the handle's history as record j (j = 0, 1, ...).  For
+ * each state i, record j >= 1 becomes the state's choice when |E_i(tau_j) -
+ * E_i(tau_{j-1})| (complex modulus) is strictly smaller than the current choice's, so
+ * the earliest minimiser wins; with plateau_slots > i the state v_i of that record is
+ * copied into slot 200 + i.  Call it at successive snapshots (e.g. after each qf_step_n
+ * chunk that ends on a snapshot).  Every call of one history uses the same n_states
+ * (QF_EINVAL otherwise); qf_set_potential, qf_set_kinetic and qf_set_wavefunction start
+ * a new history. */
+qf_status qf_track_excited(qf_lattice* lat, int n_states, qf_energy* out);
+
+/* The current choice for states 0..n_states-1: out[i] holds E_i at the chosen record,
+ * with that record's step and tau, de = |E_i(tau_j) - E_i(tau_{j-1})| and norm 1;
+ * record (may be NULL) receives j.  QF_ESTATE before two records, QF_EINVAL when
+ * n_states exceeds the history's. */
+qf_status qf_excited_plateau(qf_lattice* lat, int n_states, qf_energy* out, int* record);
+
 /* Applies a parity projector (qf_parity; axis 1..3 = x, y, z for QF_P_MINUS_PK and the
- * d-wave projectors) to the
- * live psi (target -1) or to Gram-Schmidt state 0..2 in place and renormalises it to
- * unit norm (a zero result stays zero).  Projection of the live psi cancels a pending
- * renormalisation. */
+ * d-wave projectors) to the live psi (target -1), to Gram-Schmidt state 0..2 or to a
+ * plateau state 200 + i, in place, and renormalises it to unit norm (a zero result
+ * stays zero).  Projection of the live psi cancels a pending renormalisation. */
 qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int target);
 
 /* Momentum-space distribution of a field (slot as in qf_get_wavefunction; needs an
@@ -222,7 +251,9 @@ qf_status qf_prolong(qf_lattice* coarse, int coarse_slot, qf_lattice* fine);
 qf_status qf_get_info(qf_lattice* lat, qf_info* out);
 
 /* Device pointer to a field (slot as in qf_get_wavefunction), for zero-copy access by
- * the caller on the handle's stream.  Elements are complex FP32 or FP64 pairs. */
+ * the caller on the handle's stream.  Elements are complex FP32 or FP64 pairs.  The
+ * live field and the snapshots are stored times a power of two (see qf_step_n;
+ * qf_info.field_exp2 for the live field); the states are normalised. */
 qf_status qf_field_pointer(qf_lattice* lat, int slot, void** dev_ptr);
 
 /* Per-kernel timing (no counterpart in the paper; measurement support).  enable != 0
@@ -289,6 +320,21 @@ qf_status qf_batch_remove(qf_batch* b, qf_lattice* lat);
  * (QF_ENOTCONV) and stay in the batch until removed; *n_running (may be NULL) receives
  * the number still running. */
 qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, int snap_every, int* n_running);
+
+/* Stopping rules of batch members (the paper has no automatic convergence test; the
+ * difference rule is the reading used by qf_step_n).  With d = |E_t - E_prev| at a check
+ * and tol = tol_abs + tol_rel |E_t|:
+ *   QF_STOP_DIFFERENCE (default): converged when d < tol.
+ *   QF_STOP_EXTRAPOLATED: the check energies approach their limit geometrically, so
+ *     while d shrinks (rho = d / d_prev < 1, d_prev the previous check's difference) the
+ *     distance left to the limit is about d rho/(1 - rho); converged when
+ *     max(d, d rho/(1 - rho)) < tol, never while d >= d_prev (d = 0 counts as
+ *     converged).  The reported energy is then within about tol of the limit even when
+ *     the contraction per check is slow, where the difference rule can stop far from it. */
+typedef enum { QF_STOP_DIFFERENCE = 0, QF_STOP_EXTRAPOLATED = 1 } qf_stopping;
+
+/* Selects the stopping rule (qf_stopping) for every member's following checks. */
+qf_status qf_batch_set_stopping(qf_batch* b, int rule);
 
 /* Members in insertion order: count, and per member (arrays of at least `max` entries,
  * may be NULL) its status (QF_BATCH_RUNNING, QF_OK, QF_ENOTCONV) and steps taken. */

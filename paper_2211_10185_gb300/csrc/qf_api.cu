@@ -60,8 +60,8 @@ static const char* kKindNames[K_NUM_KINDS] = {"fft_x_fwd", "fft_y_fwd", "fft_z_m
 static const int kEventPool = 4096;
 
 struct Layout {
-  size_t field = 0, f[2] = {0, 0}, v = 0, snaps = 0, states = 0, tw = 0, sym = 0, partials = 0, scalars = 0,
-         stage = 0, stage_bytes = 0, total = 0;
+  size_t field = 0, f[2] = {0, 0}, v = 0, snaps = 0, states = 0, plateau = 0, tw = 0, sym = 0, partials = 0,
+         scalars = 0, stage = 0, stage_bytes = 0, total = 0;
   int max_blocks = 0;
 };
 
@@ -83,6 +83,8 @@ static Layout make_layout(const qf_lattice_desc& d) {
   off += L.field * d.n_snap;
   L.states = off;
   off += L.field * 3;
+  L.plateau = off;
+  off += L.field * d.plateau_slots;
   L.tw = off;
   off += align_up(2 * elem * (size_t)(d.n + 64));
   L.sym = off;
@@ -120,18 +122,34 @@ struct qf_lattice {
   int64_t step = 0;
   double tau = 0;
   bool pending_scale = false;
+  // Power-of-two scale of the stored fields (DevScalars::scale): the live field holds
+  // 2^K psi, snapshot slot j holds 2^snapK[j] psi; kcur is the exponent each step applies,
+  // K_check the live field's exponent at the last check, renorm_step the step whose output
+  // was last renormalised (-1: none since the field was set).
+  int kcur = 0, jcur = 0;  // exponents of the steps and of the renormalising step's centring
+  long long K = 0, K_check = 0, snapK[3] = {0, 0, 0};
+  int64_t renorm_step = -1;
   bool have_prev = false;
   double prev_re = 0, prev_im = 0;
+  double prev_de = INFINITY;  // |E| difference at the previous check (extrapolated rule)
   bool have_last = false;
   qf_energy last{};
   int snap_count = 0, snap_head = -1;  // snap_head: slot of the latest snapshot
   bool have_states[3] = {false, false, false};
+  // plateau of E_i(tau) (qf_track_excited): records so far, the previous record, and per
+  // state the chosen record with its energy and |E_i(tau_j) - E_i(tau_{j-1})|
+  int exc_records = 0, exc_n = 0;
+  qf_energy exc_prev[3] = {};
+  bool plat_have[3] = {false, false, false};
+  qf_energy plat[3] = {};
+  int plat_rec[3] = {0, 0, 0};
+  bool have_plateau_state[3] = {false, false, false};
   // the scratch field holds the forward x transform of the live psi (written by the
   // previous step's final pass), so the next FFT step starts at its second pass
   bool xfwd_valid = false;
   // CUDA graphs of the check_every-1 steps that follow a check (see run_chunk_graph)
   struct Graph {
-    int check_every, live, tblock;
+    int check_every, live, tblock, kzero;
     cudaGraphExec_t exec;
     int flips;         // FDTD buffer swaps done by the replay
     int64_t launches;  // kernels in the graph
@@ -169,6 +187,12 @@ struct qf_lattice {
   void* tmp() const { return field(1 - live); }
   void* snap(int j) const { return ws + L.snaps + L.field * j; }
   void* state(int i) const { return ws + L.states + L.field * i; }
+  void* plateau_state(int i) const { return ws + L.plateau + L.field * i; }
+  void reset_plateau() {
+    exc_records = 0;
+    exc_n = 0;
+    for (int i = 0; i < 3; ++i) plat_have[i] = have_plateau_state[i] = false;
+  }
   double* partials() const { return reinterpret_cast<double*>(ws + L.partials); }
   DevScalars* sc() const { return reinterpret_cast<DevScalars*>(ws + L.scalars); }
   double* stage() const { return reinterpret_cast<double*>(ws + L.stage); }
@@ -235,7 +259,7 @@ static cudaError_t launch(qf_lattice* lat, int kind, F&& f) {
 
 static bool desc_ok(const qf_lattice_desc* d) {
   return d && valid_n(d->n) && d->a > 0 && isfinite(d->a) && (d->prec == QF_PREC_C64 || d->prec == QF_PREC_C128) &&
-         d->n_snap >= 1 && d->n_snap <= 3;
+         d->n_snap >= 1 && d->n_snap <= 3 && d->plateau_slots >= 0 && d->plateau_slots <= 3;
 }
 
 extern "C" qf_status qf_workspace_bytes(const qf_lattice_desc* desc, size_t* bytes) {
@@ -264,6 +288,7 @@ extern "C" qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws
     DevScalars init{};
     init.scale[0] = 1.0;
     init.scale[1] = 1.0;
+    init.scale[2] = 1.0;
     e = cudaMemcpyAsync(lat->sc(), &init, sizeof(init), cudaMemcpyHostToDevice, lat->st);
   }
   if (e == cudaSuccess && fft_supported(desc->n)) {
@@ -365,6 +390,7 @@ extern "C" qf_status qf_set_potential(qf_lattice* lat, const double* v_re, const
   lat->have_v = true;
   lat->v_real = (v_im == nullptr);
   drop_graphs(lat);
+  lat->reset_plateau();
   return QF_OK;
 }
 
@@ -384,6 +410,7 @@ extern "C" qf_status qf_set_kinetic(qf_lattice* lat, int kinetic, double mass, d
     return fail(lat, QF_EINVAL, "no FFT plan for this N (use 8,12,16,24,32,48,64,96,128,192,256,384,512)");
   const double a = lat->d.a;
   drop_graphs(lat);
+  lat->reset_plateau();
   lat->clean = false;
   lat->kinetic = kinetic;
   lat->mass = mass;
@@ -425,12 +452,17 @@ extern "C" qf_status qf_set_wavefunction(qf_lattice* lat, const double* re_im) {
   lat->pending_scale = false;
   lat->xfwd_valid = false;
   lat->clean = false;
+  lat->reset_plateau();
+  lat->K = 0;
+  lat->renorm_step = -1;
   return QF_OK;
 }
 
 static void* slot_ptr(qf_lattice* lat, int slot) {
   if (slot == -1) return lat->psi();
   if (slot >= 0 && slot < 3) return lat->have_states[slot] ? lat->state(slot) : nullptr;
+  if (slot >= 200 && slot < 200 + lat->d.plateau_slots)
+    return lat->have_plateau_state[slot - 200] ? lat->plateau_state(slot - 200) : nullptr;
   if (slot >= 100 && slot < 100 + lat->d.n_snap) {
     const int j = slot - 100;
     if (j >= lat->snap_count) return nullptr;
@@ -440,17 +472,30 @@ static void* slot_ptr(qf_lattice* lat, int slot) {
   return nullptr;
 }
 
+// Power of two the stored field of a slot carries (the live field and snapshots; the
+// normalised states carry none).
+static long long slot_exp2(const qf_lattice* lat, int slot) {
+  if (slot == -1) return lat->K;
+  if (slot >= 100 && slot < 100 + lat->d.n_snap) {
+    const int j = slot - 100;
+    const int idx = ((lat->snap_head - j) % lat->d.n_snap + lat->d.n_snap) % lat->d.n_snap;
+    return lat->snapK[idx];
+  }
+  return 0;
+}
+
 extern "C" qf_status qf_get_wavefunction(qf_lattice* lat, int slot, double* re_im) {
   if (!lat || !re_im) return fail(lat, QF_EINVAL, "null output");
   void* src = slot_ptr(lat, slot);
   if (!src) return fail(lat, QF_ESTATE, "slot holds no field");
+  const double f = ldexp(1.0, (int)-slot_exp2(lat, slot));
   const long long chunk = (long long)(lat->L.stage_bytes / sizeof(double)) / 2;
   for (long long first = 0; first < lat->sites; first += chunk) {
     const long long cnt = (lat->sites - first < chunk) ? lat->sites - first : chunk;
     cudaError_t e = launch(lat, K_CONVERT, [&] {
-      return lat->c64() ? launch_to_f64<float>(lat->stage(), reinterpret_cast<cpx<float>*>(src) + first, nullptr,
+      return lat->c64() ? launch_to_f64<float>(lat->stage(), reinterpret_cast<cpx<float>*>(src) + first, f,
                                                cnt, lat->st)
-                        : launch_to_f64<double>(lat->stage(), reinterpret_cast<cpx<double>*>(src) + first, nullptr,
+                        : launch_to_f64<double>(lat->stage(), reinterpret_cast<cpx<double>*>(src) + first, f,
                                                 cnt, lat->st);
     });
     QF_CUDA(lat, e);
@@ -654,6 +699,7 @@ static int tuned_tb_zchunk(qf_lattice* lat) {
 // on and a clean live field, no check at t or t+1 and no snapshot after step t.
 static bool fuse_pair(const qf_lattice* lat, int64_t t, int check_every, int snap_every) {
   if (lat->kinetic != QF_KIN_FDTD || !lat->c64() || lat->tblock < 2 || !lat->clean || !lat->tbmap_ok) return false;
+  if (lat->kcur != 0) return false;  // the second step of a pair applies no scale
   if (check_every > 0 && (t % check_every == 0 || (t + 1) % check_every == 0)) return false;
   if (snap_every > 0 && (t + 1) % snap_every == 0) return false;
   return true;
@@ -750,6 +796,7 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
 static cudaError_t take_snapshot(qf_lattice* lat, int snap_every, cudaStream_t st) {
   if (snap_every > 0 && lat->step % snap_every == 0) {
     lat->snap_head = (lat->snap_head + 1) % lat->d.n_snap;
+    lat->snapK[lat->snap_head] = lat->K;
     cudaError_t e = cudaMemcpyAsync(lat->snap(lat->snap_head), lat->psi(), (size_t)lat->sites * (lat->c64() ? 8 : 16),
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
@@ -762,11 +809,22 @@ static cudaError_t take_snapshot(qf_lattice* lat, int snap_every, cudaStream_t s
 // qf_step_n and qf_batch_step so both advance a lattice identically): finishing sums and
 // the pending renormalisation on a check step, buffer swap (FDTD), counters, snapshot.
 static cudaError_t after_step(qf_lattice* lat, bool check, int nb, int snap_every, cudaStream_t st) {
+  const long long k_in = lat->K;  // exponent of the step's input (the field a check measures)
+  if (lat->pending_scale) {
+    // this step's output was renormalised by 2^(k+j) / sqrt(norm at K_check)
+    lat->K += lat->kcur + lat->jcur - lat->K_check;
+    lat->renorm_step = lat->step;
+  } else {
+    lat->K += lat->kcur;
+  }
   lat->pending_scale = false;
   if (check) {
-    cudaError_t e = launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 1, st); });
+    const int interval = lat->renorm_step >= 0 ? (int)std::min<int64_t>(lat->step - lat->renorm_step, 1 << 30) : 0;
+    cudaError_t e =
+        launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 1, st, interval, lat->dtau); });
     if (e != cudaSuccess) return e;
     lat->pending_scale = true;
+    lat->K_check = k_in;
   }
   if (lat->kinetic == QF_KIN_FDTD) {
     lat->live = 1 - lat->live;
@@ -779,6 +837,10 @@ static cudaError_t after_step(qf_lattice* lat, bool check, int nb, int snap_ever
 
 // Bookkeeping after a two-step pass (steps t and t+1): one buffer swap, two steps.
 static cudaError_t after_pair(qf_lattice* lat, int snap_every, cudaStream_t st) {
+  if (lat->pending_scale) {
+    lat->K += lat->jcur - lat->K_check;  // (kcur is 0 whenever steps are paired)
+    lat->renorm_step = lat->step;
+  }
   lat->pending_scale = false;
   lat->live = 1 - lat->live;
   lat->clean = true;
@@ -789,28 +851,45 @@ static cudaError_t after_pair(qf_lattice* lat, int snap_every, cudaStream_t st) 
   return take_snapshot(lat, snap_every, st);
 }
 
-// Records the energy of the check at step t; returns whether |E_t - E_prev| < tol where
-// tol = tol_abs + tol_rel |E_t|.
+// Whether a check with energy difference d = |E_t - E_prev| (previous check's d_prev)
+// meets tol under the rule: QF_STOP_DIFFERENCE: d < tol.  QF_STOP_EXTRAPOLATED: the check
+// energies approach their limit geometrically, so while d shrinks (rho = d/d_prev < 1)
+// the distance left is about d rho/(1 - rho); converged when max(d, d rho/(1 - rho)) < tol,
+// never while d >= d_prev (an exact repeat, d = 0, counts as converged).
+static bool check_converged(int rule, double d, double d_prev, double tol) {
+  if (!(d < INFINITY)) return false;
+  if (rule != QF_STOP_EXTRAPOLATED) return d < tol;
+  if (d == 0.0) return true;
+  if (!(d_prev < INFINITY) || !(d < d_prev)) return false;
+  const double rho = d / d_prev;
+  return std::max(d, d * rho / (1.0 - rho)) < tol;
+}
+
+// Records the energy of the check at step t; returns whether it converged under `rule`
+// with tol = tol_abs + tol_rel |E_t|.
 static bool record_check(qf_lattice* lat, const double* e3, int64_t t, double tau_t, double tol_abs,
-                         double tol_rel) {
+                         double tol_rel, int rule = QF_STOP_DIFFERENCE) {
   qf_energy r{};
   r.e_re = e3[0];
   r.e_im = e3[1];
-  r.norm = e3[2];
+  r.norm = ldexp(e3[2], (int)(-2 * lat->K_check));  // the measured field held 2^K_check psi
+  lat->kcur = (int)e3[3];
+  lat->jcur = (int)e3[4];
   r.de = lat->have_prev ? hypot(e3[0] - lat->prev_re, e3[1] - lat->prev_im) : INFINITY;
   r.step = t;
   r.tau = tau_t;
   lat->last = r;
   lat->have_last = true;
-  const bool conv = lat->have_prev && r.de < tol_abs + tol_rel * hypot(e3[0], e3[1]);
+  const bool conv = check_converged(rule, r.de, lat->prev_de, tol_abs + tol_rel * hypot(e3[0], e3[1]));
   lat->have_prev = true;
   lat->prev_re = e3[0];
   lat->prev_im = e3[1];
+  lat->prev_de = r.de;
   return conv;
 }
 
 static qf_status read_energy(qf_lattice* lat, double* e3) {
-  QF_CUDA(lat, cudaMemcpyAsync(e3, lat->sc()->energy, 3 * sizeof(double), cudaMemcpyDeviceToHost, lat->st));
+  QF_CUDA(lat, cudaMemcpyAsync(e3, lat->sc()->energy, 5 * sizeof(double), cudaMemcpyDeviceToHost, lat->st));
   QF_CUDA(lat, cudaStreamSynchronize(lat->st));
   if (lat->prof) prof_harvest(lat);
   return QF_OK;
@@ -826,7 +905,9 @@ static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every, int* flips)
   const int k = check_every - 1;
   const qf_lattice::Graph* hit = nullptr;
   for (auto& g : lat->graphs)
-    if (g.check_every == check_every && g.live == lat->live && g.tblock == lat->tblock) hit = &g;
+    if (g.check_every == check_every && g.live == lat->live && g.tblock == lat->tblock &&
+        g.kzero == (lat->kcur == 0))
+      hit = &g;
   if (!hit) {
     // capture the k steps without touching the handle's state
     const int live0 = lat->live;
@@ -844,7 +925,7 @@ static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every, int* flips)
     if (e != cudaSuccess) return e;
     int64_t t = lat->step;
     for (int s = 0; s < k && e == cudaSuccess;) {
-      const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[0];
+      const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[2];
       if (pairs && s + 2 <= k && fuse_pair(lat, t, check_every, check_every)) {
         e = fdtd_pair(lat, scale, tzc);
         s += 2;
@@ -879,7 +960,7 @@ static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every, int* flips)
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) return e;
-    lat->graphs.push_back({check_every, live0, lat->tblock, exec, nflip, nlaunch});
+    lat->graphs.push_back({check_every, live0, lat->tblock, lat->kcur == 0 ? 1 : 0, exec, nflip, nlaunch});
     hit = &lat->graphs.back();
   }
   cudaError_t e = cudaGraphLaunch(hit->exec, lat->st);
@@ -904,7 +985,7 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
     const int64_t t = lat->step;
     const double tau_t = lat->tau;
     const bool check = check_every > 0 && t % check_every == 0;
-    const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[0];
+    const double* scale = lat->pending_scale ? &lat->sc()->scale[1] : &lat->sc()->scale[2];
     if (done + 2 <= max_steps && fuse_pair(lat, t, check_every, snap_every)) {
       const int tzc = tuned_tb_zchunk(lat);
       QF_CUDA(lat, fdtd_pair(lat, scale, tzc));
@@ -919,7 +1000,7 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
     QF_CUDA(lat, after_step(lat, check, nb, snap_every, lat->st));
     ++done;
     if (check) {
-      double e3[3];
+      double e3[5];
       qf_status s = read_energy(lat, e3);
       if (s != QF_OK) return s;
       if (record_check(lat, e3, t, tau_t, tol_abs, 0.0)) {
@@ -943,6 +1024,10 @@ extern "C" qf_status qf_step_n(qf_lattice* lat, int64_t max_steps, double tol_ab
           continue;
         }
         for (int s = 0; s < k; ++s) lat->tau += lat->dtau;
+        // the first replayed step renormalises (2^(kcur+jcur) / sqrt(norm at K_check)),
+        // the others scale by 2^kcur
+        lat->K += (long long)k * lat->kcur + lat->jcur - lat->K_check;
+        lat->renorm_step = lat->step;
         if (fdtd) {
           lat->live ^= flips & 1;
           lat->clean = true;
@@ -979,7 +1064,7 @@ static qf_status measure(qf_lattice* lat, void* f, qf_energy* out) {
   // FFT terms transform through tmp and read f; FDTD reads f only
   QF_CUDA(lat, kinetic_pass(lat, f, f, false, true, &lat->sc()->scale[0], &nb));
   QF_CUDA(lat, launch(lat, K_FINISH, [&] { return launch_finish(lat->partials(), nb, lat->sc(), 0, lat->st); }));
-  double e3[3];
+  double e3[5];
   qf_status s = read_energy(lat, e3);
   if (s != QF_OK) return s;
   out->e_re = e3[0];
@@ -1038,6 +1123,46 @@ extern "C" qf_status qf_project_excited(qf_lattice* lat, int n_states, qf_energy
   return QF_OK;
 }
 
+extern "C" qf_status qf_track_excited(qf_lattice* lat, int n_states, qf_energy* out) {
+  if (!lat || !out) return QF_EINVAL;
+  if (lat->exc_records > 0 && n_states != lat->exc_n)
+    return fail(lat, QF_EINVAL, "n_states differs from the one of this history");
+  qf_status s = qf_project_excited(lat, n_states, out);
+  if (s != QF_OK) return s;
+  const int j = lat->exc_records;
+  if (j >= 1) {
+    for (int i = 0; i < n_states; ++i) {
+      const double d = hypot(out[i].e_re - lat->exc_prev[i].e_re, out[i].e_im - lat->exc_prev[i].e_im);
+      if (lat->plat_have[i] && !(d < lat->plat[i].de)) continue;
+      lat->plat_have[i] = true;
+      lat->plat[i] = out[i];
+      lat->plat[i].de = d;
+      lat->plat_rec[i] = j;
+      if (i < lat->d.plateau_slots) {
+        QF_CUDA(lat, cudaMemcpyAsync(lat->plateau_state(i), lat->state(i), (size_t)lat->sites * (lat->c64() ? 8 : 16),
+                                     cudaMemcpyDeviceToDevice, lat->st));
+        lat->have_plateau_state[i] = true;
+      }
+    }
+  }
+  for (int i = 0; i < n_states; ++i) lat->exc_prev[i] = out[i];
+  lat->exc_n = n_states;
+  lat->exc_records = j + 1;
+  QF_CUDA(lat, cudaStreamSynchronize(lat->st));
+  return QF_OK;
+}
+
+extern "C" qf_status qf_excited_plateau(qf_lattice* lat, int n_states, qf_energy* out, int* record) {
+  if (!lat || !out) return QF_EINVAL;
+  if (lat->exc_records < 2) return fail(lat, QF_ESTATE, "fewer than two records of E_i(tau)");
+  if (n_states < 1 || n_states > lat->exc_n) return fail(lat, QF_EINVAL, "n_states exceeds the history's");
+  for (int i = 0; i < n_states; ++i) {
+    out[i] = lat->plat[i];
+    if (record) record[i] = lat->plat_rec[i];
+  }
+  return QF_OK;
+}
+
 template <typename R>
 static qf_status parity_t(qf_lattice* lat, int which, int axis, void* target) {
   const int nblk = field_blocks();
@@ -1056,12 +1181,17 @@ extern "C" qf_status qf_parity_project(qf_lattice* lat, int which, int axis, int
   if (!lat) return QF_EINVAL;
   if (which < QF_P_PLUS || which > QF_P_D2_K) return fail(lat, QF_EINVAL, "unknown projector");
   if (which >= QF_P_MINUS_PK && (axis < 1 || axis > 3)) return fail(lat, QF_EINVAL, "axis must be 1..3");
-  if (target < -1 || target > 2) return fail(lat, QF_EINVAL, "target must be -1..2");
+  if (!(target >= -1 && target <= 2) && !(target >= 200 && target < 200 + lat->d.plateau_slots))
+    return fail(lat, QF_EINVAL, "target must be -1..2 or a plateau slot 200 + i");
   void* f = slot_ptr(lat, target);
   if (!f || (target == -1 && !lat->have_psi)) return fail(lat, QF_ESTATE, "target holds no field");
   qf_status s = lat->c64() ? parity_t<float>(lat, which, axis, f) : parity_t<double>(lat, which, axis, f);
   if (s != QF_OK) return s;
-  if (target == -1) lat->pending_scale = false;
+  if (target == -1) {
+    lat->pending_scale = false;
+    lat->K = 0;  // renormalised to unit norm
+    lat->renorm_step = lat->step;
+  }
   return QF_OK;
 }
 
@@ -1150,6 +1280,8 @@ extern "C" qf_status qf_prolong(qf_lattice* coarse, int coarse_slot, qf_lattice*
   if (s != QF_OK) return s;
   fine->have_psi = true;
   fine->pending_scale = false;
+  fine->K = slot_exp2(coarse, coarse_slot);  // the interpolant of the stored coarse field
+  fine->renorm_step = -1;
   return QF_OK;
 }
 
@@ -1164,6 +1296,7 @@ extern "C" qf_status qf_get_info(qf_lattice* lat, qf_info* out) {
   out->launches = lat->launches;
   out->temporal_block = lat->tblock;
   out->fft_passes = lat->kinetic == QF_KIN_FDTD ? 0 : uses_fft2(lat) ? 2 : 4;
+  out->field_exp2 = lat->K;
   return QF_OK;
 }
 
@@ -1267,6 +1400,7 @@ struct qf_batch {
   std::vector<Member> m;
   std::string err;
   int64_t launches = 0;
+  int rule = QF_STOP_DIFFERENCE;
 };
 
 static qf_status bfail(qf_batch* b, qf_status s, const std::string& msg) {
@@ -1377,7 +1511,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
     for (int k = 0; k < R; ++k) {
       if (done[k]) continue;
       qf_lattice* L = b->m[run[k]].lat;
-      const double* sk = L->pending_scale ? &L->sc()->scale[1] : &L->sc()->scale[0];
+      const double* sk = L->pending_scale ? &L->sc()->scale[1] : &L->sc()->scale[2];
       const bool fdtd = L->kinetic == QF_KIN_FDTD;
       if (!L->c64()) {
         void* in = L->psi();
@@ -1405,7 +1539,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
           for (int j = 0; j < cnt; ++j) {
             const int q = g[off + j];
             qf_lattice* M = b->m[run[q]].lat;
-            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
+            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
             if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0))
               return bfail(b, QF_ECUDA, "tensor map encoding failed");
             // one error flag per launch: the first member's
@@ -1422,7 +1556,7 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
           for (int j = 0; j < cnt; ++j) {
             const int q = g[off + j];
             qf_lattice* M = b->m[run[q]].lat;
-            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[0];
+            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
             fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
             fg.a[j].emit_next = 1;
             nblk[q] = two ? fft2_final_blocks() : fft_final_blocks<float>(n);
@@ -1455,16 +1589,16 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
       any_check = any_check || chk[k];
     }
     if (any_check) {
-      e3.assign(3 * R, 0.0);
+      e3.assign(5 * R, 0.0);
       for (int k = 0; k < R; ++k)
         if (chk[k])
-          QF_BCUDA(b, cudaMemcpyAsync(&e3[3 * k], b->m[run[k]].lat->sc()->energy, 3 * sizeof(double),
+          QF_BCUDA(b, cudaMemcpyAsync(&e3[5 * k], b->m[run[k]].lat->sc()->energy, 5 * sizeof(double),
                                       cudaMemcpyDeviceToHost, st));
       QF_BCUDA(b, cudaStreamSynchronize(st));
       for (int k = 0; k < R; ++k) {
         if (!chk[k]) continue;
         auto& mb = b->m[run[k]];
-        if (record_check(mb.lat, &e3[3 * k], t_of[k], tau_t[k], mb.tol_abs, mb.tol_rel)) mb.status = QF_OK;
+        if (record_check(mb.lat, &e3[5 * k], t_of[k], tau_t[k], mb.tol_abs, mb.tol_rel, b->rule)) mb.status = QF_OK;
       }
     }
   }
@@ -1480,6 +1614,13 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
     nr += x.status == QF_BATCH_RUNNING;
   }
   if (n_running) *n_running = nr;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_set_stopping(qf_batch* b, int rule) {
+  if (!b) return QF_EINVAL;
+  if (rule != QF_STOP_DIFFERENCE && rule != QF_STOP_EXTRAPOLATED) return bfail(b, QF_EINVAL, "unknown stopping rule");
+  b->rule = rule;
   return QF_OK;
 }
 

@@ -46,15 +46,21 @@ constexpr int kNumSums = 5;  // <psi|psi>, Re/Im <psi|H_K psi>, Re/Im <psi|V psi
 constexpr int kPartialStride = 8;
 
 // Device-resident scalars of one lattice (lives in the caller's workspace).
+// Output scale of a step: [0] = 1 (no scaling); [1] = 2^(k+j) / sqrt(norm of the last
+// check), the step after a check; [2] = 2^k, the other steps.  The powers of two (exact
+// in floating point) keep a field that decays by about lambda per step near unit size
+// between checks (k ~ -log2 lambda, j centres the interval's residual growth; both chosen
+// by the finishing kernel of each check); the host tracks the accumulated power of two
+// and removes it from every field it hands out.
 struct DevScalars {
-  double scale[2];     // [0] = 1 always; [1] = 1/sqrt(norm) of the last check
+  double scale[4];     // see above; [3] unused
   double sums[8];      // last finished reduction (kNumSums used)
-  double energy[4];    // e_re, e_im, norm of the last finished reduction
+  double energy[6];    // e_re, e_im, norm of the last finished reduction; k, j of the scale
   double gs_coef[8];   // Gram-Schmidt coefficients <v_i|w> (complex, up to 3) + spare
   double gs_scale[2];  // 1/||w|| of the current Gram-Schmidt vector
   double parity_scale[2];
   int err[2];          // [0]: a bounded device wait ran out (QF_ETIMEOUT)
-  double spare[5];
+  double spare[1];
 };
 
 // Arguments of one pass of the FFT kinetic step.
@@ -225,10 +231,12 @@ bool fft_supported(int n);
 template <typename R>
 int stencil_blocks(int n, int zc = 0);
 
-// Finishing reduction: sums nblocks partial rows in index order into sc->sums, then
-// energy and (when set_scale) sc->scale[1] = 1/sqrt(norm).
+// Finishing reduction: sums nblocks partial rows in index order into sc->sums, then the
+// energy; with set_scale also the step scales sc->scale[1..2] and their exponents k, j in
+// sc->energy[3..4].  interval > 0: steps since the field last had about unit norm, from
+// which the per-step decay is measured; interval 0: estimated from the energy and dtau.
 cudaError_t launch_finish(const double* partials, int nblocks, DevScalars* sc, int set_scale,
-                          cudaStream_t st);
+                          cudaStream_t st, int interval = -1, double dtau = 0.0);
 
 // Gram-Schmidt and field helpers (FP64 accumulation).
 template <typename R>
@@ -251,7 +259,7 @@ cudaError_t launch_parity(cpx<R>* dst, const cpx<R>* src, int n, int which, int 
 template <typename R>
 cudaError_t launch_from_f64(cpx<R>* dst, const double* src, long long n_elems_complex, cudaStream_t st);
 template <typename R>
-cudaError_t launch_to_f64(double* dst, const cpx<R>* src, const double* s, long long n_complex,
+cudaError_t launch_to_f64(double* dst, const cpx<R>* src, double factor, long long n_complex,
                           cudaStream_t st);
 template <typename R>
 cudaError_t launch_real_from_f64(R* dst, const double* src, long long n, cudaStream_t st);

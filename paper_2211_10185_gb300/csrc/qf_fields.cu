@@ -15,7 +15,8 @@ int field_blocks() { return 152 * 4; }  // 4 blocks per SM of the 152-SM GB300
 // Finishing reduction of per-block partial sums
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ partials, int nblocks,
-                                                     DevScalars* sc, int set_scale) {
+                                                     DevScalars* sc, int set_scale, int interval,
+                                                     double dtau) {
   __shared__ double red_s[32 * kNumSums];
   __shared__ double tot[kNumSums];
   double s[kNumSums] = {0, 0, 0, 0, 0};
@@ -31,12 +32,40 @@ __global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ 
     sc->energy[0] = (tot[1] + tot[3]) / nrm;
     sc->energy[1] = (tot[2] + tot[4]) / nrm;
     sc->energy[2] = nrm;
-    if (set_scale) sc->scale[1] = nrm > 0 ? 1.0 / sqrt(nrm) : 1.0;
+    if (set_scale) {
+      // The field started the interval at about 2^j (unit norm times the centring power
+      // of its renormalising step) and grew by lambda 2^k per step, lambda the step's
+      // decay: log2 lambda ~ (log2(norm)/2 - j)/interval - k.  The next k cancels lambda
+      // to within 2^(+-1/2) per step, and the next j starts the field at 2^(-r c/2) for the
+      // residual r, so it ends the next interval of the same length near 2^(+r c/2).
+      int k = (int)sc->energy[3], j = (int)sc->energy[4];
+      if (interval > 0 && nrm > 0 && isfinite(nrm)) {
+        const double lam = (0.5 * log2(nrm) - j) / interval - k;
+        const double kn = fmin(fmax(rint(-lam), -30.0), 30.0);
+        const double jn = fmin(fmax(-rint(0.5 * (lam + kn) * (interval - 1)), -60.0), 60.0);
+        k = (int)kn;
+        j = (int)jn;
+      } else if (interval == 0 && dtau > 0 && nrm > 0) {
+        // no decay measured yet: a state of energy E shrinks by about
+        // (1 - dtau E/2) / (1 + dtau E/2) per step
+        const double e = sc->energy[0];
+        const double q = fabs((1.0 - 0.5 * dtau * e) / (1.0 + 0.5 * dtau * e));
+        if (q > 0 && isfinite(q)) {
+          k = (int)fmin(fmax(rint(-log2(q)), -30.0), 30.0);
+          j = 0;
+        }
+      }
+      sc->scale[1] = nrm > 0 ? ldexp(1.0, k + j) / sqrt(nrm) : ldexp(1.0, k + j);
+      sc->scale[2] = ldexp(1.0, k);
+      sc->energy[3] = (double)k;
+      sc->energy[4] = (double)j;
+    }
   }
 }
 
-cudaError_t launch_finish(const double* partials, int nblocks, DevScalars* sc, int set_scale, cudaStream_t st) {
-  finish_kernel<<<1, 256, 0, st>>>(partials, nblocks, sc, set_scale);
+cudaError_t launch_finish(const double* partials, int nblocks, DevScalars* sc, int set_scale, cudaStream_t st,
+                          int interval, double dtau) {
+  finish_kernel<<<1, 256, 0, st>>>(partials, nblocks, sc, set_scale, interval, dtau);
   return cudaGetLastError();
 }
 
@@ -303,8 +332,7 @@ cudaError_t launch_from_f64(cpx<R>* dst, const double* src, long long n, cudaStr
 }
 
 template <typename R>
-__global__ void to_f64_kernel(double* dst, const cpx<R>* __restrict__ src, const double* s, long long n) {
-  const double f = s ? *s : 1.0;
+__global__ void to_f64_kernel(double* dst, const cpx<R>* __restrict__ src, double f, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const cpx<R> x = src[i];
@@ -313,8 +341,8 @@ __global__ void to_f64_kernel(double* dst, const cpx<R>* __restrict__ src, const
   }
 }
 template <typename R>
-cudaError_t launch_to_f64(double* dst, const cpx<R>* src, const double* s, long long n, cudaStream_t st) {
-  to_f64_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(dst, src, s, n);
+cudaError_t launch_to_f64(double* dst, const cpx<R>* src, double f, long long n, cudaStream_t st) {
+  to_f64_kernel<R><<<field_blocks(), kFieldThreads, 0, st>>>(dst, src, f, n);
   return cudaGetLastError();
 }
 
@@ -447,7 +475,7 @@ cudaError_t launch_pad_spectrum(const cpx<R>* coarse, int nc, cpx<R>* fine, doub
   template cudaError_t launch_scale_copy<R>(cpx<R>*, const cpx<R>*, const double*, long long, cudaStream_t); \
   template cudaError_t launch_parity<R>(cpx<R>*, const cpx<R>*, int, int, int, double*, int, cudaStream_t); \
   template cudaError_t launch_from_f64<R>(cpx<R>*, const double*, long long, cudaStream_t);                 \
-  template cudaError_t launch_to_f64<R>(double*, const cpx<R>*, const double*, long long, cudaStream_t);    \
+  template cudaError_t launch_to_f64<R>(double*, const cpx<R>*, double, long long, cudaStream_t);    \
   template cudaError_t launch_real_from_f64<R>(R*, const double*, long long, cudaStream_t);                 \
   template cudaError_t launch_pack_f64<R>(cpx<R>*, const double*, const double*, long long, cudaStream_t); \
   template cudaError_t launch_momentum_hist<R>(const cpx<R>*, int, int, const double*, unsigned long long*, int,  \

@@ -25,13 +25,13 @@ def _check(lat_handle, status, where, ok=(Q.QF_OK,)):
 
 class Lattice:
     def __init__(self, n: int, a: float, precision: str = "c64", n_snap: int = 3, stream=None,
-                 device: int | None = None):
+                 device: int | None = None, plateau_slots: int = 0):
         import torch
 
         self.lib = Q.load()
         self.n, self.a = int(n), float(a)
         self.prec = Q.QF_PREC_C64 if precision == "c64" else Q.QF_PREC_C128
-        self.desc = Q.qf_lattice_desc(self.n, self.a, self.prec, int(n_snap))
+        self.desc = Q.qf_lattice_desc(self.n, self.a, self.prec, int(n_snap), int(plateau_slots))
         nbytes = C.c_size_t()
         _check(None, self.lib.qf_workspace_bytes(C.byref(self.desc), C.byref(nbytes)), "qf_workspace_bytes")
         dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -104,6 +104,19 @@ class Lattice:
         _check(self.h, self.lib.qf_project_excited(self.h, int(n_states), out), "qf_project_excited")
         return [out[i].as_dict() for i in range(n_states)]
 
+    def track_excited(self, n_states: int = 3):
+        """Gram-Schmidt of the latest snapshots now, recorded for the plateau of E_i(tau)."""
+        out = (Q.qf_energy * n_states)()
+        _check(self.h, self.lib.qf_track_excited(self.h, int(n_states), out), "qf_track_excited")
+        return [out[i].as_dict() for i in range(n_states)]
+
+    def excited_plateau(self, n_states: int = 3):
+        """[(record index, energy record)] of the chosen plateau record per state."""
+        out = (Q.qf_energy * n_states)()
+        rec = (C.c_int * n_states)()
+        _check(self.h, self.lib.qf_excited_plateau(self.h, int(n_states), out, rec), "qf_excited_plateau")
+        return [(rec[i], out[i].as_dict()) for i in range(n_states)]
+
     def parity_project(self, which: int, axis: int = 3, target: int = -1):
         _check(self.h, self.lib.qf_parity_project(self.h, int(which), int(axis), int(target)),
                "qf_parity_project")
@@ -128,7 +141,7 @@ class Lattice:
         _check(self.h, self.lib.qf_get_info(self.h, C.byref(i)), "qf_get_info")
         return dict(dtau=i.dtau, step=i.step, tau=i.tau, kinetic=i.kinetic, n_snapshots=i.n_snapshots,
                     workspace_bytes=i.workspace_bytes, launches=i.launches, temporal_block=i.temporal_block,
-                    fft_passes=i.fft_passes)
+                    fft_passes=i.fft_passes, field_exp2=i.field_exp2)
 
     def use_graphs(self, enable: bool = True):
         _check(self.h, self.lib.qf_use_graphs(self.h, int(bool(enable))), "qf_use_graphs")

@@ -18,10 +18,12 @@ QF_KIN_FDTD, QF_KIN_FFT_NAIVE, QF_KIN_FFT_SYMANZIK, QF_KIN_FFT_REL = range(4)
 QF_PREC_C64, QF_PREC_C128 = 0, 1
 QF_P_PLUS, QF_P_MINUS, QF_P_MINUS_PK, QF_P_D_K, QF_P_D2_K = 0, 1, 2, 3, 4
 QF_BATCH_RUNNING = -1
+QF_STOP_DIFFERENCE, QF_STOP_EXTRAPOLATED = 0, 1
 
 
 class qf_lattice_desc(C.Structure):
-    _fields_ = [("n", C.c_int), ("a", C.c_double), ("prec", C.c_int), ("n_snap", C.c_int)]
+    _fields_ = [("n", C.c_int), ("a", C.c_double), ("prec", C.c_int), ("n_snap", C.c_int),
+                ("plateau_slots", C.c_int)]
 
 
 class qf_energy(C.Structure):
@@ -36,7 +38,7 @@ class qf_energy(C.Structure):
 class qf_info(C.Structure):
     _fields_ = [("dtau", C.c_double), ("step", C.c_int64), ("tau", C.c_double), ("kinetic", C.c_int),
                 ("n_snapshots", C.c_int), ("workspace_bytes", C.c_size_t), ("launches", C.c_int64),
-                ("temporal_block", C.c_int), ("fft_passes", C.c_int)]
+                ("temporal_block", C.c_int), ("fft_passes", C.c_int), ("field_exp2", C.c_int64)]
 
 
 class qf_kernel_stat(C.Structure):
@@ -58,6 +60,8 @@ SIGNATURES = {
     "qf_energies": (C.c_int, [_P, C.POINTER(qf_energy)]),
     "qf_project_excited": (C.c_int, [_P, C.c_int, C.POINTER(qf_energy)]),
     "qf_parity_project": (C.c_int, [_P, C.c_int, C.c_int, C.c_int]),
+    "qf_track_excited": (C.c_int, [_P, C.c_int, C.POINTER(qf_energy)]),
+    "qf_excited_plateau": (C.c_int, [_P, C.c_int, C.POINTER(qf_energy), C.POINTER(C.c_int)]),
     "qf_get_info": (C.c_int, [_P, C.POINTER(qf_info)]),
     "qf_prolong": (C.c_int, [_P, C.c_int, _P]),
     "qf_momentum_distribution": (C.c_int, [_P, C.c_int, _D, _D, _D, C.c_int, C.POINTER(C.c_int)]),
@@ -73,6 +77,7 @@ SIGNATURES = {
     "qf_batch_step": (C.c_int, [_P, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "qf_batch_members": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int]),
     "qf_batch_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "qf_batch_set_stopping": (C.c_int, [_P, C.c_int]),
     "qf_batch_last_error": (C.c_char_p, [_P]),
     "qf_selftest_bounded_wait": (C.c_int, [_P]),
     "qf_use_graphs": (C.c_int, [_P, C.c_int]),

@@ -64,6 +64,10 @@ class Batch:
         self._check(self.lib.qf_batch_members(self.h, C.byref(cnt), st, sd, n), "qf_batch_members")
         return [(st[i], sd[i]) for i in range(cnt.value)]
 
+    def set_stopping(self, rule: int):
+        """Q.QF_STOP_DIFFERENCE or Q.QF_STOP_EXTRAPOLATED for the members' checks."""
+        self._check(self.lib.qf_batch_set_stopping(self.h, int(rule)), "qf_batch_set_stopping")
+
     def launches(self) -> int:
         x = C.c_int64()
         self._check(self.lib.qf_batch_info(self.h, C.byref(x)), "qf_batch_info")
@@ -94,7 +98,7 @@ class Request:
     seed: int
     precision: str = "c64"
     tol_abs: float = 1e-7
-    tol_rel: float = 1e-7
+    tol_rel: float = 1e-6
     max_steps: int = 20000
     dtau: float | None = None
     warm_start: bool = False   # solve on N/2 first, then prolong (FFT kinetic terms)
@@ -155,7 +159,8 @@ def served_mix(count: int, rate: float = 200.0, sizes=(32, 48, 64, 96, 128, 192,
                max_steps: int = 20000, box: float = 16.0, kinetics=(0, 1, 2, 3)) -> list[Request]:
     """Poisson arrivals (rate per second) of Cornell solves: N uniform over ``sizes``,
     kinetic term uniform over ``kinetics``, kappa ~ U[.3, .6], sigma ~ U[.1, .25],
-    m ~ U[.3, 5], a = box / N, default dtau, tol = 1e-7 (1 + |E|).  Drawn from
+    m ~ U[.3, 5], a = box / N, default dtau, tol = 1e-7 + 1e-6 |E| on the distance left
+    to the converged energy (the batch's extrapolated stopping rule).  Drawn from
     numpy.random.default_rng(seed) in that order per request."""
     rng = np.random.default_rng(seed)
     t = 0.0
@@ -174,12 +179,16 @@ def served_mix(count: int, rate: float = 200.0, sizes=(32, 48, 64, 96, 128, 192,
 
 class Server:
     """Admits requests by device-workspace footprint into one batch and advances the
-    batch in chunks of ``chunk`` steps; finished solves free their memory at once."""
+    batch in chunks of ``chunk`` steps; finished solves free their memory at once.  A
+    solve stops when the distance left to its converged energy, extrapolated from the
+    last two check differences, is below its tolerance (QF_STOP_EXTRAPOLATED)."""
 
-    def __init__(self, hbm_budget_bytes: int, chunk: int = 64, stream=None):
+    def __init__(self, hbm_budget_bytes: int, chunk: int = 64, stream=None,
+                 stopping: int = Q.QF_STOP_EXTRAPOLATED):
         self.budget = int(hbm_budget_bytes)
         self.chunk = int(chunk)
         self.batch = Batch(stream)
+        self.batch.set_stopping(stopping)
         self.queue: list[Request] = []
         self.active: dict[int, tuple[Request, Lattice, float]] = {}
         self.in_use = 0

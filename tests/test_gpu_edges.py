@@ -13,6 +13,7 @@ import math
 import numpy as np
 import pytest
 
+from fieldcheck import assert_field_close
 from oracle import qfdtd_oracle as O
 from paper_2211_10185_gb300 import inputs as I
 
@@ -93,7 +94,7 @@ def test_plane_wave_closed_form_at_n256(kind, two_pass):
     lam = (1 - dtau * v0 / 2 - dtau * _symbol(kind, k, a, m)) / (1 + dtau * v0 / 2)
     got = lat.get_wavefunction()
     want = lam ** steps * psi
-    assert np.linalg.norm((got - want).ravel()) / np.linalg.norm(want.ravel()) < 2e-6 * steps * math.log2(n)
+    assert_field_close(got, want, 2e-6 * steps * math.log2(n))
 
 
 @pytest.mark.parametrize("prec,offset", [("c64", 0), ("c128", 0), ("c64", 1)])
@@ -113,3 +114,32 @@ def test_upload_from_page_locked_memory_matches_pageable(prec, offset):
     two = _lat(n, a, I.FFT_SYMANZIK, 1.0, I.harmonic(n, a), np.zeros_like(psi), prec)
     two.set_wavefunction_raw(view)
     assert np.array_equal(one.get_wavefunction(), two.get_wavefunction())
+
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+@pytest.mark.parametrize("check_every", [64, 256])
+def test_fast_decay_between_checks_stays_in_range(prec, check_every):
+    """A heavy quark with the relativistic term (N=16, a=1, m=3.77) decays by ~0.59 per
+    step, so between checks the field falls by 1e-15 (64 steps) to 1e-58 (256 steps):
+    below what complex FP32 holds.  The steps scale by exact powers of two and the
+    library removes them on readback: energies, norms and fields equal the oracle's."""
+    n, a, m = 16, 1.0, 3.7744603079583525
+    v = I.cornell(n, a, 0.43989095916094956, 0.11908043740877956, 0.0)
+    r = I.radius(n, a)
+    psi0 = np.exp(-0.5 * (r / 0.5) ** 2).astype(complex)
+    lat = _lat(n, a, I.FFT_REL, m, v, psi0, prec)
+    ref = O.Lattice(n, a)
+    ref.set_potential(v)
+    ref.set_kinetic(O.FFT_REL, m)
+    ref.set_wavefunction(psi0)
+    e_tol = {"c64": 1e-5, "c128": 1e-10}[prec]
+    for _ in range(4):
+        lat.step_n(check_every, tol=0.0, check_every=check_every)
+        ref.step_n(check_every, check_every=check_every)
+        eg, er = lat.energies(), ref.energies()
+        assert abs(eg["e"] - er["e"]) < e_tol * abs(er["e"]), (eg["e"], er["e"])
+        assert eg["norm"] == pytest.approx(er["norm"], rel=e_tol)
+    assert lat.info()["field_exp2"] != 0       # the stored field was rescaled
+    assert_field_close(lat.get_wavefunction(), ref.psi, {"c64": 2e-4, "c128": 1e-10}[prec])
+    # the oracle's converged energy (3.5286693398...) is reached
+    assert abs(lat.energies()["e"].real - 3.528669339857) < 1e-5 * 3.53

@@ -10,6 +10,7 @@ import math
 import numpy as np
 import pytest
 
+from fieldcheck import assert_field_close
 from oracle import qfdtd_oracle as O
 from paper_2211_10185_gb300 import inputs as I
 
@@ -59,22 +60,36 @@ FIELD_TOL = {"c128": 1e-12, "c64": 2e-6}
 E_TOL = {"c128": 1e-10, "c64": 1e-5}
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
-@pytest.mark.parametrize("kind", KINDS)
-@pytest.mark.parametrize("n", [8, 12, 16, 24, 48])
-def test_one_step_matches_oracle(n, kind, prec):
-    a, m = 0.2, 1.3
-    v = I.cornell(n, a, 0.5, 0.2)
+def _one_step(n, kind, prec, a=0.2, m=1.3, v=None):
+    v = I.cornell(n, a, 0.5, 0.2) if v is None else v
     ref, gpu = _pair(n, a, kind, m, prec, v, seed=n)
     ref.step_n(1, check_every=1)
     st, done = gpu.step_n(1, check_every=1)
     assert done == 1
-    tol = FIELD_TOL[prec] * (1 + math.log2(n))
-    assert _rel(gpu.get_wavefunction(), ref.psi) < tol
+    assert_field_close(gpu.get_wavefunction(), ref.psi, FIELD_TOL[prec] * (1 + math.log2(n)), what=f"N={n}")
     e_ref, e_gpu = ref.energies(), gpu.energies()
     assert abs(e_gpu["e"] - e_ref["e"]) < E_TOL[prec] * abs(e_ref["e"])
     assert e_gpu["norm"] == pytest.approx(e_ref["norm"], rel=E_TOL[prec])
     assert e_gpu["step"] == 0
+    gpu.close()
+
+
+# every FFT plan the library ships below 256 (radix 16/8/4/3 stage shapes and tile
+# geometries differ per size); FDTD at the same sizes
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n", [8, 12, 16, 24, 32, 48, 64, 96, 128, 192])
+def test_one_step_matches_oracle(n, kind, prec):
+    _one_step(n, kind, prec)
+
+
+@pytest.mark.parametrize("prec,kind,cplx", [("c64", O.FFT_REL, False), ("c128", O.FFT_SYMANZIK, True)])
+def test_one_step_matches_oracle_n384(prec, kind, cplx):
+    n, a = 384, 0.05
+    v = I.cornell(n, a, 0.4, 0.2)
+    if cplx:
+        v = v - 0.05j * np.abs(v)
+    _one_step(n, kind, prec, a=a, m=0.7, v=v)
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -91,7 +106,7 @@ def test_many_steps_with_checks_and_complex_potential(kind, prec):
     assert abs(e_gpu["e"] - e_ref["e"]) < E_TOL[prec] * abs(e_ref["e"])
     assert abs(e_gpu["de"] - e_ref["de"]) < max(1e-6 if prec == "c64" else 1e-12, 1e-3 * e_ref["de"])
     tol = {"c128": 1e-10, "c64": 2e-4}[prec]
-    assert _rel(gpu.get_wavefunction(), ref.psi) < tol
+    assert_field_close(gpu.get_wavefunction(), ref.psi, tol)
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -109,30 +124,79 @@ def test_harmonic_fdtd_converges_like_the_oracle(prec):
     assert abs(e_gpu - e_ref) < E_TOL[prec] * abs(e_ref)
 
 
+def _pair_plateau(n, a, kind, m, prec, v, seed, dtau):
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    ref, gpu = _pair(n, a, kind, m, prec, v, seed=seed, dtau=dtau)
+    gpu.close()
+    gpu = Lattice(n, a, precision=prec, plateau_slots=3)
+    gpu.set_potential(v)
+    gpu.set_kinetic(kind, m, dtau)
+    psi0 = I.gaussian_field(n, seed)
+    gpu.set_wavefunction(I.zero_dirichlet_planes(psi0) if kind == O.FDTD else psi0)
+    return ref, gpu
+
+
 @pytest.mark.parametrize("prec", ["c128", "c64"])
 @pytest.mark.parametrize("kind", [O.FDTD, O.FFT_SYMANZIK])
-def test_excited_states_match_oracle_at_identical_snapshots(kind, prec):
-    # The snapshots hold Psi_2 at relative weight ~exp(-2 tau) (gaps of 1).  FP32 fields
-    # resolve it only while that weight is well above the accumulated FP32 rounding noise
-    # (~1e-7 per step), so the c64 comparison uses tau ~ 2.9 and c128 tau ~ 5.8.
+@pytest.mark.parametrize("snap", [32, 64])
+def test_excited_state_records_and_plateau_match_oracle(kind, prec, snap):
+    """E_i(tau_j) at every snapshot record, GPU against oracle at identical indices, and
+    the plateau choice (Sec. 4's saddle point of E_i(tau)).
+
+    A state's share of the snapshots decays like w_i = exp(-(E_i - E_0) tau); once it
+    nears the rounding of the field precision, E_i(tau_j) is rounding noise on either
+    side.  Records are therefore compared while w_i >= 5e-4 (complex FP32) or 1e-6 (FP64),
+    at 1e-5 relative for every energy of the FP32 path and 1e-10 / 1e-9 / 1e-8 for FP64.
+
+    The plateau: FP64 matches the oracle's choice to 1e-10.  In FP32 the plateau of E_1
+    is where its contamination by E_2 (decaying as exp(-(E_2 - E_1) tau)) meets the
+    FP32 noise of its shrinking share (growing as exp((E_1 - E_0) tau)); with the
+    oscillator's spectra that crossing is below 1e-5 for the FDTD term (E_2 - E_1 ~ 1.05)
+    and at ~3e-5 for the Eq. HK2 term (E_2 - E_1 ~ 0.66 against E_1 - E_0 ~ 1.07), where
+    E_1's plateau is checked at 1e-4.  E_0's plateau is within 1e-5 for both."""
     n, a, m = 16, 0.3, 1.0
-    ref, gpu = _pair(n, a, kind, m, prec, I.harmonic(n, a), seed=0, dtau=a * a / 8)
-    steps = 8 * 64 if prec == "c128" else 4 * 64
-    ref.step_n(steps, check_every=64, snap_every=32)
-    gpu.step_n(steps, check_every=64, snap_every=32)
-    st, ex_ref = ref.project_excited(3)
-    ex_gpu = gpu.project_excited(3)
-    tol = {"c128": [1e-10, 1e-9, 1e-8], "c64": [1e-5, 1e-4, 2e-3]}[prec]
-    for i in range(3):
-        er, eg = ex_ref[i]["e"], ex_gpu[i]["e"]
-        assert abs(eg - er) < tol[i] * abs(er), (i, eg, er)
-        assert ex_gpu[i]["norm"] == pytest.approx(1.0, abs=1e-4 if prec == "c64" else 1e-12)
-    for i in range(3):
-        s_ref = ref.states[i]
-        s_gpu = gpu.get_wavefunction(i)
-        ph = np.vdot(s_gpu, s_ref)
-        # states agree up to a phase; c64 GS residuals carry FP32 noise / r_i
-        assert abs(abs(ph) - 1) < {"c128": 1e-8, "c64": 1e-2}[prec]
+    dtau = a * a / 8
+    ref, gpu = _pair_plateau(n, a, kind, m, prec, I.harmonic(n, a), 0, dtau)
+    n_rec = (24 * 64) // snap
+    rec_ref, rec_gpu = [], []
+    for j in range(n_rec + 2):
+        ref.step_n(snap, check_every=64, snap_every=snap)
+        gpu.step_n(snap, check_every=64, snap_every=snap)
+        if j >= 2:
+            rec_ref.append(ref.track_excited(3)[1])
+            rec_gpu.append(gpu.track_excited(3))
+    plat_ref = ref.excited_plateau(3)
+    e_pl = [p["e"].real for p in plat_ref]
+    w_min = {"c64": 5e-4, "c128": 1e-6}[prec]
+    tol = {"c64": [1e-5, 1e-5, 1e-5], "c128": [1e-10, 1e-9, 1e-8]}[prec]
+    compared = [0, 0, 0]
+    for er, eg in zip(rec_ref, rec_gpu):
+        tau = eg[0]["tau"]
+        assert tau == pytest.approx(er[0]["tau"], rel=1e-12) and eg[0]["step"] == er[0]["step"]
+        for i in range(3):
+            if math.exp(-(e_pl[i] - e_pl[0]) * tau) < w_min:
+                continue
+            compared[i] += 1
+            assert abs(eg[i]["e"] - er[i]["e"]) < tol[i] * abs(er[i]["e"]), (i, tau, eg[i]["e"], er[i]["e"])
+            assert eg[i]["norm"] == pytest.approx(1.0, abs=1e-5 if prec == "c64" else 1e-12)
+    assert min(compared) >= 3
+    plat_gpu = gpu.excited_plateau(3)
+    plat_tol = {"c128": [1e-10, 1e-10], "c64": [1e-5, 1e-5 if kind == O.FDTD else 1e-4]}[prec]
+    for i in (0, 1):
+        eg = plat_gpu[i][1]["e"]
+        assert abs(eg - plat_ref[i]["e"]) < plat_tol[i] * abs(plat_ref[i]["e"]), (i, eg, plat_ref[i]["e"])
+        # the chosen record's value is one of the GPU's own records
+        assert eg == rec_gpu[plat_gpu[i][0]][i]["e"]
+    # the kept state 1 is the oracle's plateau state up to a phase (the p-level is
+    # degenerate, but both sides carry the same combination from the same psi0)
+    s_gpu = gpu.get_wavefunction(201)
+    s_ref = plat_ref[1]["state"]
+    assert abs(abs(np.vdot(s_gpu, s_ref)) - 1) < (1e-4 if prec == "c64" else 1e-8)
+    # it is odd under the full mirror: P^- returns it unchanged (plateau slot as target)
+    gpu.parity_project(O.P_MINUS, 3, 201)
+    assert abs(abs(np.vdot(gpu.get_wavefunction(201), s_gpu)) - 1) < 1e-5
+    gpu.close()
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -146,7 +210,7 @@ def test_parity_projection_matches_oracle_and_is_exactly_symmetric(n, which, axi
     ref.parity_project(which, axis, -1)
     gpu.parity_project(which, axis, -1)
     out = gpu.get_wavefunction()
-    assert _rel(out, ref.psi) < {"c128": 1e-14, "c64": 1e-6}[prec]
+    assert_field_close(out, ref.psi, {"c128": 1e-14, "c64": 1e-6}[prec])
     # exact symmetry of the projected field (bitwise, also in FP32)
     if which == O.P_PLUS:
         assert np.array_equal(out, O.mirror(out))
@@ -270,5 +334,5 @@ def test_prolongation_matches_oracle(nc, prec):
     fine.prolong_from(coarse)
     ref = O.prolong(coarse.get_wavefunction())
     got = fine.get_wavefunction()
-    assert _rel(got, ref) < {"c128": 1e-13, "c64": 1e-6}[prec]
+    assert_field_close(got, ref, {"c128": 1e-13, "c64": 1e-6}[prec])
     assert np.max(np.abs(got[::2, ::2, ::2] - coarse.get_wavefunction())) < {"c128": 1e-12, "c64": 1e-5}[prec]
