@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-requests", type=int, default=96)
     ap.add_argument("--served-cap", type=int, default=3000)
+    ap.add_argument("--served-full", action="store_true",
+                    help="only the served mix, at its stated size: 2000 Poisson requests (200/s), "
+                         "N in {32..256}, cap 20000 steps, 170 GB; prints one JSON line")
     return ap.parse_args()
 
 
@@ -219,6 +222,7 @@ class OracleCores:
 def oracle_rate_cores(name, n, seconds, procs, min_steps=2):
     """Whole-host oracle throughput: ``procs`` lattices stepped together for about
     ``seconds``; returns (site-updates/s, steps per lattice, seconds)."""
+    n_sites = I.workload(name, n)["n"] ** 3
     pool = OracleCores(name, n, procs)
     try:
         pool.step()  # warm-up
@@ -232,7 +236,7 @@ def oracle_rate_cores(name, n, seconds, procs, min_steps=2):
                 break
     finally:
         pool.close()
-    return procs * n ** 3 * steps / el, steps, el
+    return procs * n_sites * steps / el, steps, el
 
 
 def run_reference(args):
@@ -493,7 +497,10 @@ def fp64_peak(size=4096, reps=3):
 # ---------------------------------------------------------------------------------------
 # Served mix: Poisson arrivals of Cornell solves, continuous batching
 # ---------------------------------------------------------------------------------------
-def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget=170e9, n_cmp=8):
+SERVED_SIZES = (32, 48, 64, 96, 128, 192, 256)
+
+
+def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget=170e9, n_cmp=8, warm=True):
     """Serves a seeded sample of the mixed workload in real time; then, on a subsample of
     small requests, compares the batched FP32 form with serial per-lattice FP64 solves,
     and on FFT-term requests with N >= 64, cold solves with warm-started ones."""
@@ -530,6 +537,8 @@ def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget
         "requests": len(sub), "fp32_batched_solves_per_s": len(sub) / t32, "fp64_alone_solves_per_s": len(sub) / t64,
         "max_rel_energy_err_fp32_vs_fp64": max(errs) if errs else None,
         "same_status": all(r32[i].status == r64[i].status for i in r64)}
+    if not warm:
+        return out
     # warm start across N: FFT-term requests with N >= 64, all arriving at once, solved cold
     # and warm (first on the N/2 lattice of the same box, then prolonged)
     sub = [r for r in reqs if r.kinetic != 0 and r.n >= 64][:n_cmp * 2]
@@ -773,9 +782,36 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_served_full(args):
+    """The served mix at its stated size (one GPU): Poisson arrivals in real time, admission
+    by HBM footprint into 170 GB, FP32 lattices batched with FP64 reductions; solves/s,
+    p50/p99 latency from arrival to retirement, converged/capped counts, and the FP32
+    batched vs FP64 per-lattice comparator on small requests."""
+    import torch
+
+    from paper_2211_10185_gb300 import build as B
+
+    torch.cuda.set_device(0)
+    B.build()
+    clocks = ClockSampler(torch.cuda.current_device())
+    t0 = time.perf_counter()
+    served = served_benchmark(2000, 20000, sizes=SERVED_SIZES, warm=False)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    line = {"metric": "served solves/s, p50/p99 latency to convergence", "value": served.get("solves_per_s"),
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic (seeded served mix)",
+            "config": {"workload": "2000 Cornell solves, Poisson 200/s, N in {32,48,64,96,128,192,256}, "
+                                   "kinetic uniform over FDTD/HK1/HK2/HK3, kappa U[.3,.6], sigma U[.1,.25], "
+                                   "m U[.3,5], a = 16/N, default dtau, cap 20000 steps, 170 GB"},
+            "served": served, "wall_s": wall, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.served_full:
+        run_served_full(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

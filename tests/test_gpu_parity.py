@@ -193,9 +193,10 @@ def test_excited_state_records_and_plateau_match_oracle(kind, prec, snap):
     s_gpu = gpu.get_wavefunction(201)
     s_ref = plat_ref[1]["state"]
     assert abs(abs(np.vdot(s_gpu, s_ref)) - 1) < (1e-4 if prec == "c64" else 1e-8)
-    # it is odd under the full mirror: P^- returns it unchanged (plateau slot as target)
+    # it is odd under the full mirror: P^- returns it unchanged (plateau slot as target),
+    # up to the even part its plateau record still carries (1 - overlap ~ |even part|^2/2)
     gpu.parity_project(O.P_MINUS, 3, 201)
-    assert abs(abs(np.vdot(gpu.get_wavefunction(201), s_gpu)) - 1) < 1e-5
+    assert abs(abs(np.vdot(gpu.get_wavefunction(201), s_gpu)) - 1) < (1e-4 if prec == "c64" else 1e-9)
     gpu.close()
 
 

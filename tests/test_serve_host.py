@@ -84,3 +84,13 @@ def test_roofline_byte_model():
     assert bench.algorithmic_bytes_per_site_update("c128", False) == 48
     assert bench.UPDATES_PER_LAUNCH.get("stencil_2step") == 2 and bench.UPDATES_PER_LAUNCH.get("fft2_xy_inv_update", 1) == 1
     assert bench.step_kernel("fft2_xy_inv_update") and not bench.step_kernel("fft2_yz_mid_T")
+
+
+def test_oracle_on_all_cores_uses_the_workloads_default_size():
+    # the bench's CPU baseline: one oracle lattice per process, lattice size from the
+    # workload when none is given (n=None)
+    import bench
+
+    rate, steps, el = bench.oracle_rate_cores("ho_fdtd_n32", None, 0.2, 2, min_steps=2)
+    assert steps >= 2 and el > 0
+    assert rate == pytest.approx(2 * 32 ** 3 * steps / el)
