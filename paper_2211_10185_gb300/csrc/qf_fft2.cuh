@@ -15,14 +15,16 @@
 //           (and the FP64 check sums), then pass A on psi_{t+1} for the next step.
 // Steady state: B + C = 16 + (8 + 8 + 4 + 8 + 8) B per site (real V) instead of 84.
 //
-// S layout (the scratch field, 2^24 elements): [kx_hi 128][k_lo 16][z 256][y_lo 16][kx_lo 2]
+// S layout (the scratch field, 2^24 elements): [kx_hi 128][k_lo 16][y_lo 16][z 256][kx_lo 2]
 // with kx = 2 kx_hi + kx_lo.  A pass-B block owns one (kx_hi, k_lo): 8192 contiguous
-// elements.  A pass-A/C block owns YL consecutive y_lo of one z: 16 YL lines
-// y = y_lo + 16 y_hi of the natural field, and in S 16 YL bytes per (kx_hi, k_lo).
+// elements, and reads its outer y DFTs' inputs straight from global memory (a warp reads
+// 256 contiguous bytes per y_lo).  A pass-A/C block owns one y_lo and the two z-planes
+// z0, z0 + 1: the 32 lines y = y_lo + 16 y_hi of both planes, and in S one 32-byte
+// sector (2 z x 2 kx_lo) per (kx_hi, k_lo).
 //
 // Shared-memory layouts are padded for conflict-free access: the A/C line tile has pitch
-// 280 (line YL y_hi + s, one pad element per 16), the B tile pitch 33 per z row plus one
-// element of skew per 16 rows.
+// 280 (line 2 y_hi + (z - z0), one pad element per 16); pass B exchanges through a
+// [k_hi][z][kx_lo] tile and per-warp buffers of pitch 280 (one pad element per 16).
 #pragma once
 #include "qf_fft_impl.cuh"
 
@@ -32,17 +34,18 @@ constexpr int F2_N = 256;
 constexpr int F2_THREADS = 512;                       // pass B block
 constexpr int F2_BLOCKS = 2048;                       // pass B blocks per lattice
 constexpr int F2_PL = 280;                            // A/C tile line pitch
-constexpr int F2_BP = 33;                             // B tile row pitch
+constexpr int F2_BPAD = 280;                          // B per-(warp, kx_lo) buffer pitch
 constexpr int F2_TW = plan_tw_size(F2_N);             // 255 per-stage twiddles
 constexpr int F2_TW1 = plan_tw_off(F2_N, 1);          // stage-1 block: w256^{k r}
 constexpr int F2_TWB = (F2_TW * 8 + 15) / 16 * 16;    // twiddle bytes in shared memory
-constexpr int F2_BTILE = F2_N * F2_BP + F2_N / 16;    // B tile elements (with the row skew)
+constexpr int F2_BTILE = 16 * 2 * F2_BPAD;            // B tile elements (exchange buffers)
 constexpr size_t F2_SMEM_B = F2_TWB + F2_N * 4 + (size_t)F2_BTILE * 8 + 32 * kNumSums * 8;
 constexpr long long F2_SKLO = (long long)F2_N * 32;   // S stride of k_lo
 
-// pass A / C geometry for YL y_lo per block
+// pass A / C geometry: YL = 2 z-planes of one y_lo per block
 template <int YL>
 struct F2AC {
+  static_assert(YL == 2, "a pass-A/C block holds two z-planes");
   static constexpr int THREADS = 256 * YL;
   static constexpr int LINES = 16 * YL;
   static constexpr int BLOCKS = 4096 / YL;
@@ -55,9 +58,9 @@ __device__ __forceinline__ cpx<float> f2_tw(const cpx<float>* tw_s, int ylo, int
 }
 
 __device__ __forceinline__ int f2_tile(int line, int e) { return line * F2_PL + e + (e >> 4); }
-// B tile: row z (odd pitch) plus one element of skew per 16 rows, so rows 16 apart (the
-// Stockham exchange) fall in different banks as well as consecutive rows
-__device__ __forceinline__ int f2_b(int row, int col) { return row * F2_BP + col + (row >> 4); }
+// B exchange buffer position: one pad element per 16 (pitch 280 = 8 mod 16 between the
+// two kx_lo buffers of a warp), so both Stockham access patterns are conflict-free
+__device__ __forceinline__ int f2_bpad(int p) { return p + (p >> 4); }
 
 // Blocks are dispatched roughly in index order, two per SM at a time, so block b + 2 x
 // (SM count) runs about one wave after block b: passes A and B pull that block's inputs
@@ -71,11 +74,12 @@ __device__ __forceinline__ void f2_prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Offset of line `line` of pass-A/C block blk in a natural-order field.
+// Offset of line `line` of pass-A/C block blk in a natural-order field: the block holds
+// y_lo = blk mod 16 of the z-planes 2 (blk / 16) and 2 (blk / 16) + 1; line = 2 y_hi + dz.
 template <int YL>
 __device__ __forceinline__ long long f2_row(int blk, int line) {
-  const int z = blk / (16 / YL), y0 = (blk % (16 / YL)) * YL;
-  return ((long long)z * F2_N + y0 + (line % YL) + 16 * (line / YL)) * F2_N;
+  const int z = 2 * (blk >> 4) + (line & 1), y = (blk & 15) + 16 * (line >> 1);
+  return ((long long)z * F2_N + y) * F2_N;
 }
 
 // x transform of the 16 elements v[r] = line element g + 16 r of this thread's line
@@ -96,27 +100,26 @@ __device__ __forceinline__ void f2_x_transform(cpx<float> (&v)[16], int line, in
   stage_compute<float, F2_N, 1, INV>(v, g, tw_s);
 }
 
-// Thread roles in a pass-A/C block (YL consecutive y_lo of one z).
+// Thread roles in a pass-A/C block (one y_lo, z-planes z0 and z0 + 1).
 template <int YL>
 struct F2Roles {
-  int z, y0;              // first y_lo of the block
-  int line, g;            // x role: line YL y_hi + s, element group g
-  int kx, s, ylo;         // cross role: column kx of the lines with y_lo = y0 + s
+  int z0, ylo;            // the block's first z-plane and its y_lo
+  int line, g;            // x role: line 2 y_hi + s, element group g
+  int kx, s;              // cross role: column kx of the lines of z-plane z0 + s
   long long row;          // natural offset of line `line`
-  long long sbase;        // S offset of (kx_hi, k_lo = 0, z, y_lo, kx_lo)
+  long long sbase;        // S offset of (kx_hi, k_lo = 0, y_lo, z0 + s, kx_lo)
   __device__ __forceinline__ F2Roles(int blk) {
-    z = blk / (16 / YL);
-    y0 = (blk % (16 / YL)) * YL;
+    z0 = 2 * (blk >> 4);
+    ylo = blk & 15;
     const int tid = threadIdx.x;
     line = tid >> 4;
     g = tid & 15;
     row = f2_row<YL>(blk, line);
     const int kxlo = tid & 1;
-    s = YL == 1 ? 0 : (tid >> 1) & (YL - 1);
-    const int kxhi = tid >> (YL == 1 ? 1 : 2);
+    s = (tid >> 1) & 1;
+    const int kxhi = tid >> 2;
     kx = 2 * kxhi + kxlo;
-    ylo = y0 + s;
-    sbase = ((long long)kxhi * 16 * F2_N + z) * 32 + 2 * ylo + kxlo;
+    sbase = ((long long)kxhi * 16 * 16 + ylo) * (2 * F2_N) + 2 * (z0 + s) + kxlo;
   }
 };
 
@@ -178,12 +181,17 @@ __global__ void __launch_bounds__(F2AC<YL>::THREADS, 4 / YL) fft2_a_kernel(const
   }
 }
 
-// Pass B: S in place (one (kx_hi, k_lo) block of 8192 contiguous elements), staged
-// through shared memory with coalesced 16-byte accesses.  (Reading the outer y DFTs'
-// strided inputs straight from global memory measured 1.8x slower.)
-// With SUMS (energy of a field that is not stepped): after the forward transforms,
-// <v|H_K v> = sum_k T(k)/N^3 |v^(k)|^2 (Parseval) into partial row row0 + blockIdx.x, and
-// nothing is written back.
+// Pass B: S in place, one (kx_hi, k_lo) block of 8192 contiguous elements [y_lo][z][kx_lo].
+//   outer y DFTs: thread (z, kx_lo) = (tid / 2, tid % 2) reads its 16 y_lo values straight
+//     from global memory (a warp reads 256 contiguous bytes per y_lo) -> natural k_hi;
+//   exchange 1 through the [k_hi][z][kx_lo] tile to the z role: warp = k_hi, lane =
+//     (z1, kx_lo) = (lane / 2, lane % 2), holding z = z1 + 16 r;
+//   z forward, T(k), z inverse: Stockham stages with warp-local exchanges through the
+//     warp's two padded buffers (which reuse the tile);
+//   exchange 2 back to (z, kx_lo), inverse outer y DFTs, written straight to global memory.
+// Four shared-memory round trips per element.  With SUMS (energy of a field that is not
+// stepped): after the z forward transform, <v|H_K v> = sum_k T(k)/N^3 |v^(k)|^2
+// (Parseval) into partial row row0 + blockIdx.x, and nothing is written back.
 template <bool SUMS = false>
 __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_constant__ FftGroup<float> gr,
                                                                int row0 = 0) {
@@ -194,57 +202,43 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
   cpx<float>* tile = reinterpret_cast<cpx<float>*>(reinterpret_cast<unsigned char*>(sym_s) + F2_N * 4);
   const int blk = blockIdx.x, kxhi = blk >> 4, klo = blk & 15;
   const int tid = threadIdx.x;
-  const float4* S4 = reinterpret_cast<const float4*>(a.data + (long long)blk * 8192);
-  float4* D4 = reinterpret_cast<float4*>(a.data + (long long)blk * 8192);
+  cpx<float>* base = a.data + (long long)blk * 8192;
   {
     const int nb = f2_next_wave_block();
     if (nb < (int)gridDim.x && tid < 4) f2_prefetch_l2(a.data + (long long)nb * 8192 + tid * 2048, 2048 * 8);
   }
-  // outer y DFTs over y_lo for each (z, kx_lo): natural-order k_hi (a half-warp holds 16
-  // consecutive z of one kx_lo)
-  const int kxl = (tid >> 4) & 1, zr = (tid & 15) + 16 * (tid >> 5);
-  // coalesced load: element e = 2 i (+1) -> row z = e >> 5, column e & 31
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int i = tid + F2_THREADS * j, e = 2 * i;
-    const float4 w = S4[i];
-    cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
-    t[0] = mk<float>(w.x, w.y);
-    t[1] = mk<float>(w.z, w.w);
-  }
-  for (int i = tid; i < F2_TW; i += F2_THREADS) tw_s[i] = a.twiddle[i];
-  for (int i = tid; i < F2_N; i += F2_THREADS) sym_s[i] = a.symbol[i];
-  __syncthreads();
   cpx<float> u[16];
 #pragma unroll
-  for (int y = 0; y < 16; ++y) u[y] = tile[f2_b(zr, 2 * y + kxl)];
+  for (int y = 0; y < 16; ++y) u[y] = base[y * 512 + tid];
+  for (int i = tid; i < F2_TW; i += F2_THREADS) tw_s[i] = a.twiddle[i];
+  for (int i = tid; i < F2_N; i += F2_THREADS) sym_s[i] = a.symbol[i];
   dft16<float, false>(u);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) tile[f2_b(zr, 2 * k + kxl)] = u[k];
+  for (int k = 0; k < 16; ++k) tile[k * 512 + tid] = u[k];
   __syncthreads();
-  // z transforms of the 32 columns c = 2 k_hi + kx_lo: a warp owns two whole columns
-  // (lanes = 16 element groups g x 2 columns), so the stage exchange is warp-local
-  const int c = 2 * (tid >> 5) + ((tid >> 4) & 1), g = tid & 15;
+  // z role
+  const int w = tid >> 5, lane = tid & 31, kxl = lane & 1, z1 = lane >> 1;
   cpx<float> v[16];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
-  stage_compute<float, F2_N, 0, false>(v, g, tw_s);
-  __syncwarp();  // (the column's own lanes are its only readers)
+  for (int r = 0; r < 16; ++r) v[r] = tile[w * 512 + lane + 32 * r];
+  __syncthreads();  // the tile becomes the per-warp exchange buffers
+  cpx<float>* wb = tile + (2 * w + kxl) * F2_BPAD;
+  stage_compute<float, F2_N, 0, false>(v, z1, tw_s);
 #pragma unroll
-  for (int r = 0; r < 16; ++r) tile[f2_b(16 * g + r, c)] = v[r];
+  for (int r = 0; r < 16; ++r) wb[f2_bpad(16 * z1 + r)] = v[r];
   __syncwarp();
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
-  stage_compute<float, F2_N, 1, false>(v, g, tw_s);
-  // natural-order kz = g + 16 r; T(kx, ky, kz)/N^3
+  for (int r = 0; r < 16; ++r) v[r] = wb[f2_bpad(z1 + 16 * r)];
+  stage_compute<float, F2_N, 1, false>(v, z1, tw_s);
+  // natural-order kz = z1 + 16 r; T(kx, ky, kz)/N^3 with ky = k_lo + 16 k_hi
   {
-    const int kx = 2 * kxhi + (c & 1), ky = klo + 16 * (c >> 1);
+    const int kx = 2 * kxhi + kxl, ky = klo + 16 * w;
     const float sxy = sym_s[kx] + sym_s[ky];
     if constexpr (SUMS) {
       CheckSums<float> cs;
 #pragma unroll
       for (int r = 0; r < 16; ++r)
-        cs.add(v[r], cscale<float>(v[r], kin_mult<float>(a.kinetic, sxy, sym_s[g + 16 * r], a.tcoef, a.am2)),
+        cs.add(v[r], cscale<float>(v[r], kin_mult<float>(a.kinetic, sxy, sym_s[z1 + 16 * r], a.tcoef, a.am2)),
                mk<float>(0.f, 0.f));
       double acc[kNumSums];
       cs.to(acc);
@@ -255,33 +249,25 @@ __global__ void __launch_bounds__(F2_THREADS, 2) fft2_b_kernel(const __grid_cons
     }
 #pragma unroll
     for (int r = 0; r < 16; ++r)
-      v[r] = cscale<float>(v[r], kin_mult<float>(a.kinetic, sxy, sym_s[g + 16 * r], a.tcoef, a.am2));
+      v[r] = cscale<float>(v[r], kin_mult<float>(a.kinetic, sxy, sym_s[z1 + 16 * r], a.tcoef, a.am2));
   }
-  stage_compute<float, F2_N, 0, true>(v, g, tw_s);
+  stage_compute<float, F2_N, 0, true>(v, z1, tw_s);
+  __syncwarp();  // (the buffer's own lanes are its only readers)
+#pragma unroll
+  for (int r = 0; r < 16; ++r) wb[f2_bpad(16 * z1 + r)] = v[r];
   __syncwarp();
 #pragma unroll
-  for (int r = 0; r < 16; ++r) tile[f2_b(16 * g + r, c)] = v[r];
-  __syncwarp();
+  for (int r = 0; r < 16; ++r) v[r] = wb[f2_bpad(z1 + 16 * r)];
+  stage_compute<float, F2_N, 1, true>(v, z1, tw_s);
+  __syncthreads();  // every warp is done with its buffers
 #pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = tile[f2_b(g + 16 * r, c)];
-  stage_compute<float, F2_N, 1, true>(v, g, tw_s);
-  __syncwarp();
-#pragma unroll
-  for (int r = 0; r < 16; ++r) tile[f2_b(g + 16 * r, c)] = v[r];
+  for (int r = 0; r < 16; ++r) tile[w * 512 + lane + 32 * r] = v[r];
   __syncthreads();
-  // outer inverse y DFTs over k_hi: natural-order y_lo
 #pragma unroll
-  for (int k = 0; k < 16; ++k) u[k] = tile[f2_b(zr, 2 * k + kxl)];
+  for (int k = 0; k < 16; ++k) u[k] = tile[k * 512 + tid];
   dft16<float, true>(u);
 #pragma unroll
-  for (int y = 0; y < 16; ++y) tile[f2_b(zr, 2 * y + kxl)] = u[y];
-  __syncthreads();
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const int i = tid + F2_THREADS * j, e = 2 * i;
-    const cpx<float>* t = &tile[f2_b(e >> 5, e & 31)];
-    D4[i] = make_float4(t[0].x, t[0].y, t[1].x, t[1].y);
-  }
+  for (int y = 0; y < 16; ++y) base[y * 512 + tid] = u[y];
 }
 
 // Pass C: S -> inverse inner y DFTs, x inverse -> H_K psi; update / sums; with NEXT, pass A
