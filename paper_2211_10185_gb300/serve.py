@@ -194,6 +194,7 @@ class Server:
         self.in_use = 0
         self.peak_in_use = 0
         self.results: list[Result] = []
+        self.chunks = 0
 
     def _admit(self, now: float):
         kept = []
@@ -264,6 +265,7 @@ class Server:
                     time.sleep(max(0.0, min(0.01, pending[i].arrival - now)))
                 continue
             self.batch.step(self.chunk, check_every=self.chunk)
+            self.chunks += 1
             self._retire(time.perf_counter() - t0)
         self.elapsed = time.perf_counter() - t0
         return self.results
@@ -277,4 +279,4 @@ class Server:
                 "p99_s": pick(0.99), "converged": sum(r.status == Q.QF_OK for r in self.results),
                 "capped": sum(r.status == Q.QF_ENOTCONV for r in self.results),
                 "peak_workspace_bytes": self.peak_in_use, "launches": self.batch.launches(),
-                "elapsed_s": self.elapsed}
+                "elapsed_s": self.elapsed, "chunks": self.chunks}

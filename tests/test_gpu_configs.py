@@ -139,3 +139,78 @@ def test_n256_excited_states_and_parity():
     gpu.parity_project(O.P_MINUS_PK, 3, 1)
     s_gpu, s_ref = gpu.get_wavefunction(1), ref.states[1]
     assert abs(abs(np.vdot(s_gpu, s_ref)) - 1) < 1e-4
+
+
+def test_config2_cornell_n128_c64_c128_oracle_plateau_and_parity():
+    """The N=128 Cornell workload (kappa .52, sigma .18, m 1.5, a 0.1, Eq. HK1, default dtau).
+
+    (1) The first 192 steps from the same psi0: the FP64 oracle, the complex-FP32 and the
+        FP64 GPU paths measure the same energies at every check and the same excited-state
+        energies at the snapshot record (FP32 1e-5, FP64 1e-10).
+    (2) Both GPU paths run to convergence: their ground-state energies agree within 1e-5;
+        the FP64 path's plateau (Sec. 4's saddle point) gives E_0 < E_1 < E_2 with
+        |E_i(tau_j) - E_i(tau_{j-1})| below 1e-5 |E_i|, and the kept states have the parity
+        of 1S (even), 1P (odd) and 2S (even): projecting them leaves them unchanged.  The
+        converged ground state is a fixed point of the step map, checked with the oracle's
+        kinetic term.  (The FP32 path's E_1/E_2 plateau is limited here by FP32 noise: the
+        2S-1P gap is small against E_1 - E_0, see the design notes.)"""
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    w = I.workload("cornell_naive_n128")
+    n, a, m = w["n"], w["a"], w["m"]
+    v = w["potential"](n, a)
+    psi0 = I.gaussian_field(n, w["seed"])
+    ref = O.Lattice(n, a)
+    ref.set_potential(v)
+    ref.set_kinetic(w["kinetic"], m, w["dtau"])
+    ref.set_wavefunction(psi0)
+    lats = {}
+    for prec in ("c64", "c128"):
+        lat = Lattice(n, a, precision=prec, plateau_slots=3)
+        lat.set_potential(v)
+        lat.set_kinetic(w["kinetic"], m, w["dtau"])
+        lat.set_wavefunction(psi0)
+        lats[prec] = lat
+    tol = {"c64": 1e-5, "c128": 1e-10}
+    for _ in range(3):
+        ref.step_n(64, check_every=64, snap_every=64)
+        e_ref = ref.energies()["e"]
+        for prec, lat in lats.items():
+            lat.step_n(64, tol=0.0, check_every=64, snap_every=64)
+            assert abs(lat.energies()["e"] - e_ref) < tol[prec] * abs(e_ref), prec
+    st, ex_ref = ref.project_excited(3)
+    for prec, lat in lats.items():
+        ex = lat.track_excited(3)
+        for i in range(3):
+            assert abs(ex[i]["e"] - ex_ref[i]["e"]) < tol[prec] * abs(ex_ref[i]["e"]), (prec, i)
+    # (2) convergence: checks every 64 steps, snapshot records every 256 (tau ~ 55)
+    for prec, lat in lats.items():
+        for _ in range(280):
+            lat.step_n(256, tol=0.0, check_every=64, snap_every=256)
+            lat.track_excited(3)
+    e64, e128 = lats["c64"].energies()["e"].real, lats["c128"].energies()["e"].real
+    assert abs(e64 - e128) < 1e-5 * abs(e128)
+    assert lats["c128"].energies()["de"] < 1e-12
+    pl = lats["c128"].excited_plateau(3)
+    es = [p[1]["e"].real for p in pl]
+    assert es[0] == pytest.approx(e128, rel=1e-10)
+    assert es[0] < es[1] < es[2]
+    for i in range(3):
+        assert pl[i][1]["de"] < 1e-5 * abs(es[i]), (i, pl[i])
+    # the kept states' parities (their admixture of the next states is ~1e-3 at the
+    # plateau of E_1 and E_2, which the energies feel only squared)
+    lat = lats["c128"]
+    for slot, which, t in ((200, O.P_PLUS, 1e-10), (201, O.P_MINUS, 1e-5), (202, O.P_PLUS, 1e-5)):
+        before = lat.get_wavefunction(slot)
+        lat.parity_project(which, 3, slot)
+        assert abs(abs(np.vdot(lat.get_wavefunction(slot), before)) - 1) < t, slot
+    # fixed point of psi -> coef_A psi - coef_B dtau H_K psi (oracle's kinetic term)
+    psi = lat.get_wavefunction()
+    dt = lat.info()["dtau"]
+    hk = O.apply_kinetic(psi, w["kinetic"], a, m)
+    d = 1 + 0.5 * dt * v
+    mp = ((2 - d) * psi - dt * hk) / d
+    lam = np.vdot(psi, mp) / np.vdot(psi, psi)
+    assert np.linalg.norm((mp - lam * psi).ravel()) / np.linalg.norm(psi.ravel()) < 1e-9
+    for lat in lats.values():
+        lat.close()
