@@ -295,9 +295,10 @@ qf_status qf_fft_step_static(int n, double a, int kinetic, double mass, double d
 
 /* ---- Batches (no counterpart in the paper: serving many independent solves) ------
  * A batch advances many resident lattices together.  Each step, complex-FP32 lattices
- * of equal N -- and, for FFT terms, equal real/complex V and check status -- form a
- * group, and each pass of a group is a single kernel launch over all its members (up
- * to 48 per launch); FP64 lattices run their own launches.  Every member computes
+ * form groups, and each pass of a group is a single kernel launch over all its members
+ * (up to 48 per launch): FDTD lattices of any sizes together (the stencil launch maps
+ * its blocks to members through a table), FFT lattices of equal N, real/complex V and
+ * check status; FP64 lattices run their own launches.  Every member computes
  * exactly what qf_step_n computes for it alone (same kernels, same blocks, same
  * reduction order), so its results do not depend on the other members.  A batch holds
  * no device memory; members keep their own workspaces.  During qf_batch_step all

@@ -554,15 +554,15 @@ static StencilArgs<R> stencil_args(qf_lattice* lat, void* in, void* out, bool wr
 // field buffer is cached, others (state slots) are encoded on the spot.
 template <typename R>
 static bool stencil_group_member(qf_lattice* lat, void* in, void* out, bool write, bool reduce, const double* scale,
-                                 StencilTmaGroup<R>& g, bool first = true) {
+                                 StencilTmaGroup<R>& g, bool first = true, int zc = kStencilZChunks[2]) {
   if (first) {
     g.count = 0;
-    g.n = lat->d.n;
-    g.zc = kStencilZChunks[2];
     g.err = &lat->sc()->err[0];
   }
   const int i = g.count;
   if (i >= kGroupMax) return false;
+  g.nm[i] = lat->d.n;
+  g.zcm[i] = zc;
   if (in == lat->field(0) && lat->fmap_ok) g.map[i] = lat->fmap[0];
   else if (in == lat->field(1) && lat->fmap_ok) g.map[i] = lat->fmap[1];
   else if (!encode_stencil_map(&g.map[i], in, lat->d.n, lat->c64())) return false;
@@ -591,8 +591,7 @@ static int tuned_zchunk(qf_lattice* lat) {
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return best;
   for (int zc : kStencilZChunks) {
     StencilTmaGroup<R> g;
-    if (!stencil_group_member<R>(lat, lat->psi(), lat->tmp(), true, false, &lat->sc()->scale[0], g)) break;
-    g.zc = zc;
+    if (!stencil_group_member<R>(lat, lat->psi(), lat->tmp(), true, false, &lat->sc()->scale[0], g, true, zc)) break;
     float ms = 0, tot = 0;
     bool ok = launch_stencil_tma<R>(g, lat->st) == cudaSuccess;  // warm-up
     for (int rep = 0; rep < 3 && ok; ++rep) {
@@ -722,13 +721,11 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
     if (nblocks) *nblocks = stencil_blocks<float>(n, zc);
     if (lat->c64()) {
       StencilTmaGroup<float> g;
-      if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
-      g.zc = zc;
+      if (!stencil_group_member(lat, in, out, write, reduce, scale, g, true, zc)) return cudaErrorInvalidValue;
       return launch(lat, write ? K_STENCIL : K_STENCIL_SUMS, [&] { return launch_stencil_tma<float>(g, lat->st); });
     }
     StencilTmaGroup<double> g;
-    if (!stencil_group_member(lat, in, out, write, reduce, scale, g)) return cudaErrorInvalidValue;
-    g.zc = zc;
+    if (!stencil_group_member(lat, in, out, write, reduce, scale, g, true, zc)) return cudaErrorInvalidValue;
     return launch(lat, write ? K_STENCIL : K_STENCIL_SUMS, [&] { return launch_stencil_tma<double>(g, lat->st); });
   }
   // FFT terms: in place on `in` (out must equal in when writing); the scratch field is tmp.
@@ -1525,7 +1522,9 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
       for (int q = k; q < R; ++q) {
         if (done[q]) continue;
         qf_lattice* M = b->m[run[q]].lat;
-        if (!M->c64() || M->d.n != L->d.n || (M->kinetic == QF_KIN_FDTD) != fdtd) continue;
+        // complex-FP32 FDTD members of any size share a launch (the stencil kernel takes
+        // each member's N from its block table); FFT members need the same plan (N)
+        if (!M->c64() || (M->kinetic == QF_KIN_FDTD) != fdtd || (!fdtd && M->d.n != L->d.n)) continue;
         if (!fdtd && (M->v_real != L->v_real || chk[q] != chk[k] || uses_fft2(M) != uses_fft2(L))) continue;
         g.push_back(q);
         done[q] = 1;
@@ -1535,17 +1534,16 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
         const int cnt = (int)std::min<size_t>(kGroupMax, g.size() - off);
         if (fdtd) {
           StencilTmaGroup<float> sg;
-          const int zc = tuned_zchunk<float>(L);
           for (int j = 0; j < cnt; ++j) {
             const int q = g[off + j];
             qf_lattice* M = b->m[run[q]].lat;
+            const int zc = tuned_zchunk<float>(M);
             const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
-            if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0))
+            if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0, zc))
               return bfail(b, QF_ECUDA, "tensor map encoding failed");
             // one error flag per launch: the first member's
-            nblk[q] = stencil_blocks<float>(n, zc);
+            nblk[q] = stencil_blocks<float>(M->d.n, zc);
           }
-          sg.zc = zc;
           QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
           b->launches += 1;
         } else {

@@ -19,7 +19,7 @@ namespace qf {
 template <typename R>
 int stencil_blocks(int n, int zc) {
   if (zc <= 0) zc = kStencilZChunkMin;
-  return ((n + TS_X - 1) / TS_X) * ((n + TS_Y - 1) / TS_Y) * ((n + zc - 1) / zc);
+  return stencil_member_blocks(n, zc);
 }
 
 template <typename R>
@@ -30,10 +30,18 @@ cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st) {
                          (int)stencil_tma_smem<R>());
     attr = true;
   }
-  const int n = g.n;
-  if (g.zc < 1) return cudaErrorInvalidValue;
-  dim3 grid((n + TS_X - 1) / TS_X, (n + TS_Y - 1) / TS_Y, ((n + g.zc - 1) / g.zc) * g.count);
-  stencil_tma_kernel<R><<<grid, dim3(TS_X, TS_Y / TS_ROWS), stencil_tma_smem<R>(), st>>>(g);
+  if (g.count < 1 || g.count > kGroupMax) return cudaErrorInvalidValue;
+  // the block table: member i's blocks follow member i-1's
+  StencilTmaGroup<R> gl = g;
+  long long total = 0;
+  for (int i = 0; i < g.count; ++i) {
+    if (g.zcm[i] < 1 || g.nm[i] < 2) return cudaErrorInvalidValue;
+    gl.start[i] = (int)total;
+    total += stencil_member_blocks(g.nm[i], g.zcm[i]);
+  }
+  if (total > (1LL << 30)) return cudaErrorInvalidValue;
+  gl.start[g.count] = (int)total;
+  stencil_tma_kernel<R><<<(unsigned)total, dim3(TS_X, TS_Y / TS_ROWS), stencil_tma_smem<R>(), st>>>(gl);
   return cudaGetLastError();
 }
 

@@ -35,15 +35,24 @@ struct TmaTile {
   static constexpr unsigned BYTES = PLANE_WORDS * 8u;
 };
 
+// Members of one launch may have different lattice sizes: member i runs
+// tiles(n_i) x ceil(n_i / zc_i) blocks, numbered from start[i] in a one-dimensional grid
+// (tile x fastest, then tile y, then z-chunk), exactly the blocks it runs alone.
 template <typename R>
 struct alignas(64) StencilTmaGroup {
   CUtensorMap map[kGroupMax];  // input field of member i, 3D (x, y, z), 8-byte elements
   StencilArgs<R> a[kGroupMax];
+  int nm[kGroupMax];           // lattice size of member i
+  int zcm[kGroupMax];          // planes per block (z-chunk) of member i
+  int start[kGroupMax + 1];    // first block of member i; start[count] = blocks in all
   int count;
-  int n;
-  int zc;    // planes per block (z-chunk)
-  int* err;  // set to 1 when a bounded wait ran out
+  int* err;                    // set to 1 when a bounded wait ran out
 };
+
+// Blocks member i of a stencil group runs (tiles x z-chunks).
+__host__ __device__ __forceinline__ int stencil_member_blocks(int n, int zc) {
+  return ((n + TS_X - 1) / TS_X) * ((n + TS_Y - 1) / TS_Y) * ((n + zc - 1) / zc);
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -160,14 +169,25 @@ __global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), sizeof(R) == 4 ? 3 : 2)
       reinterpret_cast<unsigned long long(*)[TmaTile<R>::STRIDE_WORDS]>(planes_dyn);
   __shared__ alignas(8) unsigned long long bars[TS_BUF];
   __shared__ double red_s[32 * kNumSums];
-  const int n = g.n;
-  const int zc = g.zc;
-  const int nzb = (n + zc - 1) / zc;
-  const int member = blockIdx.z / nzb, zb = blockIdx.z % nzb;
+  // member of this block (last i with start[i] <= block), then its tile and z-chunk
+  int member = 0;
+  {
+    int hi = g.count - 1;
+    while (member < hi) {
+      const int mid = (member + hi + 1) >> 1;
+      if (g.start[mid] <= (int)blockIdx.x) member = mid;
+      else hi = mid - 1;
+    }
+  }
+  const int n = g.nm[member];
+  const int zc = g.zcm[member];
+  const int nbx = (n + TS_X - 1) / TS_X, nby = (n + TS_Y - 1) / TS_Y;
+  const int local = (int)blockIdx.x - g.start[member];
+  const int bx = local % nbx, by = (local / nbx) % nby, zb = local / (nbx * nby);
   const StencilArgs<R>& a = g.a[member];
   const CUtensorMap* map = &g.map[member];
   const int tid = threadIdx.y * TS_X + threadIdx.x;
-  const int x0 = blockIdx.x * TS_X, y0 = blockIdx.y * TS_Y;
+  const int x0 = bx * TS_X, y0 = by * TS_Y;
   const int ix = x0 + threadIdx.x;
   const int z0 = zb * zc, z1 = min(n, z0 + zc);
   const int pfirst = z0 - 1, plast = z1;  // planes needed (inclusive)
@@ -282,7 +302,7 @@ __global__ void __launch_bounds__(TS_X*(TS_Y / TS_ROWS), sizeof(R) == 4 ? 3 : 2)
   if (a.reduce) {
     double acc[kNumSums];
     cs.to(acc);
-    const int bid = (zb * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const int bid = local;  // (zb * nby + by) * nbx + bx: the member's own partial row
     warp_sum<kNumSums>(acc);
     const int lane = tid & 31, warp = tid >> 5;
     if (lane == 0)

@@ -10,7 +10,9 @@ measured from arrival to retirement.
 from __future__ import annotations
 
 import ctypes as C
+import concurrent.futures as cf
 import dataclasses
+import functools
 import heapq
 import math
 import time
@@ -138,6 +140,29 @@ class Request:
         return fine + (self.workspace_bytes(self.n // 2, 2 * self.a) if self.coarse() else 0)
 
 
+@functools.lru_cache(maxsize=16)
+def _radius(n: int, a: float) -> np.ndarray:
+    r = I.radius(n, a)
+    r.setflags(write=False)
+    return r
+
+
+def request_inputs(req: "Request", n: int | None = None, a: float | None = None):
+    """(potential, initial state) of a request on its lattice (or the N/2 lattice of a warm
+    start): the same arrays as Request.potential / initial_state, with |r| computed once
+    per lattice size."""
+    n, a = n or req.n, a or req.a
+    r = _radius(n, a)
+    rr = np.where(r == 0.0, a / 2, r)
+    v = -req.kappa / rr + req.sigma * rr + 0.0
+    rng = np.random.default_rng(req.seed)
+    w = rng.uniform(0.5, 2.0) / math.sqrt(req.mass)
+    psi = np.exp(-0.5 * (r / w) ** 2).astype(np.complex128)
+    if req.kinetic == I.FDTD:
+        psi = I.zero_dirichlet_planes(psi)
+    return v, psi
+
+
 @dataclasses.dataclass
 class Result:
     rid: int
@@ -184,17 +209,46 @@ class Server:
     last two check differences, is below its tolerance (QF_STOP_EXTRAPOLATED)."""
 
     def __init__(self, hbm_budget_bytes: int, chunk: int = 64, stream=None,
-                 stopping: int = Q.QF_STOP_EXTRAPOLATED):
+                 stopping: int = Q.QF_STOP_EXTRAPOLATED, prep_threads: int = 8,
+                 prep_bytes: int = 8 << 30):
         self.budget = int(hbm_budget_bytes)
         self.chunk = int(chunk)
         self.batch = Batch(stream)
         self.batch.set_stopping(stopping)
+        # host-side preparation of queued requests' inputs (potential, initial state) on a
+        # thread pool while the GPU steps the batch; at most prep_bytes of them in flight
+        self.prep = cf.ThreadPoolExecutor(max_workers=prep_threads)
+        self.prep_bytes = int(prep_bytes)
+        self.prepared: dict[tuple, cf.Future] = {}
+        self.prep_in_flight = 0
         self.queue: list[Request] = []
         self.active: dict[int, tuple[Request, Lattice, float]] = {}
         self.in_use = 0
         self.peak_in_use = 0
         self.results: list[Result] = []
         self.chunks = 0
+
+    def _prepare(self):
+        """Starts host-side input generation for queued requests, in queue order, while
+        the bytes in preparation stay under prep_bytes."""
+        for req in self.queue:
+            n, a = (req.n // 2, 2 * req.a) if req.coarse() else (req.n, req.a)
+            key = (req.rid, n)
+            if key in self.prepared:
+                continue
+            size = 24 * n ** 3
+            if self.prep_in_flight + size > self.prep_bytes and self.prepared:
+                break
+            self.prepared[key] = self.prep.submit(request_inputs, req, n, a)
+            self.prep_in_flight += size
+
+    def _inputs(self, req: Request, n: int, a: float):
+        key = (req.rid, n)
+        fut = self.prepared.pop(key, None)
+        if fut is None:
+            return request_inputs(req, n, a)
+        self.prep_in_flight -= 24 * n ** 3
+        return fut.result()
 
     def _admit(self, now: float):
         kept = []
@@ -205,15 +259,19 @@ class Server:
                 continue
             if req.coarse():
                 n, a = req.n // 2, 2 * req.a
+                v, psi = self._inputs(req, n, a)
                 lat = Lattice(n, a, precision=req.precision, stream=self.batch.stream)
-                lat.set_potential(req.potential(n, a))
+                lat.set_potential(v)
                 lat.set_kinetic(req.kinetic, req.mass, req.dtau)
-                lat.set_wavefunction(req.initial_state(n, a))
+                lat.set_wavefunction(psi)
                 self.batch.add(lat, req.max_steps, 10 * req.tol_abs, 10 * req.tol_rel)
                 self.active[req.rid] = (req, lat, now, "coarse", 0)
             else:
-                lat = self._fine(req)
-                lat.set_wavefunction(req.initial_state())
+                v, psi = self._inputs(req, req.n, req.a)
+                lat = Lattice(req.n, req.a, precision=req.precision, stream=self.batch.stream)
+                lat.set_potential(v)
+                lat.set_kinetic(req.kinetic, req.mass, req.dtau)
+                lat.set_wavefunction(psi)
                 self.batch.add(lat, req.max_steps, req.tol_abs, req.tol_rel)
                 self.active[req.rid] = (req, lat, now, "fine", 0)
             self.in_use += need
@@ -259,6 +317,7 @@ class Server:
             while i < len(pending) and (not realtime or pending[i].arrival <= now):
                 self.queue.append(pending[i])
                 i += 1
+            self._prepare()
             self._admit(now)
             if not self.active:
                 if i < len(pending) and realtime:
@@ -268,6 +327,7 @@ class Server:
             self.chunks += 1
             self._retire(time.perf_counter() - t0)
         self.elapsed = time.perf_counter() - t0
+        self.prep.shutdown(wait=True)
         return self.results
 
     def metrics(self) -> dict:

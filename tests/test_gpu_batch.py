@@ -185,3 +185,24 @@ def test_served_energies_match_the_oracle_within_1e5():
         checked += 1
         assert abs(got.energy - e) < 1e-5 * abs(e), (req, got.energy, e)
     assert checked >= 6
+
+
+def test_fdtd_members_of_different_sizes_share_one_launch_per_step():
+    """FDTD lattices of N = 16, 24, 40 and 48 (real and complex V) advance in a single
+    stencil launch per step, and each ends bitwise where it ends alone."""
+    from paper_2211_10185_gb300.serve import Batch
+
+    specs = [(16, I.FDTD, "c64", False), (24, I.FDTD, "c64", True), (40, I.FDTD, "c64", False),
+             (48, I.FDTD, "c64", True)]
+    alone = [_make(s, 30 + i) for i, s in enumerate(specs)]
+    mixed = [_make(s, 30 + i) for i, s in enumerate(specs)]
+    for lat in alone:
+        lat.set_temporal_blocking(1)   # one step per launch, as in a batch
+        lat.step_n(37, tol=0.0, check_every=0, snap_every=0)
+    b = Batch()
+    for lat in mixed:
+        b.add(lat, 1000, 0.0)
+    b.step(37, check_every=0, snap_every=0)
+    assert b.launches() == 37
+    for la, lm in zip(alone, mixed):
+        assert np.array_equal(la.get_wavefunction(), lm.get_wavefunction())

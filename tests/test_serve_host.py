@@ -94,3 +94,16 @@ def test_oracle_on_all_cores_uses_the_workloads_default_size():
     rate, steps, el = bench.oracle_rate_cores("ho_fdtd_n32", None, 0.2, 2, min_steps=2)
     assert steps >= 2 and el > 0
     assert rate == pytest.approx(2 * 32 ** 3 * steps / el)
+
+
+def test_prepared_request_inputs_equal_the_request_arrays():
+    # the server's background preparation (radius cached per lattice size) builds exactly
+    # the potential and initial state of Request, on the fine and the warm-start lattices
+    from paper_2211_10185_gb300.serve import request_inputs, served_mix
+
+    for r in served_mix(24, sizes=(16, 24, 32), seed=4)[:12]:
+        v, psi = request_inputs(r)
+        assert np.array_equal(v, r.potential()) and np.array_equal(psi, r.initial_state())
+        v2, psi2 = request_inputs(r, r.n // 2, 2 * r.a)
+        assert np.array_equal(v2, r.potential(r.n // 2, 2 * r.a))
+        assert np.array_equal(psi2, r.initial_state(r.n // 2, 2 * r.a))
