@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--served-requests", type=int, default=96)
     ap.add_argument("--served-cap", type=int, default=3000)
+    ap.add_argument("--config4", action="store_true",
+                    help="also time 200 steps of the N=512 Gaussian-mix workload (Eq. HK2, complex V); "
+                         "its host inputs take about a minute to generate")
     ap.add_argument("--served-full", action="store_true",
                     help="only the served mix, at its stated size: 2000 Poisson requests (200/s), "
                          "N in {32..256}, cap 20000 steps, 170 GB; prints one JSON line")
@@ -475,6 +478,55 @@ def c128_arm(w, v, psi0, bench_steps=2):
             "site_updates_per_s": n ** 3 * CHUNK / (ms * 1e-3), "energies": [e["e"].real for e in ex]}
 
 
+def workload_steps(name, steps=200, warm=64):
+    """Plain imaginary-time steps of another workload at its own size (checks every 64,
+    CUDA-graph replay between checks), timed with CUDA events on the lattice's stream; with
+    the per-kernel breakdown and the dominant step kernel's roofline on the step's floor
+    bytes."""
+    import torch
+
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    w = I.workload(name)
+    n = w["n"]
+    v, psi0 = make_inputs(w)
+    v_real = not np.iscomplexobj(v)
+    prec = w["precision"]
+    lat = Lattice(n, w["a"], precision=prec, n_snap=1)
+    lat.set_potential(v)
+    lat.set_kinetic(w["kinetic"], w["m"], w["dtau"])
+    lat.set_wavefunction(psi0)
+    lat.step_n(warm, tol=0.0, check_every=CHUNK, snap_every=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(lat.stream)
+    lat.step_n(steps, tol=0.0, check_every=CHUNK, snap_every=0)
+    e1.record(lat.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.profile(True)
+    lat.profile_read(reset=True)
+    lat.step_n(CHUNK, tol=0.0, check_every=CHUNK, snap_every=0)
+    prof = lat.profile_read(reset=True)
+    lat.profile(False)
+    peak, _ = hbm_peak()
+    alg_site = algorithmic_bytes_per_site_update(prec, v_real)
+    dom = max(((k, x) for k, x in prof.items() if step_kernel(k)), key=lambda kv: kv[1][1], default=None)
+    roof = None
+    if dom:
+        k, (cnt, tot) = dom
+        avg_s = tot / cnt * 1e-3
+        roof = {"kernel": k, "avg_launch_us": avg_s * 1e6, "frac": alg_site * n ** 3 / avg_s / 1e9 / peak,
+                "design_frac": design_bytes_per_site(k, prec, v_real) * n ** 3 / avg_s / 1e9 / peak}
+    out = {"workload": workload_config(w, prec)["workload"], "steps": steps, "ms_per_step": ms / steps,
+           "site_updates_per_s": n ** 3 * steps / (ms * 1e-3),
+           "step_frac_of_peak": alg_site * n ** 3 * steps / (ms * 1e-3) / 1e9 / peak,
+           "fft_passes": lat.info()["fft_passes"], "roofline": roof,
+           "kernels": {k: {"launches": c, "avg_us": 1e3 * t / c} for k, (c, t) in prof.items()}}
+    lat.close()
+    return out
+
+
 def fp64_peak(size=4096, reps=3):
     """Dense FP64 rate of this GPU (cuBLAS DGEMM through torch.matmul, best of reps)."""
     import torch
@@ -532,9 +584,13 @@ def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget
         r64[req.rid] = res
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t0
-    errs = [abs(r32[i].energy - r64[i].energy) / max(1e-300, abs(r64[i].energy)) for i in r64]
+    # energies are compared where both solves converged (a solve stopped by the step cap
+    # reports an unconverged energy, where the two precisions' trajectories differ)
+    conv = [i for i in r64 if r32[i].status == Q.QF_OK and r64[i].status == Q.QF_OK]
+    errs = [abs(r32[i].energy - r64[i].energy) / max(1e-300, abs(r64[i].energy)) for i in conv]
     out["fp32_batched_vs_fp64_alone"] = {
         "requests": len(sub), "fp32_batched_solves_per_s": len(sub) / t32, "fp64_alone_solves_per_s": len(sub) / t64,
+        "converged_both": len(conv),
         "max_rel_energy_err_fp32_vs_fp64": max(errs) if errs else None,
         "same_status": all(r32[i].status == r64[i].status for i in r64)}
     if not warm:
@@ -752,6 +808,8 @@ def run_ours(args):
             out["fp64_peak"] = fp64_peak()
         except Exception as exc:  # context only
             out["c128_arm"] = {"error": str(exc)[:200]}
+    if out is not None and world == 1 and args.config4:
+        out["config4_n512"] = workload_steps("gaussmix_symanzik_n512")
     if out is not None and not args.no_served:
         lat.close()
         torch.cuda.synchronize()

@@ -337,6 +337,20 @@ typedef enum { QF_STOP_DIFFERENCE = 0, QF_STOP_EXTRAPOLATED = 1 } qf_stopping;
 /* Selects the stopping rule (qf_stopping) for every member's following checks. */
 qf_status qf_batch_set_stopping(qf_batch* b, int rule);
 
+/* CUDA graphs of check-free intervals (on by default; no counterpart in the paper).
+ * When every running member took a check at the previous step, the check_every - 1
+ * steps up to the next check issue the same launches each time the batch holds the same
+ * members in the same buffer state; they are captured once into a graph and replayed.
+ * Needs check_every >= 3, snap_every 0 or equal to check_every, no member closer to its
+ * step cap than the interval, no per-kernel profiling and a stream other than the legacy
+ * default stream.  Adding or removing a member drops the captured graphs; a failed
+ * capture leaves the batch on ordinary launches.  Results are bitwise those of ordinary
+ * launches. */
+qf_status qf_batch_use_graphs(qf_batch* b, int enable);
+
+/* Graphs captured and graph replays so far. */
+qf_status qf_batch_graph_info(qf_batch* b, int64_t* captures, int64_t* replays);
+
 /* Members in insertion order: count, and per member (arrays of at least `max` entries,
  * may be NULL) its status (QF_BATCH_RUNNING, QF_OK, QF_ENOTCONV) and steps taken. */
 qf_status qf_batch_members(qf_batch* b, int* count, int* status, int64_t* steps_done, int max);

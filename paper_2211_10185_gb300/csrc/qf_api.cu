@@ -1398,6 +1398,19 @@ struct qf_batch {
   std::string err;
   int64_t launches = 0;
   int rule = QF_STOP_DIFFERENCE;
+  // CUDA graphs of check-free intervals (batch_chunk_graph), dropped when members change
+  struct BGraph {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<BGraph> graphs;
+  bool use_graphs = true;
+  int64_t graph_captures = 0, graph_replays = 0;
+  void drop_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
 };
 
 static qf_status bfail(qf_batch* b, qf_status s, const std::string& msg) {
@@ -1422,6 +1435,7 @@ extern "C" qf_status qf_batch_create(void* cuda_stream, qf_batch** out) {
 extern "C" qf_status qf_batch_destroy(qf_batch* b) {
   if (!b) return QF_OK;
   cudaStreamSynchronize(b->st);
+  b->drop_graphs();
   delete b;
   return QF_OK;
 }
@@ -1436,6 +1450,7 @@ extern "C" qf_status qf_batch_add(qf_batch* b, qf_lattice* lat, int64_t max_step
   // work of the lattice's own stream must be visible to the batch stream
   QF_BCUDA(b, cudaStreamSynchronize(lat->st));
   b->m.push_back({lat, max_steps, 0, tol_abs, tol_rel, QF_BATCH_RUNNING});
+  b->drop_graphs();
   return QF_OK;
 }
 
@@ -1445,6 +1460,7 @@ extern "C" qf_status qf_batch_remove(qf_batch* b, qf_lattice* lat) {
     if (b->m[i].lat == lat) {
       QF_BCUDA(b, cudaStreamSynchronize(b->st));
       b->m.erase(b->m.begin() + i);
+      b->drop_graphs();
       return QF_OK;
     }
   return bfail(b, QF_EINVAL, "lattice not in the batch");
@@ -1457,6 +1473,194 @@ extern "C" qf_status qf_batch_members(qf_batch* b, int* count, int* status, int6
     if (status) status[i] = b->m[i].status;
     if (steps_done) steps_done[i] = b->m[i].steps_done;
   }
+  return QF_OK;
+}
+
+// Issues the launches of one batch step for the running members `run` (check flags chk);
+// nblk receives each member's partial rows.  Host state is touched only where later
+// launches depend on it (xfwd_valid of FFT members).
+static qf_status batch_issue_step(qf_batch* b, const std::vector<int>& run, const std::vector<char>& chk,
+                                  std::vector<int>& nblk, cudaStream_t st) {
+  const int R = (int)run.size();
+  // group FP32 members by (N, kinetic family, real V, check); FP64 members run alone
+  std::vector<char> done(R, 0);
+  for (int k = 0; k < R; ++k) {
+    if (done[k]) continue;
+    qf_lattice* L = b->m[run[k]].lat;
+    const double* sk = L->pending_scale ? &L->sc()->scale[1] : &L->sc()->scale[2];
+    const bool fdtd = L->kinetic == QF_KIN_FDTD;
+    if (!L->c64()) {
+      void* in = L->psi();
+      const int64_t l0 = L->launches;
+      QF_BCUDA(b, kinetic_pass(L, in, fdtd ? L->tmp() : in, true, chk[k], sk, &nblk[k]));
+      b->launches += L->launches - l0;
+      done[k] = 1;
+      continue;
+    }
+    std::vector<int> g;
+    for (int q = k; q < R; ++q) {
+      if (done[q]) continue;
+      qf_lattice* M = b->m[run[q]].lat;
+      // complex-FP32 FDTD members of any size share a launch (the stencil kernel takes
+      // each member's N from its block table); FFT members need the same plan (N)
+      if (!M->c64() || (M->kinetic == QF_KIN_FDTD) != fdtd || (!fdtd && M->d.n != L->d.n)) continue;
+      if (!fdtd && (M->v_real != L->v_real || chk[q] != chk[k] || uses_fft2(M) != uses_fft2(L))) continue;
+      g.push_back(q);
+      done[q] = 1;
+    }
+    const int n = L->d.n;
+    for (size_t off = 0; off < g.size(); off += kGroupMax) {
+      const int cnt = (int)std::min<size_t>(kGroupMax, g.size() - off);
+      if (fdtd) {
+        StencilTmaGroup<float> sg;
+        for (int j = 0; j < cnt; ++j) {
+          const int q = g[off + j];
+          qf_lattice* M = b->m[run[q]].lat;
+          const int zc = tuned_zchunk<float>(M);
+          const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
+          if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0, zc))
+            return bfail(b, QF_ECUDA, "tensor map encoding failed");
+          // one error flag per launch: the first member's
+          nblk[q] = stencil_blocks<float>(M->d.n, zc);
+        }
+        QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
+        b->launches += 1;
+      } else {
+        const bool two = uses_fft2(L);
+        FftGroup<float> fg, f0;
+        fg.count = cnt;
+        f0.count = 0;
+        for (int j = 0; j < cnt; ++j) {
+          const int q = g[off + j];
+          qf_lattice* M = b->m[run[q]].lat;
+          const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
+          fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
+          fg.a[j].emit_next = 1;
+          nblk[q] = two ? fft2_final_blocks() : fft_final_blocks<float>(n);
+          if (!M->xfwd_valid) {
+            f0.a[f0.count] = fg.a[j];
+            f0.a[f0.count].src = fg.a[j].psi;
+            f0.count++;
+          }
+          M->xfwd_valid = true;
+        }
+        if (f0.count > 0) {
+          QF_BCUDA(b, two ? launch_fft2_group_pass(0, f0, st) : launch_fft_group_pass<float>(n, 0, f0, st));
+          b->launches += 1;
+        }
+        for (int j = 0; j < cnt; ++j) fg.a[j].src = nullptr;
+        for (int ps = 1; ps < (two ? 3 : kFftPasses); ++ps) {
+          QF_BCUDA(b, two ? launch_fft2_group_pass(ps, fg, st) : launch_fft_group_pass<float>(n, ps, fg, st));
+          b->launches += 1;
+        }
+      }
+    }
+  }
+  return QF_OK;
+}
+
+// The check_every - 1 steps after a check that every running member took together
+// issue the same launches each time the batch holds the same members in the same buffer
+// state, so they are captured once into a CUDA graph (keyed by members, FDTD buffer
+// parity and first-pass state) and replayed; the host bookkeeping of those steps follows
+// the replay.  Returns QF_OK with *used = false when the interval does not qualify.
+static qf_status batch_chunk_graph(qf_batch* b, const std::vector<int>& run, int64_t steps_left, int check_every,
+                                   int snap_every, cudaStream_t st, bool* used) {
+  *used = false;
+  const int k = check_every - 1;
+  if (!b->use_graphs || k < 2 || steps_left < k) return QF_OK;
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return QF_OK;
+  if (!(snap_every == 0 || snap_every == check_every)) return QF_OK;
+  std::vector<uintptr_t> key;
+  key.push_back((uintptr_t)k);
+  for (int i : run) {
+    const auto& mb = b->m[i];
+    qf_lattice* L = mb.lat;
+    if (!L->pending_scale || L->prof || L->step % check_every != 1 || mb.steps_done + k > mb.max_steps)
+      return QF_OK;
+    key.push_back(reinterpret_cast<uintptr_t>(L));
+    key.push_back((uintptr_t)((L->live & 1) | (L->xfwd_valid ? 2 : 0) | (uses_fft2(L) ? 4 : 0)));
+  }
+  const qf_batch::BGraph* hit = nullptr;
+  for (auto& g : b->graphs)
+    if (g.key == key) hit = &g;
+  if (!hit) {
+    // capture the k steps, then put back the host state the capture advanced
+    struct Saved {
+      int live;
+      bool clean, xfwd, pending;
+      int64_t launches;
+    };
+    std::vector<Saved> saved;
+    for (int i : run) {
+      qf_lattice* L = b->m[i].lat;
+      saved.push_back({L->live, L->clean, L->xfwd_valid, L->pending_scale, L->launches});
+    }
+    const int64_t l0 = b->launches;
+    std::vector<char> nochk(run.size(), 0);
+    std::vector<int> nblk(run.size(), 0);
+    cudaGraph_t graph = nullptr;
+    QF_BCUDA(b, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    qf_status s = QF_OK;
+    for (int j = 0; j < k && s == QF_OK; ++j) {
+      s = batch_issue_step(b, run, nochk, nblk, st);
+      for (int i : run) {
+        qf_lattice* L = b->m[i].lat;
+        L->pending_scale = false;
+        if (L->kinetic == QF_KIN_FDTD) L->live = 1 - L->live;
+      }
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+    const int64_t nl = b->launches - l0;
+    b->launches = l0;
+    for (size_t q = 0; q < run.size(); ++q) {
+      qf_lattice* L = b->m[run[q]].lat;
+      L->live = saved[q].live;
+      L->clean = saved[q].clean;
+      L->xfwd_valid = saved[q].xfwd;
+      L->pending_scale = saved[q].pending;
+      L->launches = saved[q].launches;
+    }
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = e2;
+    if (s == QF_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (s != QF_OK || e != cudaSuccess) {
+      // (a failed capture leaves the batch on ordinary launches)
+      cudaGetLastError();
+      b->use_graphs = false;
+      return QF_OK;
+    }
+    if (b->graphs.size() >= 8) {
+      cudaGraphExecDestroy(b->graphs.front().exec);
+      b->graphs.erase(b->graphs.begin());
+    }
+    b->graphs.push_back({key, exec, nl});
+    b->graph_captures += 1;
+    hit = &b->graphs.back();
+  }
+  QF_BCUDA(b, cudaGraphLaunch(hit->exec, st));
+  b->launches += hit->launches;
+  b->graph_replays += 1;
+  // host bookkeeping of the k steps: the first renormalises, the others scale by 2^kcur
+  for (int i : run) {
+    auto& mb = b->m[i];
+    qf_lattice* L = mb.lat;
+    L->K += (long long)k * L->kcur + L->jcur - L->K_check;
+    L->renorm_step = L->step;
+    L->pending_scale = false;
+    if (L->kinetic == QF_KIN_FDTD) {
+      L->live ^= (k & 1);
+      L->clean = true;
+    }
+    for (int j = 0; j < k; ++j) {
+      L->step += 1;
+      L->tau += L->dtau;
+    }
+    mb.steps_done += k;
+    QF_BCUDA(b, take_snapshot(L, snap_every, st));
+  }
+  *used = true;
   return QF_OK;
 }
 
@@ -1492,6 +1696,15 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
         else run.push_back(i);
       }
     if (run.empty()) break;
+    if (check_every > 0) {
+      bool used = false;
+      qf_status gs = batch_chunk_graph(b, run, steps - s, check_every, snap_every, st, &used);
+      if (gs != QF_OK) return gs;
+      if (used) {
+        s += check_every - 2;  // (the loop adds the last one)
+        continue;
+      }
+    }
     const int R = (int)run.size();
     chk.assign(R, 0);
     nblk.assign(R, 0);
@@ -1503,80 +1716,8 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
       tau_t[k] = L->tau;
       chk[k] = check_every > 0 && L->step % check_every == 0;
     }
-    // group FP32 members by (N, kinetic family, real V, check); FP64 members run alone
-    std::vector<char> done(R, 0);
-    for (int k = 0; k < R; ++k) {
-      if (done[k]) continue;
-      qf_lattice* L = b->m[run[k]].lat;
-      const double* sk = L->pending_scale ? &L->sc()->scale[1] : &L->sc()->scale[2];
-      const bool fdtd = L->kinetic == QF_KIN_FDTD;
-      if (!L->c64()) {
-        void* in = L->psi();
-        const int64_t l0 = L->launches;
-        QF_BCUDA(b, kinetic_pass(L, in, fdtd ? L->tmp() : in, true, chk[k], sk, &nblk[k]));
-        b->launches += L->launches - l0;
-        done[k] = 1;
-        continue;
-      }
-      std::vector<int> g;
-      for (int q = k; q < R; ++q) {
-        if (done[q]) continue;
-        qf_lattice* M = b->m[run[q]].lat;
-        // complex-FP32 FDTD members of any size share a launch (the stencil kernel takes
-        // each member's N from its block table); FFT members need the same plan (N)
-        if (!M->c64() || (M->kinetic == QF_KIN_FDTD) != fdtd || (!fdtd && M->d.n != L->d.n)) continue;
-        if (!fdtd && (M->v_real != L->v_real || chk[q] != chk[k] || uses_fft2(M) != uses_fft2(L))) continue;
-        g.push_back(q);
-        done[q] = 1;
-      }
-      const int n = L->d.n;
-      for (size_t off = 0; off < g.size(); off += kGroupMax) {
-        const int cnt = (int)std::min<size_t>(kGroupMax, g.size() - off);
-        if (fdtd) {
-          StencilTmaGroup<float> sg;
-          for (int j = 0; j < cnt; ++j) {
-            const int q = g[off + j];
-            qf_lattice* M = b->m[run[q]].lat;
-            const int zc = tuned_zchunk<float>(M);
-            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
-            if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0, zc))
-              return bfail(b, QF_ECUDA, "tensor map encoding failed");
-            // one error flag per launch: the first member's
-            nblk[q] = stencil_blocks<float>(M->d.n, zc);
-          }
-          QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
-          b->launches += 1;
-        } else {
-          const bool two = uses_fft2(L);
-          FftGroup<float> fg, f0;
-          fg.count = cnt;
-          f0.count = 0;
-          for (int j = 0; j < cnt; ++j) {
-            const int q = g[off + j];
-            qf_lattice* M = b->m[run[q]].lat;
-            const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
-            fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
-            fg.a[j].emit_next = 1;
-            nblk[q] = two ? fft2_final_blocks() : fft_final_blocks<float>(n);
-            if (!M->xfwd_valid) {
-              f0.a[f0.count] = fg.a[j];
-              f0.a[f0.count].src = fg.a[j].psi;
-              f0.count++;
-            }
-            M->xfwd_valid = true;
-          }
-          if (f0.count > 0) {
-            QF_BCUDA(b, two ? launch_fft2_group_pass(0, f0, st) : launch_fft_group_pass<float>(n, 0, f0, st));
-            b->launches += 1;
-          }
-          for (int j = 0; j < cnt; ++j) fg.a[j].src = nullptr;
-          for (int ps = 1; ps < (two ? 3 : kFftPasses); ++ps) {
-            QF_BCUDA(b, two ? launch_fft2_group_pass(ps, fg, st) : launch_fft_group_pass<float>(n, ps, fg, st));
-            b->launches += 1;
-          }
-        }
-      }
-    }
+    qf_status is = batch_issue_step(b, run, chk, nblk, st);
+    if (is != QF_OK) return is;
     // per-member bookkeeping, identical to qf_step_n
     bool any_check = false;
     for (int k = 0; k < R; ++k) {
@@ -1612,6 +1753,20 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
     nr += x.status == QF_BATCH_RUNNING;
   }
   if (n_running) *n_running = nr;
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_use_graphs(qf_batch* b, int enable) {
+  if (!b) return QF_EINVAL;
+  b->use_graphs = enable != 0;
+  if (!b->use_graphs) b->drop_graphs();
+  return QF_OK;
+}
+
+extern "C" qf_status qf_batch_graph_info(qf_batch* b, int64_t* captures, int64_t* replays) {
+  if (!b) return QF_EINVAL;
+  if (captures) *captures = b->graph_captures;
+  if (replays) *replays = b->graph_replays;
   return QF_OK;
 }
 

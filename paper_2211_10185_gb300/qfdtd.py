@@ -78,6 +78,8 @@ SIGNATURES = {
     "qf_batch_members": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64), C.c_int]),
     "qf_batch_info": (C.c_int, [_P, C.POINTER(C.c_int64)]),
     "qf_batch_set_stopping": (C.c_int, [_P, C.c_int]),
+    "qf_batch_use_graphs": (C.c_int, [_P, C.c_int]),
+    "qf_batch_graph_info": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "qf_batch_last_error": (C.c_char_p, [_P]),
     "qf_selftest_bounded_wait": (C.c_int, [_P]),
     "qf_use_graphs": (C.c_int, [_P, C.c_int]),

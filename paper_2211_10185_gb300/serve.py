@@ -29,7 +29,10 @@ class Batch:
         import torch
 
         self.lib = Q.load()
-        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        # a stream of its own: CUDA graphs cannot capture the legacy default stream (members
+        # hand over on it: qf_batch_add synchronises their streams, qf_batch_step ends
+        # synchronised)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
         h = C.c_void_p()
         st = self.lib.qf_batch_create(C.c_void_p(self.stream.cuda_stream), C.byref(h))
         if st != Q.QF_OK:
@@ -69,6 +72,15 @@ class Batch:
     def set_stopping(self, rule: int):
         """Q.QF_STOP_DIFFERENCE or Q.QF_STOP_EXTRAPOLATED for the members' checks."""
         self._check(self.lib.qf_batch_set_stopping(self.h, int(rule)), "qf_batch_set_stopping")
+
+    def use_graphs(self, enable: bool = True):
+        self._check(self.lib.qf_batch_use_graphs(self.h, int(bool(enable))), "qf_batch_use_graphs")
+
+    def graph_info(self) -> tuple[int, int]:
+        """(graphs captured, graph replays)."""
+        c, r = C.c_int64(), C.c_int64()
+        self._check(self.lib.qf_batch_graph_info(self.h, C.byref(c), C.byref(r)), "qf_batch_graph_info")
+        return c.value, r.value
 
     def launches(self) -> int:
         x = C.c_int64()

@@ -206,3 +206,33 @@ def test_fdtd_members_of_different_sizes_share_one_launch_per_step():
     assert b.launches() == 37
     for la, lm in zip(alone, mixed):
         assert np.array_equal(la.get_wavefunction(), lm.get_wavefunction())
+
+
+def test_batch_graph_replay_is_bitwise_identical_to_launches():
+    """A fixed batch (FFT members of two sizes, FDTD members of two sizes, an FP64
+    member) stepped in check intervals: the intervals after the first check replay one
+    captured graph, and every field, energy and snapshot equals the ordinary launches'."""
+    from paper_2211_10185_gb300.serve import Batch
+
+    specs = [(16, I.FFT_REL, "c64", False), (24, I.FFT_SYMANZIK, "c64", True), (32, I.FFT_NAIVE, "c64", False),
+             (24, I.FDTD, "c64", False), (32, I.FDTD, "c64", True), (16, I.FFT_NAIVE, "c128", False)]
+    runs = []
+    for graphs in (True, False):
+        lats = [_make(s, 50 + i) for i, s in enumerate(specs)]
+        b = Batch()
+        b.use_graphs(graphs)
+        for lat in lats:
+            b.add(lat, 100000, 0.0)
+        for _ in range(5):
+            b.step(32, check_every=32)
+        runs.append((b, lats))
+    (bg, lg), (bn, ln) = runs
+    captures, replays = bg.graph_info()
+    assert captures == 1 and replays == 5
+    assert bn.graph_info() == (0, 0)
+    assert bg.launches() == bn.launches()
+    for a, c in zip(lg, ln):
+        assert np.array_equal(a.get_wavefunction(), c.get_wavefunction())
+        assert a.energies() == c.energies()
+        assert np.array_equal(a.get_wavefunction(100), c.get_wavefunction(100))
+        assert a.info()["step"] == c.info()["step"] == 160
