@@ -227,6 +227,17 @@ qf_status qf_use_graphs(qf_lattice* lat, int enable);
  * any captured graphs. */
 qf_status qf_use_two_pass_fft(qf_lattice* lat, int enable);
 
+/* Tile choice of the complex-FP32 four-pass FFT kernels for lattice size n (no
+ * counterpart in the paper; every size but the two-pass N = 256 step).  Variant 0 tiles
+ * about 4096 elements per block with up to 16 contiguous columns; variant 1 half of both
+ * (more, smaller blocks per SM).  Both compute the same transforms (the fields agree
+ * bitwise; reductions may differ in their last bits).  variant -1, the default, lets the
+ * autotuner time both on the first FFT step of a lattice of that size and keep the
+ * faster for the process; 0 or 1 fixes it (process-wide, affects every handle).
+ * qf_get_fft_tiles returns -1 while the choice is pending. */
+qf_status qf_set_fft_tiles(int n, int variant);
+qf_status qf_get_fft_tiles(int n, int* variant);
+
 /* Temporal blocking of the FDTD step (the step of Sec. 2 with the Eq. HK0 term; no
  * counterpart in the paper).  k = 2, the default: on complex-FP32 lattices qf_step_n
  * runs two consecutive steps with no check at either and no snapshot after the first as

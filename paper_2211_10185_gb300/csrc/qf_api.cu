@@ -92,7 +92,7 @@ static Layout make_layout(const qf_lattice_desc& d) {
   // partial sums: the largest grid of any reducing kernel
   int mb = field_blocks();
   if (fft_supported(d.n)) {
-    int fb = d.prec == QF_PREC_C64 ? fft_final_blocks<float>(d.n) : fft_final_blocks<double>(d.n);
+    int fb = d.prec == QF_PREC_C64 ? fft_final_blocks_max<float>(d.n) : fft_final_blocks_max<double>(d.n);
     if (fb > mb) mb = fb;
   }
   int sb = d.prec == QF_PREC_C64 ? stencil_blocks<float>(d.n) : stencil_blocks<double>(d.n);
@@ -613,6 +613,56 @@ static int tuned_zchunk(qf_lattice* lat) {
   return best;
 }
 
+// ---- autotuner: tile variant of the complex-FP32 four-pass FFT kernels, per N ---------
+// On the first four-pass FFT step of a size, both variants time the five passes of a step
+// (the reducing pass measuring only: psi is untouched, the scratch field is overwritten)
+// and the faster is kept for the process.  Never runs while the stream is being captured.
+static void tune_fft_tiles(qf_lattice* lat) {
+  const int n = lat->d.n;
+  if (!lat->c64() || lat->kinetic == QF_KIN_FDTD || uses_fft2(lat) || fft_tile_choice(n) >= 0) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(lat->st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (fft_tile_choice(n) >= 0) return;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return;
+  }
+  FftPassArgs<float> p = fft_args<float>(lat, lat->psi(), false, true, &lat->sc()->scale[0]);
+  p.emit_next = 0;
+  float best_ms = 1e30f;
+  int best = 0;
+  for (int v = 0; v < 2; ++v) {
+    set_fft_tile_choice(n, v);
+    auto step = [&] {
+      cudaError_t e = cudaSuccess;
+      for (int ps = 0; ps < kFftPasses && e == cudaSuccess; ++ps)
+        e = launch_fft_pass<float>(n, ps, p, p.data, lat->st, nullptr);
+      return e;
+    };
+    bool ok = step() == cudaSuccess;  // warm-up
+    float ms = 0, tot = 0;
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+      ok = cudaEventRecord(e0, lat->st) == cudaSuccess && step() == cudaSuccess &&
+           cudaEventRecord(e1, lat->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      tot += ms;
+    }
+    lat->launches += 4 * kFftPasses;
+    if (ok && tot < best_ms) {
+      best_ms = tot;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  set_fft_tile_choice(n, best);
+  lat->xfwd_valid = false;  // the scratch field was overwritten
+}
+
 // Reads and clears the bounded-wait failure flag of a lattice.
 static qf_status check_device_error(qf_lattice* lat) {
   int err = 0;
@@ -730,6 +780,7 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
   }
   // FFT terms: in place on `in` (out must equal in when writing); the scratch field is tmp.
   // A step on the live psi emits the next step's first pass and may skip its own.
+  tune_fft_tiles(lat);  // first four-pass step of this size in the process (overwrites tmp)
   const bool live = write && in == lat->psi();
   const int first = (live && lat->xfwd_valid) ? 1 : 0;
   lat->xfwd_valid = false;
@@ -912,6 +963,7 @@ static cudaError_t run_chunk_graph(qf_lattice* lat, int check_every, int* flips)
     const int64_t launches0 = lat->launches;
     const bool pairs = lat->kinetic == QF_KIN_FDTD && lat->c64() && lat->tblock >= 2 && lat->tbmap_ok;
     const int tzc = pairs ? tuned_tb_zchunk(lat) : 0;  // timed outside the capture
+    tune_fft_tiles(lat);
     if (lat->kinetic == QF_KIN_FDTD) {
       if (lat->c64()) tuned_zchunk<float>(lat);
       else tuned_zchunk<double>(lat);
@@ -1362,6 +1414,17 @@ extern "C" qf_status qf_use_two_pass_fft(qf_lattice* lat, int enable) {
   return QF_OK;
 }
 
+extern "C" qf_status qf_set_fft_tiles(int n, int variant) {
+  if (!fft_supported(n) || variant < -1 || variant > 1) return QF_EINVAL;
+  return set_fft_tile_choice(n, variant) ? QF_OK : QF_EINVAL;
+}
+
+extern "C" qf_status qf_get_fft_tiles(int n, int* variant) {
+  if (!fft_supported(n) || !variant) return QF_EINVAL;
+  *variant = fft_tile_choice(n);
+  return QF_OK;
+}
+
 extern "C" qf_status qf_set_temporal_blocking(qf_lattice* lat, int k) {
   if (!lat) return QF_EINVAL;
   if (k != 1 && k != 2) return fail(lat, QF_EINVAL, "temporal blocking factor must be 1 or 2");
@@ -1527,6 +1590,7 @@ static qf_status batch_issue_step(qf_batch* b, const std::vector<int>& run, cons
         b->launches += 1;
       } else {
         const bool two = uses_fft2(L);
+        tune_fft_tiles(L);  // (runs once per size; never inside a capture)
         FftGroup<float> fg, f0;
         fg.count = cnt;
         f0.count = 0;

@@ -225,6 +225,15 @@ cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStr
 template <typename R>
 int fft_final_blocks(int n);
 
+// The most partial rows any tile variant's reducing pass writes (workspace sizing).
+template <typename R>
+int fft_final_blocks_max(int n);
+// Tile variant of the complex-FP32 four-pass kernels for size n: the choice (-1 while
+// the autotuner has not run), the variant in use, and the setter (false for bad n/v).
+int fft_tile_choice(int n);
+int fft_tile_variant(int n);
+bool set_fft_tile_choice(int n, int v);
+
 // Whether the FFT path has kernels for this n.
 bool fft_supported(int n);
 

@@ -2,13 +2,54 @@
 // qf_fft_impl.cuh; the complex-FP32 entry points are instantiated in qf_fft_group.cu).
 #include <math.h>
 
+#include <atomic>
+
 #include "qf_fft_impl.cuh"
 
 namespace qf {
 
 template int fft_final_blocks<float>(int);
+template int fft_final_blocks_max<float>(int);
 
 bool fft_supported(int n) { return plan_stages(n) > 0; }
+
+// Tile variant of the complex-FP32 four-pass kernels per FFT size: -1 until chosen
+// (variant 0 runs meanwhile), else 0 or 1.  Process-wide.
+static int plan_index(int n) {
+  switch (n) {
+    case 8: return 0;
+    case 12: return 1;
+    case 16: return 2;
+    case 24: return 3;
+    case 32: return 4;
+    case 48: return 5;
+    case 64: return 6;
+    case 96: return 7;
+    case 128: return 8;
+    case 192: return 9;
+    case 256: return 10;
+    case 384: return 11;
+    case 512: return 12;
+    default: return -1;
+  }
+}
+static std::atomic<int> g_tile_variant[13] = {{-1}, {-1}, {-1}, {-1}, {-1}, {-1}, {-1},
+                                              {-1}, {-1}, {-1}, {-1}, {-1}, {-1}};
+
+int fft_tile_choice(int n) {
+  const int i = plan_index(n);
+  return i < 0 ? 0 : g_tile_variant[i].load(std::memory_order_relaxed);
+}
+int fft_tile_variant(int n) {
+  const int v = fft_tile_choice(n);
+  return v < 0 ? 0 : v;
+}
+bool set_fft_tile_choice(int n, int v) {
+  const int i = plan_index(n);
+  if (i < 0 || v < -1 || v > 1) return false;
+  g_tile_variant[i].store(v, std::memory_order_relaxed);
+  return true;
+}
 
 // Host-side twiddle table in the per-stage layout the kernels read.
 int fft_twiddle_count(int n) {

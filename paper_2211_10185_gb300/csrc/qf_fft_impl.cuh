@@ -61,11 +61,14 @@ constexpr int largest_divisor_le(int n, int cap) {
   return best;
 }
 
-template <typename R, int N>
+// Tile geometry of the four-pass kernels.  V = 0: about 4096 (FP32) / 2048 (FP64)
+// elements per tile, y/z tiles up to 16 (8) contiguous columns wide; V = 1: half the tile
+// and half the width (more, smaller blocks per SM).  The autotuner picks V per N.
+template <typename R, int N, int V = 0>
 struct Geom {
   static constexpr int EPT = plan_ept(N);
   static constexpr int S = plan_stages(N);
-  static constexpr int TARGET = sizeof(R) == 4 ? 4096 : 2048;  // elements per tile
+  static constexpr int TARGET = (sizeof(R) == 4 ? 4096 : 2048) >> V;  // elements per tile
   // x pass: LC whole lines per block
   static constexpr int LC = largest_divisor_le(N * N, TARGET / N > 0 ? TARGET / N : 1);
   static constexpr int TL = N / EPT;                       // threads per line
@@ -73,7 +76,7 @@ struct Geom {
   static constexpr int PAD_SHIFT = sizeof(R) == 4 ? 4 : 3;  // one pad element per 128 B
   static constexpr int PL = N + (N >> PAD_SHIFT) + 1;       // padded line length
   // y/z passes: C = L contiguous columns x P outer slices
-  static constexpr int L = largest_divisor_le(N, sizeof(R) == 4 ? 16 : 8);
+  static constexpr int L = largest_divisor_le(N, (sizeof(R) == 4 ? 16 : 8) >> V);
   static constexpr int P = largest_divisor_le(N, TARGET / (L * N) > 0 ? TARGET / (L * N) : 1);
   static constexpr int C = L * P;
   static constexpr int THREADS_S = C * N / EPT;
@@ -248,9 +251,9 @@ __device__ __forceinline__ int e_out(int g, int b, int r) {
 // ------------------------------------------------------------------------------------
 // Shared-memory accessors for the two tile layouts
 // ------------------------------------------------------------------------------------
-template <typename R, int N, bool STRIDED>
+template <typename R, int N, bool STRIDED, int V = 0>
 struct Tile {
-  using G = Geom<R, N>;
+  using G = Geom<R, N, V>;
   cpx<R>* s;
   int col;  // STRIDED: column; contiguous: line
   __device__ __forceinline__ int idx(int e) const {
@@ -264,8 +267,8 @@ struct Tile {
 // Runs stages [FIRST, LAST] of one transform direction.  Stage FIRST reads either global
 // memory (gsrc: element e of this thread's line at gsrc[e * gstride]) or shared memory;
 // stage LAST leaves its outputs in v (natural-order element e_out<N, LAST>).
-template <typename R, int N, bool STRIDED, bool INV, int ST, int LAST>
-__device__ __forceinline__ void run_stages(cpx<R> (&v)[plan_ept(N)], int g, const Tile<R, N, STRIDED>& t,
+template <typename R, int N, bool STRIDED, bool INV, int ST, int LAST, int V = 0>
+__device__ __forceinline__ void run_stages(cpx<R> (&v)[plan_ept(N)], int g, const Tile<R, N, STRIDED, V>& t,
                                            const cpx<R>* tw_s) {
   constexpr int RAD = plan_radix(N, ST);
   constexpr int EPT = plan_ept(N);
@@ -282,7 +285,7 @@ __device__ __forceinline__ void run_stages(cpx<R> (&v)[plan_ept(N)], int g, cons
     for (int b = 0; b < EPT / RN; ++b)
 #pragma unroll
       for (int r = 0; r < RN; ++r) v[b * RN + r] = t.ld(e_in<N, ST + 1>(g, b, r));
-    run_stages<R, N, STRIDED, INV, ST + 1, LAST>(v, g, t, tw_s);
+    run_stages<R, N, STRIDED, INV, ST + 1, LAST, V>(v, g, t, tw_s);
   }
 }
 
@@ -315,9 +318,9 @@ __device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
 // x pass: LC contiguous lines per block.  OP_FWD: src -> data.  OP_FINAL: data (H_K psi
 // in x-transformed space) -> inverse x -> update of psi.  The final pass loads psi and V
 // of its output sites at the start, so those reads overlap the inverse transform.
-template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
+template <typename R, int N, int OP, bool VREAL, bool NEXT = false, int V = 0>
 __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bid) {
-  using G = Geom<R, N>;
+  using G = Geom<R, N, V>;
   constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
   constexpr bool FIN = is_final(OP);
   constexpr bool INV = FIN || OP == OP_INV;
@@ -366,8 +369,8 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
   }
   __syncthreads();  // twiddles visible
 
-  Tile<R, N, false> t{data_s, line};
-  run_stages<R, N, false, INV, 0, S - 1>(v, g, t, tw_s);
+  Tile<R, N, false, V> t{data_s, line};
+  run_stages<R, N, false, INV, 0, S - 1, V>(v, g, t, tw_s);
 
   if constexpr (OP == OP_FWD || OP == OP_INV) {
 #pragma unroll
@@ -425,7 +428,7 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
             for (int r = 0; r < R0; ++r) v[b * R0 + r] = t.ld(e_in<N, 0>(g, b, r));
         }
         // (equal first and last radix: the thread already holds the first stage's inputs)
-        run_stages<R, N, false, false, 0, S - 1>(v, g, t, tw_s);
+        run_stages<R, N, false, false, 0, S - 1, V>(v, g, t, tw_s);
 #pragma unroll
         for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
@@ -437,9 +440,9 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
 
 // y / z passes: C = L x P columns per block.  AXIS 1: points stride N, outer = z (stride
 // N^2).  AXIS 2: points stride N^2, outer = y (stride N).
-template <typename R, int N, int AXIS, int OP>
+template <typename R, int N, int AXIS, int OP, int V = 0>
 __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bid) {
-  using G = Geom<R, N>;
+  using G = Geom<R, N, V>;
   constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
   constexpr long long PSTRIDE = AXIS == 1 ? N : (long long)N * N;
   constexpr long long OSTRIDE = AXIS == 1 ? (long long)N * N : N;
@@ -466,9 +469,9 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
     for (int r = 0; r < R0; ++r) v[b * R0 + r] = a.data[base + e_in<N, 0>(g, b, r) * PSTRIDE];
   __syncthreads();
 
-  Tile<R, N, true> t{data_s, c};
+  Tile<R, N, true, V> t{data_s, c};
   if constexpr (OP == OP_MID) {
-    run_stages<R, N, true, false, 0, S - 1>(v, g, t, tw_s);
+    run_stages<R, N, true, false, 0, S - 1, V>(v, g, t, tw_s);
     // forward z transform done: natural-order kz; multiply by T and start the inverse
     const R sxy = sym_s[x] + sym_s[o];  // kx = x, ky = o (after the x and y passes)
     if constexpr (R0 == RL) {
@@ -497,9 +500,9 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
           v[b * R0 + r] = cscale<R>(t.ld(kz), tm);
         }
     }
-    run_stages<R, N, true, true, 0, S - 1>(v, g, t, tw_s);
+    run_stages<R, N, true, true, 0, S - 1, V>(v, g, t, tw_s);
   } else {
-    run_stages<R, N, true, INV, 0, S - 1>(v, g, t, tw_s);
+    run_stages<R, N, true, INV, 0, S - 1, V>(v, g, t, tw_s);
   }
 #pragma unroll
   for (int b = 0; b < EPT / RL; ++b)
@@ -528,37 +531,38 @@ template <typename R, int N, int AXIS, int OP>
 __global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_kernel(FftPassArgs<R> a) {
   fft_s_body<R, N, AXIS, OP>(a, blockIdx.x);
 }
-template <typename R, int N, int OP, bool VREAL, bool NEXT = false>
-__global__ void __launch_bounds__(Geom<R, N>::THREADS_X) fft_x_group_kernel(const __grid_constant__ FftGroup<R> g) {
-  fft_x_body<R, N, OP, VREAL, NEXT>(g.a[blockIdx.y], x_block<OP>(blockIdx.x));
+template <typename R, int N, int OP, bool VREAL, bool NEXT = false, int V = 0>
+__global__ void __launch_bounds__(Geom<R, N, V>::THREADS_X) fft_x_group_kernel(const __grid_constant__ FftGroup<R> g) {
+  fft_x_body<R, N, OP, VREAL, NEXT, V>(g.a[blockIdx.y], x_block<OP>(blockIdx.x));
 }
-template <typename R, int N, int AXIS, int OP>
-__global__ void __launch_bounds__(Geom<R, N>::THREADS_S) fft_s_group_kernel(const __grid_constant__ FftGroup<R> g) {
-  fft_s_body<R, N, AXIS, OP>(g.a[blockIdx.y], blockIdx.x);
+template <typename R, int N, int AXIS, int OP, int V = 0>
+__global__ void __launch_bounds__(Geom<R, N, V>::THREADS_S) fft_s_group_kernel(const __grid_constant__ FftGroup<R> g) {
+  fft_s_body<R, N, AXIS, OP, V>(g.a[blockIdx.y], blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------
-template <typename R, int N>
+template <typename R, int N, int V = 0>
 static size_t smem_x() {
-  using G = Geom<R, N>;
+  using G = Geom<R, N, V>;
   return G::TW * sizeof(cpx<R>) + G::LC * G::PL * sizeof(cpx<R>) + 32 * kNumSums * sizeof(double);
 }
-template <typename R, int N>
+template <typename R, int N, int V = 0>
 static size_t smem_s() {
-  using G = Geom<R, N>;
+  using G = Geom<R, N, V>;
   return G::TW * sizeof(cpx<R>) + ((N * sizeof(R) + 15) / 16) * 16 + (size_t)G::C * N * sizeof(cpx<R>);
 }
 
 // Variant of the final x pass for (real V, writes psi', check sums, emits the next x transform).
-template <typename R, int N, bool GROUP, bool VREAL>
+template <typename R, int N, bool GROUP, bool VREAL, int V = 0>
 static auto final_kernel(bool write, bool sums, bool next) {
   if constexpr (GROUP) {
-    if (!write) return fft_x_group_kernel<R, N, OP_SUMS, VREAL, false>;
-    if (sums) return next ? fft_x_group_kernel<R, N, OP_FINAL_SUMS, VREAL, true>
-                          : fft_x_group_kernel<R, N, OP_FINAL_SUMS, VREAL, false>;
-    return next ? fft_x_group_kernel<R, N, OP_FINAL, VREAL, true> : fft_x_group_kernel<R, N, OP_FINAL, VREAL, false>;
+    if (!write) return fft_x_group_kernel<R, N, OP_SUMS, VREAL, false, V>;
+    if (sums) return next ? fft_x_group_kernel<R, N, OP_FINAL_SUMS, VREAL, true, V>
+                          : fft_x_group_kernel<R, N, OP_FINAL_SUMS, VREAL, false, V>;
+    return next ? fft_x_group_kernel<R, N, OP_FINAL, VREAL, true, V>
+                : fft_x_group_kernel<R, N, OP_FINAL, VREAL, false, V>;
   } else {
     if (!write) return fft_x_kernel<R, N, OP_SUMS, VREAL, false>;
     if (sums) return next ? fft_x_kernel<R, N, OP_FINAL_SUMS, VREAL, true> : fft_x_kernel<R, N, OP_FINAL_SUMS, VREAL, false>;
@@ -568,18 +572,18 @@ static auto final_kernel(bool write, bool sums, bool next) {
 
 // Raises the dynamic shared-memory limit of every x-pass variant (the largest tiles need
 // more than the default 48 KB).
-template <typename R, int N, bool GROUP>
+template <typename R, int N, bool GROUP, int V = 0>
 static void set_x_attrs(size_t sx) {
   for (int vr = 0; vr < 2; ++vr)
     for (int w = 0; w < 2; ++w)
       for (int su = 0; su < 2; ++su)
         for (int nx = 0; nx < 2; ++nx) {
-          const void* f = vr ? (const void*)final_kernel<R, N, GROUP, true>(w, su, nx)
-                             : (const void*)final_kernel<R, N, GROUP, false>(w, su, nx);
+          const void* f = vr ? (const void*)final_kernel<R, N, GROUP, true, V>(w, su, nx)
+                             : (const void*)final_kernel<R, N, GROUP, false, V>(w, su, nx);
           cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
         }
   if constexpr (GROUP)
-    cudaFuncSetAttribute((const void*)fft_x_group_kernel<R, N, OP_FWD, false, false>,
+    cudaFuncSetAttribute((const void*)fft_x_group_kernel<R, N, OP_FWD, false, false, V>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
   else
     cudaFuncSetAttribute((const void*)fft_x_kernel<R, N, OP_FWD, false, false>,
@@ -627,39 +631,98 @@ static cudaError_t pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t 
 // One pass for a group of lattices of size N: g.a[i] holds lattice i's arguments as
 // launch_fft_pass would build them (data = its scratch field, src = psi on pass 0).  The
 // final pass variant follows member 0 (members of a group agree on it).
-template <typename R, int N>
+template <typename R, int N, int V = 0>
 static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st) {
-  using G = Geom<R, N>;
-  const size_t sx = smem_x<R, N>(), ss = smem_s<R, N>();
+  using G = Geom<R, N, V>;
+  const size_t sx = smem_x<R, N, V>(), ss = smem_s<R, N, V>();
   static bool attr_done = false;
   if (!attr_done) {
-    set_x_attrs<R, N, true>(sx);
-    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_MID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    cudaFuncSetAttribute(fft_x_group_kernel<R, N, OP_INV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
+    set_x_attrs<R, N, true, V>(sx);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_FWD, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_MID, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 1, OP_INV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_FWD, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_s_group_kernel<R, N, 2, OP_INV, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    cudaFuncSetAttribute(fft_x_group_kernel<R, N, OP_INV, false, false, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx);
     attr_done = true;
   }
   const dim3 gx(N * N / G::LC, g.count), gs((N / G::L) * (N / G::P), g.count);
   const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0, write = g.a[0].write_psi != 0;
   const bool next = write && g.a[0].emit_next != 0;
   switch (pass) {
-    case 0: fft_x_group_kernel<R, N, OP_FWD, false><<<gx, G::THREADS_X, sx, st>>>(g); break;
-    case 1: fft_s_group_kernel<R, N, 1, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
-    case 2: fft_s_group_kernel<R, N, 2, OP_MID><<<gs, G::THREADS_S, ss, st>>>(g); break;
-    case 3: fft_s_group_kernel<R, N, 1, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
-    case 5: fft_s_group_kernel<R, N, 2, OP_FWD><<<gs, G::THREADS_S, ss, st>>>(g); break;
-    case 6: fft_s_group_kernel<R, N, 2, OP_INV><<<gs, G::THREADS_S, ss, st>>>(g); break;
-    case 7: fft_x_group_kernel<R, N, OP_INV, false><<<gx, G::THREADS_X, sx, st>>>(g); break;
+    case 0: fft_x_group_kernel<R, N, OP_FWD, false, false, V><<<gx, G::THREADS_X, sx, st>>>(g); break;
+    case 1: fft_s_group_kernel<R, N, 1, OP_FWD, V><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 2: fft_s_group_kernel<R, N, 2, OP_MID, V><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 3: fft_s_group_kernel<R, N, 1, OP_INV, V><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 5: fft_s_group_kernel<R, N, 2, OP_FWD, V><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 6: fft_s_group_kernel<R, N, 2, OP_INV, V><<<gs, G::THREADS_S, ss, st>>>(g); break;
+    case 7: fft_x_group_kernel<R, N, OP_INV, false, false, V><<<gx, G::THREADS_X, sx, st>>>(g); break;
     case 4:
-      if (vreal) final_kernel<R, N, true, true>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
-      else final_kernel<R, N, true, false>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
+      if (vreal) final_kernel<R, N, true, true, V>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
+      else final_kernel<R, N, true, false, V>(write, sums, next)<<<gx, G::THREADS_X, sx, st>>>(g);
       break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+// Tile variant of the complex-FP32 four-pass kernels in use for size n (0 or 1; chosen
+// by the autotuner in the C ABI, qf_fft_f32.cu holds the table) and the launcher of
+// variant 1, compiled in its own translation unit (qf_fft_group_t1.cu).
+int fft_tile_variant(int n);
+cudaError_t launch_fft_group_pass_t1(int n, int pass, const FftGroup<float>& g, cudaStream_t st);
+
+// Partial-sum rows of the reducing x pass for size n with tile variant V.
+template <typename R, int V>
+int fft_final_blocks_v(int n) {
+  switch (n) {
+#define QF_CASE(NN) \
+  case NN:          \
+    return NN * NN / Geom<R, NN, V>::LC;
+    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
+    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
+#undef QF_CASE
+    default:
+      return 0;
+  }
+}
+
+template <typename R>
+cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st) {
+  if constexpr (sizeof(R) == 4) {
+    if (fft_tile_variant(n) == 1) return launch_fft_group_pass_t1(n, pass, g, st);
+  }
+  switch (n) {
+#define QF_CASE(NN) \
+  case NN:          \
+    return group_pass_n<R, NN>(pass, g, st);
+    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
+    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
+#undef QF_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+// Partial-sum rows of the reducing x pass for size n as launched now (complex FP32: the
+// tile variant in use).
+template <typename R>
+int fft_final_blocks(int n) {
+  if constexpr (sizeof(R) == 4) {
+    if (fft_tile_variant(n) == 1) return fft_final_blocks_v<R, 1>(n);
+  }
+  return fft_final_blocks_v<R, 0>(n);
+}
+
+// The most partial rows any variant's reducing pass writes (workspace sizing).
+template <typename R>
+int fft_final_blocks_max(int n) {
+  const int a = fft_final_blocks_v<R, 0>(n);
+  if constexpr (sizeof(R) == 4) {
+    const int b = fft_final_blocks_v<R, 1>(n);
+    return a > b ? a : b;
+  }
+  return a;
 }
 
 // Complex-FP32 lattices always run the grouped kernels (a lone lattice is a group of one),
@@ -667,14 +730,13 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
 template <typename R, int N>
 static cudaError_t single_pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
   if constexpr (sizeof(R) == 4) {
-    using G = Geom<R, N>;
-    if (nfinal) *nfinal = N * N / G::LC;
+    if (nfinal) *nfinal = fft_final_blocks<R>(N);
     FftGroup<R> g;
     g.count = 1;
     g.a[0] = a;
     g.a[0].data = tmp;
     g.a[0].src = (pass == 0) ? a.psi : nullptr;
-    return group_pass_n<R, N>(pass, g, st);
+    return launch_fft_group_pass<R>(N, pass, g, st);
   } else {
     return pass_n<R, N>(pass, a, tmp, st, nfinal);
   }
@@ -691,34 +753,6 @@ cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, c
 #undef QF_CASE
     default:
       return cudaErrorInvalidValue;
-  }
-}
-
-template <typename R>
-cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st) {
-  switch (n) {
-#define QF_CASE(NN) \
-  case NN:          \
-    return group_pass_n<R, NN>(pass, g, st);
-    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
-    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
-#undef QF_CASE
-    default:
-      return cudaErrorInvalidValue;
-  }
-}
-
-template <typename R>
-int fft_final_blocks(int n) {
-  switch (n) {
-#define QF_CASE(NN) \
-  case NN:          \
-    return NN * NN / Geom<R, NN>::LC;
-    QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
-    QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
-#undef QF_CASE
-    default:
-      return 0;
   }
 }
 

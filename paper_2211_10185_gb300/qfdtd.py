@@ -85,6 +85,8 @@ SIGNATURES = {
     "qf_use_graphs": (C.c_int, [_P, C.c_int]),
     "qf_set_temporal_blocking": (C.c_int, [_P, C.c_int]),
     "qf_use_two_pass_fft": (C.c_int, [_P, C.c_int]),
+    "qf_set_fft_tiles": (C.c_int, [C.c_int, C.c_int]),
+    "qf_get_fft_tiles": (C.c_int, [C.c_int, C.POINTER(C.c_int)]),
     "qf_last_error": (C.c_char_p, [_P]),
     "qf_version": (C.c_char_p, []),
 }

@@ -337,3 +337,35 @@ def test_prolongation_matches_oracle(nc, prec):
     got = fine.get_wavefunction()
     assert_field_close(got, ref, {"c128": 1e-13, "c64": 1e-6}[prec])
     assert np.max(np.abs(got[::2, ::2, ::2] - coarse.get_wavefunction())) < {"c128": 1e-12, "c64": 1e-5}[prec]
+
+
+@pytest.mark.parametrize("n", [16, 48, 96, 128, 192])
+def test_fft_tile_variants_agree_bitwise_and_match_oracle(n):
+    """Both tile variants of the complex-FP32 four-pass kernels (the autotuner's choices)
+    give bitwise the same fields, each equal to the oracle's step; the choice is then put
+    back as it was."""
+    import ctypes as C
+
+    from paper_2211_10185_gb300 import qfdtd as Q
+
+    lib = Q.load()
+    old = C.c_int()
+    assert lib.qf_get_fft_tiles(n, C.byref(old)) == Q.QF_OK
+    a, m = 0.2, 1.3
+    v = I.cornell(n, a, 0.5, 0.2)
+    fields = []
+    try:
+        for variant in (0, 1):
+            assert lib.qf_set_fft_tiles(n, variant) == Q.QF_OK
+            ref, gpu = _pair(n, a, O.FFT_REL, m, "c64", v, seed=n + 5)
+            ref.step_n(3, check_every=2)
+            gpu.step_n(3, check_every=2)
+            got = gpu.get_wavefunction()
+            assert_field_close(got, ref.psi, FIELD_TOL["c64"] * 3 * (1 + math.log2(n)), what=f"N={n} variant {variant}")
+            assert abs(gpu.energies()["e"] - ref.energies()["e"]) < 1e-5 * abs(ref.energies()["e"])
+            fields.append(got)
+            gpu.close()
+    finally:
+        lib.qf_set_fft_tiles(n, old.value)
+    assert np.array_equal(fields[0], fields[1])
+    assert lib.qf_set_fft_tiles(10, 0) == Q.QF_EINVAL and lib.qf_set_fft_tiles(n, 2) == Q.QF_EINVAL
