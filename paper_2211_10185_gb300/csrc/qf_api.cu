@@ -1,7 +1,7 @@
 // C ABI of libqfdtd (declared in include/qfdtd.h): lattice handles over a caller-owned
 // device workspace, the step loop with its checks and snapshots, Gram-Schmidt excited
 // states and parity projection.  Every arithmetic step on fields runs in the kernels of
-// qf_fft_impl.cuh (four-pass FFT step), qf_fft2.cuh (two-pass N = 256 step),
+// qf_fft_impl.cuh (four-pass FFT step), qf_fft2.cuh (two-pass step, N = 128 and 256),
 // qf_stencil_tma.cuh / qf_stencil_tb.cuh (FDTD steps) and qf_fields.cu; this file only
 // sequences them.
 #include <math.h>
@@ -24,9 +24,9 @@ namespace qf {
 bool encode_stencil_map(CUtensorMap* map, void* field, int n, bool c64);
 bool encode_tb_map(CUtensorMap* map, void* field, int n);
 bool fft2_supported(int n);
-int fft2_final_blocks();
-int fft2_measure_blocks();
-cudaError_t launch_fft2_group_pass(int pass, const FftGroup<float>& g, cudaStream_t st);
+int fft2_final_blocks(int n);
+int fft2_measure_blocks(int n);
+cudaError_t launch_fft2_group_pass(int n, int pass, const FftGroup<float>& g, cudaStream_t st);
 cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st);
 cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st);
 template <typename R>
@@ -95,6 +95,7 @@ static Layout make_layout(const qf_lattice_desc& d) {
     int fb = d.prec == QF_PREC_C64 ? fft_final_blocks_max<float>(d.n) : fft_final_blocks_max<double>(d.n);
     if (fb > mb) mb = fb;
   }
+  if (d.prec == QF_PREC_C64 && fft2_supported(d.n) && fft2_measure_blocks(d.n) > mb) mb = fft2_measure_blocks(d.n);
   int sb = d.prec == QF_PREC_C64 ? stencil_blocks<float>(d.n) : stencil_blocks<double>(d.n);
   if (sb > mb) mb = sb;
   L.max_blocks = mb;
@@ -166,7 +167,7 @@ struct qf_lattice {
   // the Dirichlet planes (it is after any FDTD step), which the two-step kernel needs
   int tblock = 2;
   bool clean = false;
-  // N = 256 complex-FP32 FFT steps in two passes over HBM (qf_fft2.cuh) instead of four;
+  // N = 128 and 256 complex-FP32 FFT steps in two passes over HBM (qf_fft2.cuh) instead of four;
   // the scratch field then holds the four-step layout, so switching drops xfwd_valid
   bool two_pass = true;
   std::string err;
@@ -791,11 +792,11 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
     g.count = 1;
     g.a[0] = fft_args<float>(lat, in, false, true, scale);
     g.a[0].src = reinterpret_cast<const cpx<float>*>(in);
-    if (nblocks) *nblocks = fft2_measure_blocks();
-    cudaError_t e = launch(lat, K_FFT2_XY_FWD_SUMS, [&] { return launch_fft2_group_pass(3, g, lat->st); });
+    if (nblocks) *nblocks = fft2_measure_blocks(n);
+    cudaError_t e = launch(lat, K_FFT2_XY_FWD_SUMS, [&] { return launch_fft2_group_pass(n, 3, g, lat->st); });
     if (e != cudaSuccess) return e;
     g.a[0].src = nullptr;
-    return launch(lat, K_FFT2_YZ_SUMS, [&] { return launch_fft2_group_pass(4, g, lat->st); });
+    return launch(lat, K_FFT2_YZ_SUMS, [&] { return launch_fft2_group_pass(n, 4, g, lat->st); });
   }
   if (uses_fft2(lat)) {
     // two-pass step: A (natural -> scratch; skipped when the previous step emitted it),
@@ -804,12 +805,12 @@ static cudaError_t kinetic_pass(qf_lattice* lat, void* in, void* out, bool write
     g.count = 1;
     g.a[0] = fft_args<float>(lat, in, write, reduce, scale);
     g.a[0].emit_next = live ? 1 : 0;
-    if (nblocks) *nblocks = fft2_final_blocks();
+    if (nblocks) *nblocks = fft2_final_blocks(n);
     for (int ps = first; ps < 3; ++ps) {
       g.a[0].src = ps == 0 ? reinterpret_cast<const cpx<float>*>(in) : nullptr;
       const int kind = ps == 0 ? K_FFT2_XY_FWD : ps == 1 ? K_FFT2_YZ_MID : write ? K_FFT2_XY_INV_UPDATE
                                                                                   : K_FFT2_XY_INV_SUMS;
-      cudaError_t e = launch(lat, kind, [&] { return launch_fft2_group_pass(ps, g, lat->st); });
+      cudaError_t e = launch(lat, kind, [&] { return launch_fft2_group_pass(n, ps, g, lat->st); });
       if (e != cudaSuccess) return e;
     }
     lat->xfwd_valid = live;
@@ -1600,7 +1601,7 @@ static qf_status batch_issue_step(qf_batch* b, const std::vector<int>& run, cons
           const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
           fg.a[j] = fft_args<float>(M, M->psi(), true, chk[q], sq);
           fg.a[j].emit_next = 1;
-          nblk[q] = two ? fft2_final_blocks() : fft_final_blocks<float>(n);
+          nblk[q] = two ? fft2_final_blocks(n) : fft_final_blocks<float>(n);
           if (!M->xfwd_valid) {
             f0.a[f0.count] = fg.a[j];
             f0.a[f0.count].src = fg.a[j].psi;
@@ -1609,12 +1610,12 @@ static qf_status batch_issue_step(qf_batch* b, const std::vector<int>& run, cons
           M->xfwd_valid = true;
         }
         if (f0.count > 0) {
-          QF_BCUDA(b, two ? launch_fft2_group_pass(0, f0, st) : launch_fft_group_pass<float>(n, 0, f0, st));
+          QF_BCUDA(b, two ? launch_fft2_group_pass(n, 0, f0, st) : launch_fft_group_pass<float>(n, 0, f0, st));
           b->launches += 1;
         }
         for (int j = 0; j < cnt; ++j) fg.a[j].src = nullptr;
         for (int ps = 1; ps < (two ? 3 : kFftPasses); ++ps) {
-          QF_BCUDA(b, two ? launch_fft2_group_pass(ps, fg, st) : launch_fft_group_pass<float>(n, ps, fg, st));
+          QF_BCUDA(b, two ? launch_fft2_group_pass(n, ps, fg, st) : launch_fft_group_pass<float>(n, ps, fg, st));
           b->launches += 1;
         }
       }

@@ -77,11 +77,14 @@ def _symbol(kind, k, a, m):
     return math.sqrt(s2 + (a * m) ** 2) / a
 
 
+@pytest.mark.parametrize("n,nvec", [(256, (3, -5, 7)), (128, (5, 63, -64))])
 @pytest.mark.parametrize("two_pass", [True, False])
 @pytest.mark.parametrize("kind", [I.FFT_NAIVE, I.FFT_SYMANZIK, I.FFT_REL])
-def test_plane_wave_closed_form_at_n256(kind, two_pass):
-    n, a, m, v0 = 256, 0.05, 0.3, 0.7
-    nvec = (3, -5, 7)                       # momentum index per axis (x, y, z)
+def test_plane_wave_closed_form(kind, two_pass, n, nvec):
+    """psi = exp(i k.x) with V constant is an eigenvector of the step: one factor per step.
+    nvec is the momentum index per axis (x, y, z); at N = 128 it has the largest k_lo of
+    the split y transform and the Nyquist index in z."""
+    a, m, v0 = 12.8 / n, 0.3, 0.7
     k = [2 * math.pi * j / n for j in nvec]
     idx = np.arange(n)
     # psi[z, y, x] = exp(i (kx x + ky y + kz z)) on the lattice indices

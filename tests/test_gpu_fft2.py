@@ -1,6 +1,7 @@
-"""The two-pass FFT step (N = 256, complex FP32) against the oracle and the four-pass step.
+"""The two-pass FFT step (N = 128 and 256, complex FP32) against the oracle and the
+four-pass step.
 
-The two-pass form splits the y transform 16 x 16 between its passes and keeps the
+The two-pass form splits the y transform (N/16) x 16 between its passes and keeps the
 scratch field in a blocked layout; it must compute the same step as the four-pass form
 to FP32 rounding, match the FP64 oracle to the usual c64 tolerance, and run bitwise the
 same alone and inside a batch (both launch the same grouped kernels).
@@ -17,6 +18,12 @@ from paper_2211_10185_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 N, A = 256, 0.05
+SIZES = [128, 256]
+
+
+def _a(n):
+    # the same physical box at every size: a = 0.05 at N = 256
+    return A * N / n
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,56 +40,59 @@ def _rel(a, b):
     return np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel())
 
 
-def _potential(cplx):
-    v = I.cornell(N, A, 0.4, 0.2)
+def _potential(cplx, n=N):
+    v = I.cornell(n, _a(n), 0.4, 0.2)
     return v - 0.04j * np.abs(v) if cplx else v
 
 
-def _dtau(kind):
+def _dtau(kind, n=N):
     # a/4 for the relativistic term (the bench workload); the stable default otherwise
-    return A / 4 if kind == I.FFT_REL else None
+    return _a(n) / 4 if kind == I.FFT_REL else None
 
 
 def _lat(kind, v, psi0, two_pass=True, m=0.3):
     from paper_2211_10185_gb300.lattice import Lattice
 
-    lat = Lattice(N, A, precision="c64")
+    n = v.shape[0]
+    lat = Lattice(n, _a(n), precision="c64")
     lat.set_potential(v)
-    lat.set_kinetic(kind, m, _dtau(kind))
+    lat.set_kinetic(kind, m, _dtau(kind, n))
     lat.set_wavefunction(psi0)
     lat.use_two_pass_fft(two_pass)
     return lat
 
 
+@pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("kind", [I.FFT_NAIVE, I.FFT_SYMANZIK, I.FFT_REL])
-def test_two_pass_step_matches_oracle_every_site(kind, cplx):
-    v = _potential(cplx)
-    psi0 = I.gaussian_field(N, 11 + kind)
+def test_two_pass_step_matches_oracle_every_site(kind, cplx, n):
+    v = _potential(cplx, n)
+    psi0 = I.gaussian_field(n, 11 + kind)
     gpu = _lat(kind, v, psi0)
     assert gpu.info()["fft_passes"] == 2
-    ref = O.Lattice(N, A)
+    ref = O.Lattice(n, _a(n))
     if cplx:
         ref.set_potential(v.real, v.imag)
     else:
         ref.set_potential(v)
-    ref.set_kinetic(kind, 0.3, _dtau(kind))
+    ref.set_kinetic(kind, 0.3, _dtau(kind, n))
     ref.set_wavefunction(psi0)
     # step 0 with a check (sums), step 1 plain with the renormalisation (the first step
     # starts from the natural-order pass, the second from the emitted scratch field)
     for _ in range(2):
         ref.step_n(1, check_every=2)
         gpu.step_n(1, tol=0.0, check_every=2)
-    assert_field_close(gpu.get_wavefunction(), ref.psi, 2e-6 * (1 + math.log2(N)))
+    assert_field_close(gpu.get_wavefunction(), ref.psi, 2e-6 * (1 + math.log2(n)), what=f"N={n}")
     e_ref, e_gpu = ref.energies(), gpu.energies()
     assert abs(e_gpu["e"] - e_ref["e"]) < 1e-5 * abs(e_ref["e"])
     assert e_gpu["norm"] == pytest.approx(e_ref["norm"], rel=1e-5)
 
 
+@pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("kind", [I.FFT_SYMANZIK, I.FFT_REL])
-def test_two_pass_and_four_pass_agree_over_many_steps(kind):
-    v = _potential(True)
-    psi0 = I.gaussian_field(N, 3)
+def test_two_pass_and_four_pass_agree_over_many_steps(kind, n):
+    v = _potential(True, n)
+    psi0 = I.gaussian_field(n, 3)
     two = _lat(kind, v, psi0, True)
     four = _lat(kind, v, psi0, False)
     assert four.info()["fft_passes"] == 4
@@ -100,9 +110,10 @@ def test_two_pass_and_four_pass_agree_over_many_steps(kind):
     assert two.info()["launches"] < four.info()["launches"]
 
 
-def test_switching_forms_mid_run_keeps_the_step():
-    v = _potential(False)
-    psi0 = I.gaussian_field(N, 5)
+@pytest.mark.parametrize("n", SIZES)
+def test_switching_forms_mid_run_keeps_the_step(n):
+    v = _potential(False, n)
+    psi0 = I.gaussian_field(n, 5)
     ref = _lat(I.FFT_REL, v, psi0, True)
     mix = _lat(I.FFT_REL, v, psi0, True)
     ref.step_n(6, tol=0.0, check_every=3)
@@ -115,13 +126,15 @@ def test_switching_forms_mid_run_keeps_the_step():
 
 
 def test_two_pass_batch_members_match_alone_bitwise():
+    """Members of both two-pass sizes in one batch (each size launches as its own group)."""
     from paper_2211_10185_gb300.serve import Batch
 
-    specs = [(I.FFT_REL, False, 1), (I.FFT_NAIVE, True, 2), (I.FFT_SYMANZIK, False, 3)]
+    specs = [(I.FFT_REL, False, 1, 256), (I.FFT_NAIVE, True, 2, 128), (I.FFT_SYMANZIK, False, 3, 256),
+             (I.FFT_REL, True, 4, 128)]
     alone, mixed = [], []
-    for kind, cplx, seed in specs:
-        v = _potential(cplx)
-        psi0 = I.gaussian_field(N, seed)
+    for kind, cplx, seed, n in specs:
+        v = _potential(cplx, n)
+        psi0 = I.gaussian_field(n, seed)
         alone.append(_lat(kind, v, psi0))
         mixed.append(_lat(kind, v, psi0))
     for lat in alone:

@@ -60,9 +60,12 @@ FIELD_TOL = {"c128": 1e-12, "c64": 2e-6}
 E_TOL = {"c128": 1e-10, "c64": 1e-5}
 
 
-def _one_step(n, kind, prec, a=0.2, m=1.3, v=None):
+def _one_step(n, kind, prec, a=0.2, m=1.3, v=None, two_pass=True):
     v = I.cornell(n, a, 0.5, 0.2) if v is None else v
     ref, gpu = _pair(n, a, kind, m, prec, v, seed=n)
+    if not two_pass:
+        gpu.use_two_pass_fft(False)
+        assert gpu.info()["fft_passes"] == 4
     ref.step_n(1, check_every=1)
     st, done = gpu.step_n(1, check_every=1)
     assert done == 1
@@ -90,6 +93,13 @@ def test_one_step_matches_oracle_n384(prec, kind, cplx):
     if cplx:
         v = v - 0.05j * np.abs(v)
     _one_step(n, kind, prec, a=a, m=0.7, v=v)
+
+
+@pytest.mark.parametrize("kind", [O.FFT_NAIVE, O.FFT_SYMANZIK, O.FFT_REL])
+def test_one_step_four_pass_n128_matches_oracle(kind):
+    """N = 128 complex-FP32 lattices step in two passes by default; the four-pass plan
+    (16 x 8 Stockham stages, also the FP64 form) stays selectable and is checked too."""
+    _one_step(128, kind, "c64", two_pass=False)
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
@@ -358,6 +368,8 @@ def test_fft_tile_variants_agree_bitwise_and_match_oracle(n):
         for variant in (0, 1):
             assert lib.qf_set_fft_tiles(n, variant) == Q.QF_OK
             ref, gpu = _pair(n, a, O.FFT_REL, m, "c64", v, seed=n + 5)
+            gpu.use_two_pass_fft(False)  # the tile variants are the four-pass kernels
+            assert gpu.info()["fft_passes"] == 4
             ref.step_n(3, check_every=2)
             gpu.step_n(3, check_every=2)
             got = gpu.get_wavefunction()
