@@ -104,8 +104,8 @@ typedef struct {
   size_t workspace_bytes;
   int64_t launches;   /* kernels this handle has launched so far                     */
   int temporal_block; /* FDTD steps fused per pass (qf_set_temporal_blocking)         */
-  int fft_passes;     /* HBM passes of a steady-state FFT step: 2 (N = 256 complex
-                         FP32, qf_use_two_pass_fft) or 4; 0 for the FDTD term         */
+  int fft_passes;     /* HBM passes of a steady-state FFT step: 2 (N = 128 or 256
+                         complex FP32, qf_use_two_pass_fft) or 4; 0 for FDTD          */
   int64_t field_exp2; /* the stored live field is 2^field_exp2 times the one
                          qf_get_wavefunction returns (see qf_step_n)                  */
 } qf_info;
@@ -219,16 +219,18 @@ qf_status qf_momentum_distribution(qf_lattice* lat, int slot, double* p, double*
 qf_status qf_use_graphs(qf_lattice* lat, int enable);
 
 /* Form of the FFT step (no counterpart in the paper; the paper's FFTW transforms are
- * replaced by GPU passes).  enable != 0, the default: complex-FP32 lattices with N = 256
- * run a steady-state step in two passes over HBM (the y transform split 16 x 16
- * four-step fashion between the two passes; the scratch field holds a blocked layout),
- * other lattices in four.  enable == 0 selects the four-pass form for N = 256 too.  Both
+ * replaced by GPU passes).  enable != 0, the default: complex-FP32 lattices with N = 128
+ * or 256 run a steady-state step in two passes over HBM (the y transform split
+ * (N/16) x 16 four-step fashion between the two passes; the scratch field holds a
+ * blocked layout), other lattices in four.  enable == 0 selects the four-pass form for
+ * N = 128 and 256 too.  Both
  * compute the same step to rounding; switching discards the scratch field's contents and
  * any captured graphs. */
 qf_status qf_use_two_pass_fft(qf_lattice* lat, int enable);
 
 /* Tile choice of the complex-FP32 four-pass FFT kernels for lattice size n (no
- * counterpart in the paper; every size but the two-pass N = 256 step).  Variant 0 tiles
+ * counterpart in the paper; every size, N = 128 and 256 when their four-pass form is
+ * selected).  Variant 0 tiles
  * about 4096 elements per block with up to 16 contiguous columns; variant 1 half of both
  * (more, smaller blocks per SM).  Both compute the same transforms (the fields agree
  * bitwise; reductions may differ in their last bits).  variant -1, the default, lets the

@@ -147,7 +147,7 @@ class Lattice:
         _check(self.h, self.lib.qf_use_graphs(self.h, int(bool(enable))), "qf_use_graphs")
 
     def use_two_pass_fft(self, enable: bool = True):
-        """Two HBM passes per FFT step for N = 256 complex FP32 (default) or four."""
+        """Two HBM passes per FFT step for N = 128 and 256 complex FP32 (default) or four."""
         _check(self.h, self.lib.qf_use_two_pass_fft(self.h, int(bool(enable))), "qf_use_two_pass_fft")
 
     def set_temporal_blocking(self, k: int):
