@@ -124,6 +124,16 @@ __device__ __forceinline__ void f2_prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Programmatic dependent launch: a pass launched with programmatic stream serialization
+// may start while the kernel before it in the stream is still running.  Every pass
+// issues only L2 prefetch hints before this point and reads nothing else, then waits for
+// the previous kernel to complete with its writes visible, and lets the next pass launch
+// once all of its own blocks are running.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void f2_grid_dependency() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // Offset of line `line` of pass-A/C block blk in a natural-order field: the block holds
 // y_lo = blk mod L of the z-planes 2 (blk / L) and 2 (blk / L) + 1; line = 2 y_hi + dz.
 template <int N>
@@ -209,6 +219,7 @@ __global__ void __launch_bounds__(F2G<N>::AC_THREADS, F2G<N>::AC_PER_SM)
   cpx<float>* tw_s = reinterpret_cast<cpx<float>*>(f2_smem);
   cpx<float>* tile = reinterpret_cast<cpx<float>*>(f2_smem + G::TWB);
   const F2Roles<N> q(blockIdx.x);
+  f2_grid_dependency();
   const cpx<float>* __restrict__ src = a.src ? a.src : a.psi;
   cpx<float> v[16];
 #pragma unroll
@@ -273,6 +284,7 @@ __global__ void __launch_bounds__(F2G<N>::B_THREADS, F2G<N>::B_PER_SM)
     if (nb < (int)gridDim.x && tid < 4)
       f2_prefetch_l2(a.data + (long long)nb * G::B_ELEMS + tid * (G::B_ELEMS / 4), G::B_ELEMS / 4 * 8);
   }
+  f2_grid_dependency();
   cpx<float> u[16];
 #pragma unroll
   for (int q = 0; q < G::PAIRS; ++q)
@@ -443,6 +455,7 @@ __global__ void __launch_bounds__(F2G<N>::AC_THREADS, F2G<N>::AC_PER_SM)
   // site; and a persistent form with one block per SM that stages the next item's sectors
   // with cp.async while computing, 16 warps per SM being too few for the transforms.)
   f2_prefetch_psi_v<N, VREAL>(a, blockIdx.x);
+  f2_grid_dependency();
   for (int i = threadIdx.x; i < G::TW; i += G::AC_THREADS) tw_s[i] = a.twiddle[i];
   cpx<float> u[16];
 #pragma unroll

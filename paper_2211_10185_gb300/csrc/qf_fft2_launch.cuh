@@ -32,6 +32,30 @@ static bool f2_set_attrs() {
   return true;
 }
 
+// Launch with or without programmatic stream serialization (the kernels wait for the
+// previous kernel before their first dependent read: f2_grid_dependency).
+template <typename... KArgs, typename... Args>
+static cudaError_t f2_launch(void (*kern)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t st, bool pdl,
+                             Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Steady-state passes B and C start during the previous pass's last wave at N = 256
+// (measured 218 -> 211 us per B + C in a CUDA graph); at N = 128 both grids fit one
+// wave and early blocks only take slots (26.0 -> 27.0 us), so it stays off there.
+template <int N>
+constexpr bool kF2Pdl = N == 256;
+
 // pass 0: natural field -> S (members' src); 1: S in place; 2: S -> update / sums (+ the
 // next step's pass 0 when emit_next).  The pass-2 variant follows member 0.  Energy of a
 // field that is not stepped: 3 = pass 0 with <v|v>, <v|V v> sums, 4 = forward half of
@@ -45,13 +69,15 @@ cudaError_t launch_fft2_pass_n(int pass, const FftGroup<float>& g, cudaStream_t 
   const dim3 grid_b(G::B_BLOCKS, g.count), grid_ac(G::AC_BLOCKS, g.count);
   const bool vreal = g.a[0].v_real != 0, sums = g.a[0].reduce != 0, write = g.a[0].write_psi != 0;
   const bool next = write && g.a[0].emit_next != 0;
+  cudaError_t e = cudaSuccess;
   switch (pass) {
     case 0: fft2_a_kernel<N, false><<<grid_ac, G::AC_THREADS, G::SMEM_AC, st>>>(g); break;
-    case 1: fft2_b_kernel<N, false><<<grid_b, G::B_THREADS, G::SMEM_B, st>>>(g, 0); break;
+    case 1: e = f2_launch(fft2_b_kernel<N, false>, grid_b, G::B_THREADS, G::SMEM_B, st, kF2Pdl<N>, g, 0); break;
     case 3: fft2_a_kernel<N, true><<<grid_ac, G::AC_THREADS, G::SMEM_AC, st>>>(g); break;
     case 4: fft2_b_kernel<N, true><<<grid_b, G::B_THREADS, G::SMEM_B, st>>>(g, G::AC_BLOCKS); break;
     case 2:
-#define F2_C(OP, VR, NX) fft2_c_kernel<N, OP, VR, NX><<<grid_ac, G::AC_THREADS, G::SMEM_AC, st>>>(g)
+#define F2_C(OP, VR, NX) \
+  e = f2_launch(fft2_c_kernel<N, OP, VR, NX>, grid_ac, G::AC_THREADS, G::SMEM_AC, st, kF2Pdl<N>, g)
       if (!write) {
         if (vreal) F2_C(OP_SUMS, true, false);
         else F2_C(OP_SUMS, false, false);
@@ -66,7 +92,7 @@ cudaError_t launch_fft2_pass_n(int pass, const FftGroup<float>& g, cudaStream_t 
       break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace qf
