@@ -28,6 +28,7 @@ int fft2_final_blocks(int n);
 int fft2_measure_blocks(int n);
 cudaError_t launch_fft2_group_pass(int n, int pass, const FftGroup<float>& g, cudaStream_t st);
 cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st);
+cudaError_t launch_stencil_tb_group(const StencilTbGroup& g, cudaStream_t st);
 cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st);
 template <typename R>
 cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st);
@@ -1456,6 +1457,7 @@ struct qf_batch {
     int64_t max_steps, steps_done;
     double tol_abs, tol_rel;
     int status;  // QF_BATCH_RUNNING, QF_OK (converged), QF_ENOTCONV (step cap reached)
+    bool mid_pair;  // advanced two steps by the previous batch step's launch: sits this one out
   };
   cudaStream_t st = nullptr;
   std::vector<Member> m;
@@ -1513,7 +1515,7 @@ extern "C" qf_status qf_batch_add(qf_batch* b, qf_lattice* lat, int64_t max_step
     if (x.lat == lat) return bfail(b, QF_EINVAL, "lattice already in the batch");
   // work of the lattice's own stream must be visible to the batch stream
   QF_BCUDA(b, cudaStreamSynchronize(lat->st));
-  b->m.push_back({lat, max_steps, 0, tol_abs, tol_rel, QF_BATCH_RUNNING});
+  b->m.push_back({lat, max_steps, 0, tol_abs, tol_rel, QF_BATCH_RUNNING, false});
   b->drop_graphs();
   return QF_OK;
 }
@@ -1540,11 +1542,20 @@ extern "C" qf_status qf_batch_members(qf_batch* b, int* count, int* status, int6
   return QF_OK;
 }
 
+// Whether a batch member's FDTD steps may run two per launch (the conditions of fuse_pair
+// that do not depend on the step's place in the check and snapshot schedule).
+static bool pairable(const qf_lattice* L) {
+  return L->kinetic == QF_KIN_FDTD && L->c64() && L->tblock >= 2 && L->clean && L->tbmap_ok && L->kcur == 0;
+}
+
 // Issues the launches of one batch step for the running members `run` (check flags chk);
-// nblk receives each member's partial rows.  Host state is touched only where later
+// nblk receives each member's partial rows.  pm (optional, per member of run) selects the
+// FDTD members' form: 0 one step, 1 two steps in one pass (psi_{t+2} into the scratch
+// field; the caller skips the member in the next batch step), 2 nothing (the second step
+// of a pair issued in the previous batch step).  Host state is touched only where later
 // launches depend on it (xfwd_valid of FFT members).
 static qf_status batch_issue_step(qf_batch* b, const std::vector<int>& run, const std::vector<char>& chk,
-                                  std::vector<int>& nblk, cudaStream_t st) {
+                                  std::vector<int>& nblk, cudaStream_t st, const std::vector<char>* pm = nullptr) {
   const int R = (int)run.size();
   // group FP32 members by (N, kinetic family, real V, check); FP64 members run alone
   std::vector<char> done(R, 0);
@@ -1576,19 +1587,37 @@ static qf_status batch_issue_step(qf_batch* b, const std::vector<int>& run, cons
     for (size_t off = 0; off < g.size(); off += kGroupMax) {
       const int cnt = (int)std::min<size_t>(kGroupMax, g.size() - off);
       if (fdtd) {
+        // single steps in one launch, pairs in one launch per kind of potential
         StencilTmaGroup<float> sg;
+        StencilTbGroup tg[2];
+        sg.count = 0;
+        tg[0].count = tg[1].count = 0;
         for (int j = 0; j < cnt; ++j) {
           const int q = g[off + j];
           qf_lattice* M = b->m[run[q]].lat;
-          const int zc = tuned_zchunk<float>(M);
+          const int mode = pm ? (*pm)[q] : 0;
           const double* sq = M->pending_scale ? &M->sc()->scale[1] : &M->sc()->scale[2];
-          if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, j == 0, zc))
+          if (mode == 2) continue;
+          if (mode == 1) {
+            StencilTbGroup& t = tg[M->v_real ? 1 : 0];
+            tb_args(M, sq, tuned_tb_zchunk(M), t.m[t.count++]);
+            continue;
+          }
+          const int zc = tuned_zchunk<float>(M);
+          if (!stencil_group_member<float>(M, M->psi(), M->tmp(), true, chk[q], sq, sg, sg.count == 0, zc))
             return bfail(b, QF_ECUDA, "tensor map encoding failed");
           // one error flag per launch: the first member's
           nblk[q] = stencil_blocks<float>(M->d.n, zc);
         }
-        QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
-        b->launches += 1;
+        if (sg.count > 0) {
+          QF_BCUDA(b, launch_stencil_tma<float>(sg, st));
+          b->launches += 1;
+        }
+        for (auto& t : tg)
+          if (t.count > 0) {
+            QF_BCUDA(b, launch_stencil_tb_group(t, st));
+            b->launches += 1;
+          }
       } else {
         const bool two = uses_fft2(L);
         tune_fft_tiles(L);  // (runs once per size; never inside a capture)
@@ -1627,8 +1656,11 @@ static qf_status batch_issue_step(qf_batch* b, const std::vector<int>& run, cons
 // The check_every - 1 steps after a check that every running member took together
 // issue the same launches each time the batch holds the same members in the same buffer
 // state, so they are captured once into a CUDA graph (keyed by members, FDTD buffer
-// parity and first-pass state) and replayed; the host bookkeeping of those steps follows
-// the replay.  Returns QF_OK with *used = false when the interval does not qualify.
+// parity, first-pass state and FDTD pairing) and replayed; the host bookkeeping of those
+// steps follows the replay.  FDTD members that qualify (pairable) take the interval's
+// steps two per launch from its first step on, the last one alone when the count is odd,
+// as a lone lattice does.  Returns QF_OK with *used = false when the interval does not
+// qualify.
 static qf_status batch_chunk_graph(qf_batch* b, const std::vector<int>& run, int64_t steps_left, int check_every,
                                    int snap_every, cudaStream_t st, bool* used) {
   *used = false;
@@ -1644,7 +1676,14 @@ static qf_status batch_chunk_graph(qf_batch* b, const std::vector<int>& run, int
     if (!L->pending_scale || L->prof || L->step % check_every != 1 || mb.steps_done + k > mb.max_steps)
       return QF_OK;
     key.push_back(reinterpret_cast<uintptr_t>(L));
-    key.push_back((uintptr_t)((L->live & 1) | (L->xfwd_valid ? 2 : 0) | (uses_fft2(L) ? 4 : 0)));
+    key.push_back((uintptr_t)((L->live & 1) | (L->xfwd_valid ? 2 : 0) | (uses_fft2(L) ? 4 : 0) |
+                              (pairable(L) ? 8 : 0)));
+  }
+  std::vector<char> pair(run.size(), 0);
+  for (size_t q = 0; q < run.size(); ++q) {
+    qf_lattice* L = b->m[run[q]].lat;
+    pair[q] = pairable(L) ? 1 : 0;
+    if (pair[q]) tuned_tb_zchunk(L);  // timed outside the capture
   }
   const qf_batch::BGraph* hit = nullptr;
   for (auto& g : b->graphs)
@@ -1662,15 +1701,17 @@ static qf_status batch_chunk_graph(qf_batch* b, const std::vector<int>& run, int
       saved.push_back({L->live, L->clean, L->xfwd_valid, L->pending_scale, L->launches});
     }
     const int64_t l0 = b->launches;
-    std::vector<char> nochk(run.size(), 0);
+    std::vector<char> nochk(run.size(), 0), pm(run.size(), 0);
     std::vector<int> nblk(run.size(), 0);
     cudaGraph_t graph = nullptr;
     QF_BCUDA(b, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     qf_status s = QF_OK;
     for (int j = 0; j < k && s == QF_OK; ++j) {
-      s = batch_issue_step(b, run, nochk, nblk, st);
-      for (int i : run) {
-        qf_lattice* L = b->m[i].lat;
+      for (size_t q = 0; q < run.size(); ++q) pm[q] = !pair[q] ? 0 : (j & 1) ? 2 : (j + 1 < k) ? 1 : 0;
+      s = batch_issue_step(b, run, nochk, nblk, st, &pm);
+      for (size_t q = 0; q < run.size(); ++q) {
+        qf_lattice* L = b->m[run[q]].lat;
+        if (pm[q] == 2) continue;
         L->pending_scale = false;
         if (L->kinetic == QF_KIN_FDTD) L->live = 1 - L->live;
       }
@@ -1708,14 +1749,15 @@ static qf_status batch_chunk_graph(qf_batch* b, const std::vector<int>& run, int
   b->launches += hit->launches;
   b->graph_replays += 1;
   // host bookkeeping of the k steps: the first renormalises, the others scale by 2^kcur
-  for (int i : run) {
-    auto& mb = b->m[i];
+  for (size_t q = 0; q < run.size(); ++q) {
+    auto& mb = b->m[run[q]];
     qf_lattice* L = mb.lat;
     L->K += (long long)k * L->kcur + L->jcur - L->K_check;
     L->renorm_step = L->step;
     L->pending_scale = false;
     if (L->kinetic == QF_KIN_FDTD) {
-      L->live ^= (k & 1);
+      const int swaps = pair[q] ? k / 2 + (k & 1) : k;  // one buffer swap per launch
+      L->live ^= (swaps & 1);
       L->clean = true;
     }
     for (int j = 0; j < k; ++j) {
@@ -1753,15 +1795,26 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
   std::vector<double> tau_t;
   std::vector<int64_t> t_of;
   std::vector<double> e3;
+  std::vector<char> pm;
   for (int64_t s = 0; s < steps; ++s) {
     run.clear();
+    bool any = false;
     for (int i = 0; i < (int)b->m.size(); ++i)
       if (b->m[i].status == QF_BATCH_RUNNING) {
-        if (b->m[i].steps_done >= b->m[i].max_steps) b->m[i].status = QF_ENOTCONV;
-        else run.push_back(i);
+        if (b->m[i].mid_pair) {
+          b->m[i].mid_pair = false;  // this step was the second of its pair
+          any = true;
+        } else if (b->m[i].steps_done >= b->m[i].max_steps) {
+          b->m[i].status = QF_ENOTCONV;
+        } else {
+          run.push_back(i);
+        }
       }
-    if (run.empty()) break;
-    if (check_every > 0) {
+    if (run.empty()) {
+      if (any) continue;
+      break;
+    }
+    if (check_every > 0 && !any) {  // (not while a member is between the steps of a pair)
       bool used = false;
       qf_status gs = batch_chunk_graph(b, run, steps - s, check_every, snap_every, st, &used);
       if (gs != QF_OK) return gs;
@@ -1775,21 +1828,33 @@ extern "C" qf_status qf_batch_step(qf_batch* b, int64_t steps, int check_every, 
     nblk.assign(R, 0);
     tau_t.assign(R, 0);
     t_of.assign(R, 0);
+    pm.assign(R, 0);
     for (int k = 0; k < R; ++k) {
-      qf_lattice* L = b->m[run[k]].lat;
+      const auto& mb = b->m[run[k]];
+      qf_lattice* L = mb.lat;
       t_of[k] = L->step;
       tau_t[k] = L->tau;
       chk[k] = check_every > 0 && L->step % check_every == 0;
+      // two FDTD steps in one launch where a lone lattice would pair them too
+      if (s + 2 <= steps && mb.steps_done + 2 <= mb.max_steps && fuse_pair(L, L->step, check_every, snap_every))
+        pm[k] = 1;
     }
-    qf_status is = batch_issue_step(b, run, chk, nblk, st);
+    qf_status is = batch_issue_step(b, run, chk, nblk, st, &pm);
     if (is != QF_OK) return is;
     // per-member bookkeeping, identical to qf_step_n
     bool any_check = false;
     for (int k = 0; k < R; ++k) {
-      qf_lattice* L = b->m[run[k]].lat;
+      auto& mb = b->m[run[k]];
+      qf_lattice* L = mb.lat;
+      if (pm[k]) {
+        QF_BCUDA(b, after_pair(L, snap_every, st));
+        mb.steps_done += 2;
+        mb.mid_pair = true;
+        continue;
+      }
       QF_BCUDA(b, after_step(L, chk[k], nblk[k], snap_every, st));
       if (chk[k]) b->launches += 1;
-      b->m[run[k]].steps_done += 1;
+      mb.steps_done += 1;
       any_check = any_check || chk[k];
     }
     if (any_check) {

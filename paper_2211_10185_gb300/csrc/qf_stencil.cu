@@ -61,6 +61,32 @@ cudaError_t launch_stencil_tb(const StencilTbArgs& g, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Two steps for every member of g (any sizes, one kind of potential) in one launch.
+cudaError_t launch_stencil_tb_group(const StencilTbGroup& g, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(stencil_tb_group_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stencil_tb_smem());
+    cudaFuncSetAttribute(stencil_tb_group_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stencil_tb_smem());
+    attr = true;
+  }
+  if (g.count < 1 || g.count > kGroupMax) return cudaErrorInvalidValue;
+  StencilTbGroup gl = g;
+  long long total = 0;
+  for (int i = 0; i < g.count; ++i) {
+    const StencilTbArgs& m = g.m[i];
+    if (m.n < 2 || m.nzb < 1 || m.nzb > m.n || m.v_real != g.m[0].v_real) return cudaErrorInvalidValue;
+    gl.start[i] = (int)total;
+    total += stencil_tb_member_blocks(m.n, m.nzb);
+  }
+  if (total > (1LL << 30)) return cudaErrorInvalidValue;
+  gl.start[g.count] = (int)total;
+  if (g.m[0].v_real) stencil_tb_group_kernel<true><<<(unsigned)total, TB_THREADS, stencil_tb_smem(), st>>>(gl);
+  else stencil_tb_group_kernel<false><<<(unsigned)total, TB_THREADS, stencil_tb_smem(), st>>>(gl);
+  return cudaGetLastError();
+}
+
 // Tensor map of an N^3 complex field for plane boxes of box_w x box_h 8-byte elements
 // (one complex FP32 or one FP64 component).
 static bool encode_field_map(CUtensorMap* map, void* field, int n, bool c64, unsigned box_w, unsigned box_h) {

@@ -21,6 +21,10 @@
 //
 // Every wait is bounded as in the single-step kernel: on time-out the block records a
 // flag, drains its own copies with a bounded wait and returns.
+//
+// A group launch (stencil_tb_group_kernel) steps several lattices of any sizes at once:
+// a one-dimensional grid whose blocks are numbered member by member from a block table,
+// each block running the same body on its member's tile and z-chunk.
 #pragma once
 #include "qf_stencil_tma.cuh"
 
@@ -69,9 +73,24 @@ __device__ __forceinline__ cpx<float> tb_v(const StencilTbArgs& g, long long pla
   else return (reinterpret_cast<const cpx<float>*>(g.v) + plane_off)[off];
 }
 
-// VREAL: the potential is real (g.v holds floats)
+// Members of a group launch: blocks of member i are start[i] .. start[i+1] - 1 (the
+// launcher fills start), each member (n/32)^2 nzb blocks.  All members have the same kind
+// of potential (v_real).
+struct StencilTbGroup {
+  StencilTbArgs m[kGroupMax];
+  int start[kGroupMax + 1];
+  int count;
+};
+
+__host__ __device__ inline int stencil_tb_member_blocks(int n, int nzb) {
+  return ((n + TB_X - 1) / TB_X) * ((n + TB_Y - 1) / TB_Y) * nzb;
+}
+
+// The two steps for column tile (bx, by) and z-chunk bz of the lattice in g.  VREAL: the
+// potential is real (g.v holds floats).  g must live in kernel parameter space (its
+// tensor map is read by the copies).
 template <bool VREAL>
-__global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_constant__ StencilTbArgs g) {
+__device__ __forceinline__ void stencil_tb_body(const StencilTbArgs& g, int bx, int by, int bz) {
   extern __shared__ __align__(128) unsigned long long tb_dyn[];
   cpx<float>* l0 = reinterpret_cast<cpx<float>*>(tb_dyn);
   cpx<float>* l1 = l0 + TB_D0 * TB_L0_WORDS;
@@ -79,8 +98,8 @@ __global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_
   const int n = g.n;
   const long long plane_sites = (long long)n * n;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int x0 = blockIdx.x * TB_X, y0 = blockIdx.y * TB_Y;
-  const int z0 = (int)((long long)blockIdx.z * n / g.nzb), z1 = (int)((long long)(blockIdx.z + 1) * n / g.nzb);
+  const int x0 = bx * TB_X, y0 = by * TB_Y;
+  const int z0 = (int)((long long)bz * n / g.nzb), z1 = (int)((long long)(bz + 1) * n / g.nzb);
   const int pbase = z0 - 2, last0 = z1 + 1;  // level-0 planes z0-2 .. z1+1
   const float hd = g.half_dtau, kd = g.kd;
   const float sc1 = (float)*g.scale;
@@ -226,6 +245,29 @@ __global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_
       mbar_wait_bounded(&bars[u % TB_D0], (unsigned)((u / TB_D0) & 1));
     }
   }
+}
+
+template <bool VREAL>
+__global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_kernel(const __grid_constant__ StencilTbArgs g) {
+  stencil_tb_body<VREAL>(g, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <bool VREAL>
+__global__ void __launch_bounds__(TB_THREADS, 2) stencil_tb_group_kernel(const __grid_constant__ StencilTbGroup gr) {
+  // member of this block: the last i with start[i] <= block
+  int member = 0;
+  {
+    int hi = gr.count - 1;
+    while (member < hi) {
+      const int mid = (member + hi + 1) >> 1;
+      if (gr.start[mid] <= (int)blockIdx.x) member = mid;
+      else hi = mid - 1;
+    }
+  }
+  const StencilTbArgs& g = gr.m[member];
+  const int nbx = (g.n + TB_X - 1) / TB_X, nby = (g.n + TB_Y - 1) / TB_Y;
+  const int local = (int)blockIdx.x - gr.start[member];
+  stencil_tb_body<VREAL>(g, local % nbx, (local / nbx) % nby, local / (nbx * nby));
 }
 
 }  // namespace qf
