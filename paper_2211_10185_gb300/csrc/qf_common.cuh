@@ -161,6 +161,11 @@ struct Acc<double> {
   double v = 0.0;
   __device__ __forceinline__ void add(double x) { v += x; }
   __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  // a b + c d
+  __device__ __forceinline__ void add_dot2(double a, double b, double c, double d) {
+    v = fma(a, b, v);
+    v = fma(c, d, v);
+  }
   __device__ __forceinline__ double value() const { return v; }
 };
 template <>
@@ -178,6 +183,10 @@ struct Acc<float> {
     const float e = __fmaf_rn(a, b, -p);
     add(p);
     lo = __fadd_rn(lo, e);
+  }
+  // a b + c d formed in FP32 (within 2^-24 of its terms), then added exactly
+  __device__ __forceinline__ void add_dot2(float a, float b, float c, float d) {
+    add(__fmaf_rn(a, b, __fmul_rn(c, d)));
   }
   __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };

@@ -88,13 +88,10 @@ __global__ void __launch_bounds__(kFieldThreads) dots_kernel(Basis2<R> basis, co
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
       const cpx<R> u = basis.v[j][i];
-      acc[2 * j].add_prod(u.x, x.x);  // Re conj(u) w
-      acc[2 * j].add_prod(u.y, x.y);
-      acc[2 * j + 1].add_prod(u.x, x.y);  // Im conj(u) w
-      acc[2 * j + 1].add_prod(-u.y, x.x);
+      acc[2 * j].add_dot2(u.x, x.x, u.y, x.y);       // Re conj(u) w
+      acc[2 * j + 1].add_dot2(u.x, x.y, -u.y, x.x);  // Im conj(u) w
     }
-    acc[4].add_prod(x.x, x.x);
-    acc[4].add_prod(x.y, x.y);
+    acc[4].add_dot2(x.x, x.x, x.y, x.y);
   }
   double s[kNumSums];
 #pragma unroll
@@ -186,13 +183,10 @@ __global__ void __launch_bounds__(kFieldThreads) axpy_dots_kernel(cpx<R>* w, con
     w[i] = x;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      acc[2 * j].add_prod(u[j].x, x.x);
-      acc[2 * j].add_prod(u[j].y, x.y);
-      acc[2 * j + 1].add_prod(u[j].x, x.y);
-      acc[2 * j + 1].add_prod(-u[j].y, x.x);
+      acc[2 * j].add_dot2(u[j].x, x.x, u[j].y, x.y);
+      acc[2 * j + 1].add_dot2(u[j].x, x.y, -u[j].y, x.x);
     }
-    acc[4].add_prod(x.x, x.x);
-    acc[4].add_prod(x.y, x.y);
+    acc[4].add_dot2(x.x, x.x, x.y, x.y);
   }
   double s[kNumSums];
 #pragma unroll
@@ -236,7 +230,7 @@ cudaError_t launch_scale_copy(cpx<R>* dst, const cpx<R>* src, const double* s, l
 // other two axes flipped)) - (psi(r with axis k flipped) + psi(-r)))/4.  The grouping
 // makes mirror-image outputs bitwise equal (or exactly negated).
 // ------------------------------------------------------------------------------------
-template <typename R>
+template <typename R, bool IDX32>
 __global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restrict__ dst, const cpx<R>* __restrict__ src,
                                                                int n, int which, int axis, double* partials) {
   __shared__ double red_s[32 * kNumSums];
@@ -244,7 +238,17 @@ __global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restric
   const long long total = (long long)n * n * n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
-    const int ix = (int)(i % n), iy = (int)((i / n) % n), iz = (int)(i / ((long long)n * n));
+    int ix, iy, iz;
+    if constexpr (IDX32) {  // (32-bit divisions: several times cheaper than 64-bit ones)
+      const unsigned u = (unsigned)i, t = u / (unsigned)n;
+      ix = (int)(u - t * (unsigned)n);
+      iy = (int)(t % (unsigned)n);
+      iz = (int)(t / (unsigned)n);
+    } else {
+      ix = (int)(i % n);
+      iy = (int)((i / n) % n);
+      iz = (int)(i / ((long long)n * n));
+    }
     const int mx = ix == 0 ? 0 : n - ix, my = iy == 0 ? 0 : n - iy, mz = iz == 0 ? 0 : n - iz;
     auto at = [&](int x, int y, int z) { return src[((long long)z * n + y) * n + x]; };
     const cpx<R> p = src[i];
@@ -291,8 +295,7 @@ __global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restric
       }
     }
     dst[i] = o;
-    nrm.add_prod(o.x, o.x);
-    nrm.add_prod(o.y, o.y);
+    nrm.add_dot2(o.x, o.x, o.y, o.y);
   }
   double s[kNumSums] = {0, 0, 0, 0, nrm.value()};  // slot 4 = squared norm (as the dots)
   block_sum_store<kNumSums>(s, red_s, partials + (long long)blockIdx.x * kPartialStride);
@@ -301,7 +304,10 @@ __global__ void __launch_bounds__(kFieldThreads) parity_kernel(cpx<R>* __restric
 template <typename R>
 cudaError_t launch_parity(cpx<R>* dst, const cpx<R>* src, int n, int which, int axis, double* partials, int nblocks,
                           cudaStream_t st) {
-  parity_kernel<R><<<nblocks, kFieldThreads, 0, st>>>(dst, src, n, which, axis, partials);
+  if ((long long)n * n * n < (1LL << 31))
+    parity_kernel<R, true><<<nblocks, kFieldThreads, 0, st>>>(dst, src, n, which, axis, partials);
+  else
+    parity_kernel<R, false><<<nblocks, kFieldThreads, 0, st>>>(dst, src, n, which, axis, partials);
   return cudaGetLastError();
 }
 
