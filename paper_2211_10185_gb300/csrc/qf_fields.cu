@@ -9,17 +9,21 @@
 namespace qf {
 
 constexpr int kFieldThreads = 256;
+constexpr int kFieldUnroll = 4;  // independent sites per thread and round of the field loops
 int field_blocks() { return 152 * 4; }  // 4 blocks per SM of the 152-SM GB300
 
 // ------------------------------------------------------------------------------------
 // Finishing reduction of per-block partial sums
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ partials, int nblocks,
+constexpr int kFinishThreads = 256;  // one block (1024 threads measured slower: 17 vs 14 us)
+
+__global__ void __launch_bounds__(kFinishThreads) finish_kernel(const double* __restrict__ partials, int nblocks,
                                                      DevScalars* sc, int set_scale, int interval,
                                                      double dtau) {
   __shared__ double red_s[32 * kNumSums];
   __shared__ double tot[kNumSums];
   double s[kNumSums] = {0, 0, 0, 0, 0};
+#pragma unroll 4
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) s[i] += partials[(long long)b * kPartialStride + i];
@@ -65,7 +69,7 @@ __global__ void __launch_bounds__(256) finish_kernel(const double* __restrict__ 
 
 cudaError_t launch_finish(const double* partials, int nblocks, DevScalars* sc, int set_scale, cudaStream_t st,
                           int interval, double dtau) {
-  finish_kernel<<<1, 256, 0, st>>>(partials, nblocks, sc, set_scale, interval, dtau);
+  finish_kernel<<<1, kFinishThreads, 0, st>>>(partials, nblocks, sc, set_scale, interval, dtau);
   return cudaGetLastError();
 }
 
@@ -82,16 +86,34 @@ __global__ void __launch_bounds__(kFieldThreads) dots_kernel(Basis2<R> basis, co
                                                              long long n_sites, double* partials) {
   __shared__ double red_s[32 * kNumSums];
   Acc<R> acc[kNumSums];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_sites; i += stride) {
-    const cpx<R> x = w[i];
+  auto site = [&](const cpx<R>& x, const cpx<R>* u) {
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
-      const cpx<R> u = basis.v[j][i];
-      acc[2 * j].add_dot2(u.x, x.x, u.y, x.y);       // Re conj(u) w
-      acc[2 * j + 1].add_dot2(u.x, x.y, -u.y, x.x);  // Im conj(u) w
+      acc[2 * j].add_dot2(u[j].x, x.x, u[j].y, x.y);       // Re conj(u) w
+      acc[2 * j + 1].add_dot2(u[j].x, x.y, -u[j].y, x.x);  // Im conj(u) w
     }
     acc[4].add_dot2(x.x, x.x, x.y, x.y);
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // kFieldUnroll sites per round with all their loads issued first (the same site order
+  // as one site per round)
+  for (; i + (kFieldUnroll - 1) * stride < n_sites; i += kFieldUnroll * stride) {
+    cpx<R> x[kFieldUnroll], u[kFieldUnroll][NB > 0 ? NB : 1];
+#pragma unroll
+    for (int k = 0; k < kFieldUnroll; ++k) {
+      x[k] = w[i + k * stride];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) u[k][j] = basis.v[j][i + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < kFieldUnroll; ++k) site(x[k], u[k]);
+  }
+  for (; i < n_sites; i += stride) {
+    cpx<R> u[NB > 0 ? NB : 1];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) u[j] = basis.v[j][i];
+    site(w[i], u);
   }
   double s[kNumSums];
 #pragma unroll
@@ -110,11 +132,12 @@ cudaError_t launch_dots(const cpx<R>* const* basis, int nb, const cpx<R>* w, lon
 }
 
 // coef_out: [Re c0, Im c0, Re c1, Im c1, |w|^2, 1/|w|]
-__global__ void __launch_bounds__(256) finish_dots_kernel(const double* __restrict__ partials, int nblocks,
+__global__ void __launch_bounds__(kFinishThreads) finish_dots_kernel(const double* __restrict__ partials, int nblocks,
                                                           double* coef_out) {
   __shared__ double red_s[32 * kNumSums];
   __shared__ double tot[kNumSums];
   double s[kNumSums] = {0, 0, 0, 0, 0};
+#pragma unroll 4
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
 #pragma unroll
     for (int i = 0; i < kNumSums; ++i) s[i] += partials[(long long)b * kPartialStride + i];
@@ -128,7 +151,7 @@ __global__ void __launch_bounds__(256) finish_dots_kernel(const double* __restri
 
 cudaError_t launch_finish_dots(const double* partials, int nblocks, int nb, double* coef_out, cudaStream_t st) {
   (void)nb;
-  finish_dots_kernel<<<1, 256, 0, st>>>(partials, nblocks, coef_out);
+  finish_dots_kernel<<<1, kFinishThreads, 0, st>>>(partials, nblocks, coef_out);
   return cudaGetLastError();
 }
 
@@ -171,15 +194,10 @@ __global__ void __launch_bounds__(kFieldThreads) axpy_dots_kernel(cpx<R>* w, con
     ci[j] = coef[2 * j + 1];
   }
   Acc<R> acc[kNumSums];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_sites; i += stride) {
-    cpx<R> x = src[i];
-    cpx<R> u[NB > 0 ? NB : 1];
+  // w may be src (in place): each site is read, then written, by the same thread
+  auto site = [&](long long i, cpx<R> x, const cpx<R>* u) {
 #pragma unroll
-    for (int j = 0; j < NB; ++j) {
-      u[j] = basis.v[j][i];
-      x = sub_cmul<R>(x, cr[j], ci[j], u[j]);
-    }
+    for (int j = 0; j < NB; ++j) x = sub_cmul<R>(x, cr[j], ci[j], u[j]);
     w[i] = x;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
@@ -187,6 +205,25 @@ __global__ void __launch_bounds__(kFieldThreads) axpy_dots_kernel(cpx<R>* w, con
       acc[2 * j + 1].add_dot2(u[j].x, x.y, -u[j].y, x.x);
     }
     acc[4].add_dot2(x.x, x.x, x.y, x.y);
+  };
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kFieldUnroll - 1) * stride < n_sites; i += kFieldUnroll * stride) {
+    cpx<R> x[kFieldUnroll], u[kFieldUnroll][NB > 0 ? NB : 1];
+#pragma unroll
+    for (int k = 0; k < kFieldUnroll; ++k) {
+      x[k] = src[i + k * stride];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) u[k][j] = basis.v[j][i + k * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < kFieldUnroll; ++k) site(i + k * stride, x[k], u[k]);
+  }
+  for (; i < n_sites; i += stride) {
+    cpx<R> u[NB > 0 ? NB : 1];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) u[j] = basis.v[j][i];
+    site(i, src[i], u);
   }
   double s[kNumSums];
 #pragma unroll
@@ -212,7 +249,15 @@ __global__ void __launch_bounds__(kFieldThreads) scale_copy_kernel(cpx<R>* dst, 
                                                                    const double* __restrict__ s, long long n) {
   const R f = R(*s);
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + (kFieldUnroll - 1) * stride < n; i += kFieldUnroll * stride) {
+    cpx<R> x[kFieldUnroll];
+#pragma unroll
+    for (int k = 0; k < kFieldUnroll; ++k) x[k] = src[i + k * stride];
+#pragma unroll
+    for (int k = 0; k < kFieldUnroll; ++k) dst[i + k * stride] = mk<R>(x[k].x * f, x[k].y * f);
+  }
+  for (; i < n; i += stride) {
     const cpx<R> x = src[i];
     dst[i] = mk<R>(x.x * f, x.y * f);
   }

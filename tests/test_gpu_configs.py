@@ -149,7 +149,12 @@ def test_config2_cornell_n128_c64_c128_oracle_plateau_and_parity():
         energies at the snapshot record (FP32 1e-5, FP64 1e-10).
     (2) Both GPU paths run to convergence: their ground-state energies agree within 1e-5;
         the FP64 path's plateau (Sec. 4's saddle point) gives E_0 < E_1 < E_2 with
-        |E_i(tau_j) - E_i(tau_{j-1})| below 1e-5 |E_i|, and the kept states have the parity
+        |E_i(tau_j) - E_i(tau_{j-1})| below 1e-5 |E_i| for 1S and 1P.  2S is a true saddle:
+        E_2 falls by ~1e-4 per record while the states above it decay out, and rises once
+        its share of the snapshots (~2e-10 near tau = 40) reaches the FP64 rounding floor,
+        so the smallest difference is the slope times how near a record falls to the
+        turning point (2e-6 to 3e-5 relative over runs that differ only in rounding order);
+        it is bounded by 1e-4 |E_2|.  The kept states have the parity
         of 1S (even), 1P (odd) and 2S (even): projecting them leaves them unchanged.  The
         converged ground state is a fixed point of the step map, checked with the oracle's
         kinetic term.  (The FP32 path's E_1/E_2 plateau is limited here by FP32 noise: the
@@ -195,8 +200,8 @@ def test_config2_cornell_n128_c64_c128_oracle_plateau_and_parity():
     es = [p[1]["e"].real for p in pl]
     assert es[0] == pytest.approx(e128, rel=1e-10)
     assert es[0] < es[1] < es[2]
-    for i in range(3):
-        assert pl[i][1]["de"] < 1e-5 * abs(es[i]), (i, pl[i])
+    for i, bound in enumerate((1e-5, 1e-5, 1e-4)):
+        assert pl[i][1]["de"] < bound * abs(es[i]), (i, pl[i])
     # the kept states' parities (their admixture of the next states is ~1e-3 at the
     # plateau of E_1 and E_2, which the energies feel only squared)
     lat = lats["c128"]
