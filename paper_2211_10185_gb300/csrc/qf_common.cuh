@@ -191,9 +191,8 @@ struct Acc<float> {
   __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
-// The sums of a check: <psi|psi>, Re/Im <psi|H_K psi>, Re/Im <psi|V psi> (slots 0-4;
-// the finishing kernel adds slots 1 + 3 and 2 + 4).  Kernels that hold only some of the
-// parts at a site pass zeros for the others.
+// The five sums of a check: <psi|psi>, Re/Im <psi|H_K psi>, Re/Im <psi|V psi>.  Kernels
+// that hold only some of the parts at a site pass zeros for the others.
 template <typename R>
 struct CheckSums {
   Acc<R> n, kr, ki, vr, vi;
@@ -217,26 +216,28 @@ struct CheckSums {
   }
 };
 
-// Complex FP32 fields: the site's three values |psi|^2 and Re/Im conj(psi) (H_K psi +
-// V psi) are formed in FP32 (a few roundings, each within 2^-24 of the site's terms,
-// below the FP32 field's own rounding) and accumulated across sites in compensated
-// (FP64-equivalent) sums: three accumulators instead of eight exact products per site.
-// The kinetic and potential parts share slots 1 and 2; slots 3 and 4 stay zero.
+// Complex FP32 fields: the site's values |psi|^2, Re/Im conj(psi) H_K psi and
+// Re/Im |psi|^2 V are formed in FP32 (a fused multiply-add pair each, within a few 2^-24
+// of the site's terms, below the FP32 field's own rounding) and accumulated across
+// sites in compensated (FP64-equivalent) sums: five additions per site instead of eight
+// exact products.
 template <>
 struct CheckSums<float> {
-  Acc<float> n, er, ei;
+  Acc<float> n, kr, ki, vr, vi;
   __device__ __forceinline__ void add(cpx<float> p, cpx<float> h, cpx<float> v) {
     const float w = __fmaf_rn(p.x, p.x, __fmul_rn(p.y, p.y));
     n.add(w);
-    er.add(__fmaf_rn(p.x, h.x, __fmaf_rn(p.y, h.y, __fmul_rn(w, v.x))));
-    ei.add(__fmaf_rn(p.x, h.y, __fmaf_rn(-p.y, h.x, __fmul_rn(w, v.y))));
+    kr.add(__fmaf_rn(p.x, h.x, __fmul_rn(p.y, h.y)));
+    ki.add(__fmaf_rn(p.x, h.y, __fmul_rn(-p.y, h.x)));
+    vr.add(__fmul_rn(w, v.x));
+    vi.add(__fmul_rn(w, v.y));
   }
   __device__ __forceinline__ void to(double (&s)[kNumSums]) const {
     s[0] = n.value();
-    s[1] = er.value();
-    s[2] = ei.value();
-    s[3] = 0.0;
-    s[4] = 0.0;
+    s[1] = kr.value();
+    s[2] = ki.value();
+    s[3] = vr.value();
+    s[4] = vi.value();
   }
 };
 

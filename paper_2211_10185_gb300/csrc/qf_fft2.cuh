@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(F2G<N>::B_THREADS, F2G<N>::B_PER_SM)
                mk<float>(0.f, 0.f));
       double acc[kNumSums];
       cs.to(acc);
-      acc[0] = acc[3] = acc[4] = 0.0;  // the norm and the potential part come from pass A
+      acc[0] = acc[3] = acc[4] = 0.0;  // norm and potential terms come from pass A
       block_sum_store<kNumSums>(acc, reinterpret_cast<double*>(tile + G::B_TILE),
                                 a.partials + (long long)(row0 + blockIdx.x) * kPartialStride);
       return;

@@ -82,6 +82,13 @@ def test_static_step_matches_the_lattice_step_twice(lib, n, kind, v_complex, wit
             e_static = complex(s[1] + s[3], s[2] + s[4]) / s[0]
             assert abs(e_static - e_ref["e"]) < 1e-5 * abs(e_ref["e"])
             assert s[0] == pytest.approx(e_ref["norm"], rel=1e-5)
+            if call == 0:
+                # the parts separately: <psi|psi> and <psi|V psi> of the input field
+                p0 = np.abs(psi0.astype(np.complex64).astype(np.complex128)) ** 2
+                v64 = v.astype(np.complex64 if v_complex else np.float32).astype(np.complex128)
+                assert s[0] == pytest.approx(p0.sum(), rel=1e-6)
+                pv = (p0 * v64).sum()
+                assert abs(complex(s[3], s[4]) - pv) < 1e-6 * abs(pv)
         scale = 1.0 / math.sqrt(e_ref["norm"])
     lat.close()
 
