@@ -4,9 +4,10 @@ Some callers cannot hand the library a workspace (no allocator of their own, mem
 already owned by a host application, or a loop that must not fail on out-of-memory);
 this entry point keeps its scratch in a fixed array inside the library instead.  The
 tests run it twice in a row on caller-owned torch tensors and check each result against
-the lattice path (qf_step_n) on the same inputs, at the smallest sizes and at the size
-cap (N = 64, where the fixed scratch is fullest), for every FFT kinetic term and for
-real and complex potentials.  This file is collected last.
+the lattice path (qf_step_n) on the same inputs, and the first step and its five sums
+against the FP64 oracle's step (Sec. 2), at the smallest sizes and at the size cap
+(N = 64, where the fixed scratch is fullest), for every FFT kinetic term and for real
+and complex potentials.  This file is collected last.
 """
 import ctypes as C
 import math
@@ -14,6 +15,8 @@ import math
 import numpy as np
 import pytest
 
+from fieldcheck import assert_field_close
+from oracle import qfdtd_oracle as O
 from paper_2211_10185_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -73,6 +76,20 @@ def test_static_step_matches_the_lattice_step_twice(lib, n, kind, v_complex, wit
         lat.step_n(1, check_every=1)
         ref_psi = lat.get_wavefunction()
         got = psi.cpu().numpy().astype(np.complex128)
+        if call == 0:
+            # the oracle's step from the same (complex-FP32) input field, no rescaling
+            p0 = psi0.astype(np.complex64).astype(np.complex128)
+            v64 = v.astype(np.complex64 if v_complex else np.float32).astype(np.complex128)
+            hk = O.apply_kinetic(p0, kind, a, m)
+            coef_a, coef_b = O.update_coefficients(v64, dtau)
+            assert_field_close(got, coef_a * p0 - coef_b * dtau * hk, 2e-6 * (1 + math.log2(n)),
+                               what=f"static step N={n}")
+            if with_sums:
+                s = sums.cpu().numpy()
+                nrm, ek, ev = O.reductions(p0, hk, v64)
+                assert s[0] == pytest.approx(nrm, rel=1e-6)
+                assert abs(complex(s[1], s[2]) - ek) < 1e-5 * abs(ek)
+                assert abs(complex(s[3], s[4]) - ev) < 1e-5 * abs(ev)
         assert _rel(got, ref_psi) < 2e-6 * (1 + math.log2(n))
         rms = np.sqrt(np.mean(np.abs(ref_psi) ** 2))
         assert np.max(np.abs(got - ref_psi)) < 2e-6 * (1 + math.log2(n)) * 8 * rms
@@ -82,13 +99,6 @@ def test_static_step_matches_the_lattice_step_twice(lib, n, kind, v_complex, wit
             e_static = complex(s[1] + s[3], s[2] + s[4]) / s[0]
             assert abs(e_static - e_ref["e"]) < 1e-5 * abs(e_ref["e"])
             assert s[0] == pytest.approx(e_ref["norm"], rel=1e-5)
-            if call == 0:
-                # the parts separately: <psi|psi> and <psi|V psi> of the input field
-                p0 = np.abs(psi0.astype(np.complex64).astype(np.complex128)) ** 2
-                v64 = v.astype(np.complex64 if v_complex else np.float32).astype(np.complex128)
-                assert s[0] == pytest.approx(p0.sum(), rel=1e-6)
-                pv = (p0 * v64).sum()
-                assert abs(complex(s[3], s[4]) - pv) < 1e-6 * abs(pv)
         scale = 1.0 / math.sqrt(e_ref["norm"])
     lat.close()
 
