@@ -585,8 +585,6 @@ def served_benchmark(n_req, cap, sizes=(32, 48, 64, 96, 128), rate=200.0, budget
     torch.cuda.synchronize()
     t64 = time.perf_counter() - t0
     # energies are compared where both solves converged (a solve stopped by the step cap
-    # reports an unconverged energy, where the two precisions' trajectories differ)
-    # energies are compared where both solves converged (a solve stopped by the step cap
     # reports an unconverged energy, where the two precisions' trajectories differ).  The
     # stopping tolerance is 1e-7 + 1e-6 |E|, so near E = 0 (kinetic and potential parts of
     # order 1 cancelling) it is absolute: relative errors are reported for |E| >= 0.05 and

@@ -570,6 +570,28 @@ def test_kinetic_energy_in_k_space_equals_real_space(kind):
 # The plateau ("saddle point") of E_i(tau), Sec. 4: the reported excited-state energy
 # ----------------------------------------------------------------------------------
 
+@pytest.mark.parametrize("cond", [1.0, 1e-6])
+def test_gram_schmidt_matches_householder_qr(cond):
+    """Sec. 1's orthogonalisation of the snapshots: the oracle's Gram-Schmidt of three
+    vectors equals the Q of a Householder QR (numpy) up to a unit phase per column, also
+    for snapshots that are nearly parallel (the excited shares of late snapshots are
+    small: third vector = first + cond x noise)."""
+    rng = np.random.default_rng(7)
+    m = 4096
+    a = rng.standard_normal((m, 3)) + 1j * rng.standard_normal((m, 3))
+    a[:, 2] = a[:, 0] + cond * (rng.standard_normal(m) + 1j * rng.standard_normal(m))
+    basis = O.gram_schmidt([a[:, j] for j in range(3)])
+    q, r = np.linalg.qr(a)
+    g = np.stack(basis, axis=1)
+    assert np.abs(g.conj().T @ g - np.eye(3)).max() < 1e-12
+    for j in range(3):
+        overlap = np.vdot(q[:, j], g[:, j])
+        assert abs(abs(overlap) - 1) < 1e-10, (j, overlap)
+        # each v_j lies in the span of the first j + 1 vectors (triangular structure)
+        coef = np.linalg.lstsq(a[:, : j + 1], g[:, j], rcond=None)[0]
+        assert np.linalg.norm(a[:, : j + 1] @ coef - g[:, j]) < 1e-9
+
+
 def test_plateau_index_on_hand_made_sequences():
     # differences 2, .5, .1, .05, 6.55: the flattest step ends at index 4
     assert O.plateau_index([5.0, 3.0, 2.5, 2.4, 2.45, 9.0]) == 4
