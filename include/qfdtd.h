@@ -228,14 +228,17 @@ qf_status qf_use_graphs(qf_lattice* lat, int enable);
  * any captured graphs. */
 qf_status qf_use_two_pass_fft(qf_lattice* lat, int enable);
 
-/* Tile choice of the complex-FP32 four-pass FFT kernels for lattice size n (no
- * counterpart in the paper; every size, N = 128 and 256 when their four-pass form is
- * selected).  Variant 0 tiles
- * about 4096 elements per block with up to 16 contiguous columns; variant 1 half of both
- * (more, smaller blocks per SM).  Both compute the same transforms (the fields agree
- * bitwise; reductions may differ in their last bits).  variant -1, the default, lets the
- * autotuner time both on the first FFT step of a lattice of that size and keep the
- * faster for the process; 0 or 1 fixes it (process-wide, affects every handle).
+/* Tile and radix-plan choice of the complex-FP32 four-pass FFT kernels for lattice size n
+ * (no counterpart in the paper; every size, N = 128 and 256 when their four-pass form is
+ * selected).  Variant 0 tiles about 4096 elements per block with up to 16 contiguous
+ * columns; variant 1 half of both (more, smaller blocks per SM); the two compute the same
+ * transforms (the fields agree bitwise; reductions may differ in their last bits).
+ * Variants 2 and 3 are variants 0 and 1 with the size's second radix plan (a radix-16
+ * first stage and 16 elements per thread: 16 x 2 for N = 32, 16 x 4 for N = 64,
+ * 16 x 8 x 4 for N = 512; other sizes have none and reject them); the fields agree with
+ * variants 0 and 1 to rounding.  variant -1, the default, lets the autotuner time every
+ * variant of the size on the first FFT step of a lattice of that size and keep the
+ * fastest for the process; 0-3 fixes it (process-wide, affects every handle).
  * qf_get_fft_tiles returns -1 while the choice is pending. */
 qf_status qf_set_fft_tiles(int n, int variant);
 qf_status qf_get_fft_tiles(int n, int* variant);

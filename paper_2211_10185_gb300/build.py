@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 LIBNAME = "libqfdtd.so"
-SOURCES = ["qf_fft_f32.cu", "qf_fft_group.cu", "qf_fft_group_t1.cu", "qf_fft_f64.cu", "qf_fft2.cu", "qf_fft2_n128.cu", "qf_stencil.cu", "qf_fields.cu", "qf_api.cu", "qf_static.cu"]
+SOURCES = ["qf_fft_f32.cu", "qf_fft_group.cu", "qf_fft_group_t1.cu", "qf_fft_group_p1.cu", "qf_fft_f64.cu", "qf_fft2.cu", "qf_fft2_n128.cu", "qf_stencil.cu", "qf_fields.cu", "qf_api.cu", "qf_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-O2",
          "-Xptxas", "-v"]

@@ -32,8 +32,6 @@ cudaError_t launch_stencil_tb_group(const StencilTbGroup& g, cudaStream_t st);
 cudaError_t launch_bounded_wait_probe(int* err, cudaStream_t st);
 template <typename R>
 cudaError_t launch_stencil_tma(const StencilTmaGroup<R>& g, cudaStream_t st);
-int fft_twiddle_count(int n);
-void fft_twiddles(int n, double* re_im);
 template <typename R>
 cudaError_t launch_pack_f64(cpx<R>* dst, const double* re, const double* im, long long n, cudaStream_t st);
 }  // namespace qf
@@ -87,7 +85,7 @@ static Layout make_layout(const qf_lattice_desc& d) {
   L.plateau = off;
   off += L.field * d.plateau_slots;
   L.tw = off;
-  off += align_up(2 * elem * (size_t)(d.n + 64));
+  off += align_up(4 * elem * (size_t)(d.n + 64));  // the tables of up to two radix plans
   L.sym = off;
   off += align_up(elem * (size_t)d.n);
   // partial sums: the largest grid of any reducing kernel
@@ -294,10 +292,14 @@ extern "C" qf_status qf_create_lattice(const qf_lattice_desc* desc, void* dev_ws
     e = cudaMemcpyAsync(lat->sc(), &init, sizeof(init), cudaMemcpyHostToDevice, lat->st);
   }
   if (e == cudaSuccess && fft_supported(desc->n)) {
-    // per-stage twiddle table exp(-2 pi i r k/(Ns R)) in the lattice precision
-    const int cnt = fft_twiddle_count(desc->n);
+    // per-stage twiddle table exp(-2 pi i r k/(Ns R)) in the lattice precision; complex-FP32
+    // lattices of sizes with a second radix plan hold its table right after the first
+    const int cnt0 = fft_twiddle_count(desc->n);
+    const int cnt1 = desc->prec == QF_PREC_C64 ? fft_twiddle_count(desc->n, 1) : 0;
+    const int cnt = cnt0 + cnt1;
     double* tw = new double[2 * (size_t)cnt + 2];
     fft_twiddles(desc->n, tw);
+    if (cnt1 > 0) fft_twiddles(desc->n, tw + 2 * (size_t)cnt0, 1);
     if (desc->prec == QF_PREC_C64) {
       float* f = new float[2 * (size_t)cnt + 2];
       for (int i = 0; i < 2 * cnt; ++i) f[i] = (float)tw[i];
@@ -615,10 +617,11 @@ static int tuned_zchunk(qf_lattice* lat) {
   return best;
 }
 
-// ---- autotuner: tile variant of the complex-FP32 four-pass FFT kernels, per N ---------
-// On the first four-pass FFT step of a size, both variants time the five passes of a step
-// (the reducing pass measuring only: psi is untouched, the scratch field is overwritten)
-// and the faster is kept for the process.  Never runs while the stream is being captured.
+// ---- autotuner: tile geometry and radix plan of the complex-FP32 four-pass FFT, per N ---
+// On the first four-pass FFT step of a size, every variant (two tile geometries, times two
+// radix plans where the size has a second one) times the five passes of a step (the
+// reducing pass measuring only: psi is untouched, the scratch field is overwritten) and
+// the fastest is kept for the process.  Never runs while the stream is being captured.
 static void tune_fft_tiles(qf_lattice* lat) {
   const int n = lat->d.n;
   if (!lat->c64() || lat->kinetic == QF_KIN_FDTD || uses_fft2(lat) || fft_tile_choice(n) >= 0) return;
@@ -636,7 +639,8 @@ static void tune_fft_tiles(qf_lattice* lat) {
   p.emit_next = 0;
   float best_ms = 1e30f;
   int best = 0;
-  for (int v = 0; v < 2; ++v) {
+  const int nvar = fft_has_alt_plan(n) ? 4 : 2;
+  for (int v = 0; v < nvar; ++v) {
     set_fft_tile_choice(n, v);
     auto step = [&] {
       cudaError_t e = cudaSuccess;
@@ -1417,7 +1421,7 @@ extern "C" qf_status qf_use_two_pass_fft(qf_lattice* lat, int enable) {
 }
 
 extern "C" qf_status qf_set_fft_tiles(int n, int variant) {
-  if (!fft_supported(n) || variant < -1 || variant > 1) return QF_EINVAL;
+  if (!fft_supported(n) || variant < -1 || variant > 3) return QF_EINVAL;
   return set_fft_tile_choice(n, variant) ? QF_OK : QF_EINVAL;
 }
 

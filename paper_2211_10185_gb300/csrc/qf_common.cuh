@@ -249,13 +249,15 @@ constexpr int kFftPasses = 5;
 // extra passes for plain transforms: forward = 0, 1, 5 (psi -> data); inverse, in place
 // on data and unnormalised = 6 (z), 3 (y), 7 (x)
 constexpr int kFftPassZForward = 5, kFftPassZInverse = 6, kFftPassXInverse = 7;
+// alt_plan false: the twiddle region holds the first radix plan's table only, so the
+// autotuner's plan choice is not used (the tile choice still is).
 template <typename R>
 cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st,
-                            int* nblocks_final);
+                            int* nblocks_final, bool alt_plan = true);
 // One pass for a group of lattices of size n sharing real/complex V and check status
 // (c64 only); each member's arguments are as launch_fft_pass would use them.
 template <typename R>
-cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st);
+cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st, bool alt_plan = true);
 // Number of blocks the reducing (final) pass of the FFT step uses for lattice size n.
 template <typename R>
 int fft_final_blocks(int n);
@@ -319,7 +321,9 @@ cudaError_t launch_momentum_finish(const unsigned long long* part, int blocks, i
 // Spectral zero-padding of an nc^3 transform into an (2 nc)^3 one (see qf_fields.cu).
 template <typename R>
 cudaError_t launch_pad_spectrum(const cpx<R>* coarse, int nc, cpx<R>* fine, double scale, cudaStream_t st);
-int fft_twiddle_count(int n);
-void fft_twiddles(int n, double* re_im);
+// Twiddle table of radix plan p (0, or 1 for the sizes that have a second plan).
+int fft_twiddle_count(int n, int p = 0);
+void fft_twiddles(int n, double* re_im, int p = 0);
+bool fft_has_alt_plan(int n);
 
 }  // namespace qf

@@ -5,7 +5,7 @@
 
 namespace qf {
 
-template cudaError_t launch_fft_pass<double>(int, int, FftPassArgs<double>, cpx<double>*, cudaStream_t, int*);
+template cudaError_t launch_fft_pass<double>(int, int, FftPassArgs<double>, cpx<double>*, cudaStream_t, int*, bool);
 template int fft_final_blocks<double>(int);
 template int fft_final_blocks_max<double>(int);
 

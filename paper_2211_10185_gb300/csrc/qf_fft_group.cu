@@ -4,7 +4,7 @@
 
 namespace qf {
 
-template cudaError_t launch_fft_group_pass<float>(int, int, const FftGroup<float>&, cudaStream_t);
-template cudaError_t launch_fft_pass<float>(int, int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*);
+template cudaError_t launch_fft_group_pass<float>(int, int, const FftGroup<float>&, cudaStream_t, bool);
+template cudaError_t launch_fft_pass<float>(int, int, FftPassArgs<float>, cpx<float>*, cudaStream_t, int*, bool);
 
 }  // namespace qf

@@ -19,14 +19,22 @@
 namespace qf {
 
 // ------------------------------------------------------------------------------------
-// Radix plans.  EPT = elements per thread = lcm of the radices.
+// Radix plans.  EPT = elements per thread = lcm of the radices.  Plan 0 is the default of
+// each size; sizes with has_alt_plan also have plan 1, a radix-16 first stage with 16
+// elements per thread (half the threads per line), which the autotuner times against
+// plan 0 (tile variants 2 and 3 below).
 // ------------------------------------------------------------------------------------
-constexpr int plan_stages(int n) {
+constexpr bool has_alt_plan(int n) { return n == 32 || n == 64 || n == 512; }
+constexpr int alt_plan_stages(int n) { return n == 32 ? 2 : n == 64 ? 2 : n == 512 ? 3 : 0; }
+constexpr int alt_plan_radix(int n, int s) {
+  return n == 32 ? (s == 0 ? 16 : 2) : n == 64 ? (s == 0 ? 16 : 4) : n == 512 ? (s == 0 ? 16 : s == 1 ? 8 : 4) : 0;
+}
+constexpr int plan_stages0(int n) {
   return n == 8 ? 1 : n == 16 ? 1 : n == 12 ? 2 : n == 24 ? 2 : n == 32 ? 2 : n == 48 ? 3
        : n == 64 ? 2 : n == 96 ? 3 : n == 128 ? 2 : n == 192 ? 3 : n == 256 ? 2 : n == 384 ? 4
        : n == 512 ? 3 : 0;
 }
-constexpr int plan_radix(int n, int s) {
+constexpr int plan_radix0(int n, int s) {
   return n == 8 ? 8
        : n == 16 ? 16
        : n == 12 ? (s == 0 ? 4 : 3)
@@ -41,18 +49,24 @@ constexpr int plan_radix(int n, int s) {
        : n == 384 ? (s == 0 ? 8 : s == 3 ? 3 : 4)
        : n == 512 ? 8 : 0;
 }
-constexpr int plan_ept(int n) {
+constexpr int plan_ept0(int n) {
   return n == 8 ? 8 : n == 16 ? 16 : n == 12 ? 12 : n == 24 ? 24 : n == 32 ? 8 : n == 48 ? 12
        : n == 64 ? 8 : n == 96 ? 24 : n == 128 ? 16 : n == 192 ? 24 : n == 256 ? 16
        : n == 384 ? 24 : n == 512 ? 8 : 0;
 }
+constexpr bool use_alt(int n, int p) { return p == 1 && has_alt_plan(n); }
+constexpr int plan_stages(int n, int p = 0) { return use_alt(n, p) ? alt_plan_stages(n) : plan_stages0(n); }
+constexpr int plan_radix(int n, int s, int p = 0) { return use_alt(n, p) ? alt_plan_radix(n, s) : plan_radix0(n, s); }
+constexpr int plan_ept(int n, int p = 0) { return use_alt(n, p) ? 16 : plan_ept0(n); }
 // product of the radices before stage s
-constexpr int plan_ns(int n, int s) { return s == 0 ? 1 : plan_ns(n, s - 1) * plan_radix(n, s - 1); }
-// offset of stage s in the per-stage twiddle table: entries [k][r-1], k < Ns, 1 <= r < R
-constexpr int plan_tw_off(int n, int s) {
-  return s == 0 ? 0 : plan_tw_off(n, s - 1) + plan_ns(n, s - 1) * (plan_radix(n, s - 1) - 1);
+constexpr int plan_ns(int n, int s, int p = 0) {
+  return s == 0 ? 1 : plan_ns(n, s - 1, p) * plan_radix(n, s - 1, p);
 }
-constexpr int plan_tw_size(int n) { return plan_tw_off(n, plan_stages(n)); }
+// offset of stage s in the per-stage twiddle table: entries [k][r-1], k < Ns, 1 <= r < R
+constexpr int plan_tw_off(int n, int s, int p = 0) {
+  return s == 0 ? 0 : plan_tw_off(n, s - 1, p) + plan_ns(n, s - 1, p) * (plan_radix(n, s - 1, p) - 1);
+}
+constexpr int plan_tw_size(int n, int p = 0) { return plan_tw_off(n, plan_stages(n, p), p); }
 
 constexpr int largest_divisor_le(int n, int cap) {
   int best = 1;
@@ -61,14 +75,16 @@ constexpr int largest_divisor_le(int n, int cap) {
   return best;
 }
 
-// Tile geometry of the four-pass kernels.  V = 0: about 4096 (FP32) / 2048 (FP64)
-// elements per tile, y/z tiles up to 16 (8) contiguous columns wide; V = 1: half the tile
-// and half the width (more, smaller blocks per SM).  The autotuner picks V per N.
+// Tile geometry of the four-pass kernels.  Bit 0 of V: 0 = about 4096 (FP32) / 2048
+// (FP64) elements per tile, y/z tiles up to 16 (8) contiguous columns wide; 1 = half the
+// tile and half the width (more, smaller blocks per SM).  Bit 1: the radix plan (PLAN).
+// The autotuner picks V per N.
 template <typename R, int N, int V = 0>
 struct Geom {
-  static constexpr int EPT = plan_ept(N);
-  static constexpr int S = plan_stages(N);
-  static constexpr int TARGET = (sizeof(R) == 4 ? 4096 : 2048) >> V;  // elements per tile
+  static constexpr int PLAN = V >> 1;
+  static constexpr int EPT = plan_ept(N, PLAN);
+  static constexpr int S = plan_stages(N, PLAN);
+  static constexpr int TARGET = (sizeof(R) == 4 ? 4096 : 2048) >> (V & 1);  // elements per tile
   // x pass: LC whole lines per block
   static constexpr int LC = largest_divisor_le(N * N, TARGET / N > 0 ? TARGET / N : 1);
   static constexpr int TL = N / EPT;                       // threads per line
@@ -76,11 +92,11 @@ struct Geom {
   static constexpr int PAD_SHIFT = sizeof(R) == 4 ? 4 : 3;  // one pad element per 128 B
   static constexpr int PL = N + (N >> PAD_SHIFT) + 1;       // padded line length
   // y/z passes: C = L contiguous columns x P outer slices
-  static constexpr int L = largest_divisor_le(N, (sizeof(R) == 4 ? 16 : 8) >> V);
+  static constexpr int L = largest_divisor_le(N, (sizeof(R) == 4 ? 16 : 8) >> (V & 1));
   static constexpr int P = largest_divisor_le(N, TARGET / (L * N) > 0 ? TARGET / (L * N) : 1);
   static constexpr int C = L * P;
   static constexpr int THREADS_S = C * N / EPT;
-  static constexpr int TW = plan_tw_size(N);
+  static constexpr int TW = plan_tw_size(N, PLAN);
   static_assert(S > 0 && EPT > 0, "unsupported N");
 };
 
@@ -200,10 +216,10 @@ __device__ __forceinline__ void dft(cpx<R>* x) {
 // One Stockham stage on the registers of one thread: EPT/RAD butterflies, butterfly b
 // of thread group g has index j = g + b * TL (TL = N/EPT threads per line).
 // ------------------------------------------------------------------------------------
-template <typename R, int N, int ST, bool INV>
-__device__ __forceinline__ void stage_compute(cpx<R> (&v)[plan_ept(N)], int g, const cpx<R>* tw_s) {
-  constexpr int EPT = plan_ept(N), RAD = plan_radix(N, ST), NS = plan_ns(N, ST), TL = N / EPT;
-  constexpr int OFF = plan_tw_off(N, ST);
+template <typename R, int N, int ST, bool INV, int PL = 0>
+__device__ __forceinline__ void stage_compute(cpx<R> (&v)[plan_ept(N, PL)], int g, const cpx<R>* tw_s) {
+  constexpr int EPT = plan_ept(N, PL), RAD = plan_radix(N, ST, PL), NS = plan_ns(N, ST, PL), TL = N / EPT;
+  constexpr int OFF = plan_tw_off(N, ST, PL);
 #pragma unroll
   for (int b = 0; b < EPT / RAD; ++b) {
     if constexpr (NS > 1) {
@@ -235,15 +251,15 @@ __device__ __forceinline__ void stage_compute(cpx<R> (&v)[plan_ept(N)], int g, c
 }
 
 // element index read by (b, r) at stage ST
-template <int N, int ST>
+template <int N, int ST, int PL = 0>
 __device__ __forceinline__ int e_in(int g, int b, int r) {
-  constexpr int EPT = plan_ept(N), RAD = plan_radix(N, ST), TL = N / EPT;
+  constexpr int EPT = plan_ept(N, PL), RAD = plan_radix(N, ST, PL), TL = N / EPT;
   return g + b * TL + r * (N / RAD);
 }
 // element index written by (b, r) at stage ST
-template <int N, int ST>
+template <int N, int ST, int PL = 0>
 __device__ __forceinline__ int e_out(int g, int b, int r) {
-  constexpr int EPT = plan_ept(N), RAD = plan_radix(N, ST), NS = plan_ns(N, ST), TL = N / EPT;
+  constexpr int EPT = plan_ept(N, PL), RAD = plan_radix(N, ST, PL), NS = plan_ns(N, ST, PL), TL = N / EPT;
   const int j = g + b * TL;
   return (j / NS) * NS * RAD + (j % NS) + r * NS;
 }
@@ -268,23 +284,24 @@ struct Tile {
 // memory (gsrc: element e of this thread's line at gsrc[e * gstride]) or shared memory;
 // stage LAST leaves its outputs in v (natural-order element e_out<N, LAST>).
 template <typename R, int N, bool STRIDED, bool INV, int ST, int LAST, int V = 0>
-__device__ __forceinline__ void run_stages(cpx<R> (&v)[plan_ept(N)], int g, const Tile<R, N, STRIDED, V>& t,
+__device__ __forceinline__ void run_stages(cpx<R> (&v)[plan_ept(N, V >> 1)], int g, const Tile<R, N, STRIDED, V>& t,
                                            const cpx<R>* tw_s) {
-  constexpr int RAD = plan_radix(N, ST);
-  constexpr int EPT = plan_ept(N);
-  stage_compute<R, N, ST, INV>(v, g, tw_s);
+  constexpr int PL = V >> 1;
+  constexpr int RAD = plan_radix(N, ST, PL);
+  constexpr int EPT = plan_ept(N, PL);
+  stage_compute<R, N, ST, INV, PL>(v, g, tw_s);
   if constexpr (ST < LAST) {
     __syncthreads();  // all reads of this stage's inputs are done
 #pragma unroll
     for (int b = 0; b < EPT / RAD; ++b)
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) t.st(e_out<N, ST>(g, b, r), v[b * RAD + r]);
+      for (int r = 0; r < RAD; ++r) t.st(e_out<N, ST, PL>(g, b, r), v[b * RAD + r]);
     __syncthreads();
-    constexpr int RN = plan_radix(N, ST + 1);
+    constexpr int RN = plan_radix(N, ST + 1, PL);
 #pragma unroll
     for (int b = 0; b < EPT / RN; ++b)
 #pragma unroll
-      for (int r = 0; r < RN; ++r) v[b * RN + r] = t.ld(e_in<N, ST + 1>(g, b, r));
+      for (int r = 0; r < RN; ++r) v[b * RN + r] = t.ld(e_in<N, ST + 1, PL>(g, b, r));
     run_stages<R, N, STRIDED, INV, ST + 1, LAST, V>(v, g, t, tw_s);
   }
 }
@@ -310,9 +327,9 @@ __device__ __forceinline__ R kin_mult(int kinetic, R sxy, R sz, R tcoef, R am2) 
 enum PassOp : int { OP_FWD = 0, OP_INV = 1, OP_MID = 2, OP_FINAL = 3, OP_FINAL_SUMS = 4, OP_SUMS = 5 };
 constexpr bool is_final(int op) { return op >= OP_FINAL; }
 
-template <typename R, int N>
+template <typename R, int N, int V = 0>
 __device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
-  for (int i = threadIdx.x; i < Geom<R, N>::TW; i += blockDim.x) tw_s[i] = tw[i];
+  for (int i = threadIdx.x; i < Geom<R, N, V>::TW; i += blockDim.x) tw_s[i] = tw[i];
 }
 
 // x pass: LC contiguous lines per block.  OP_FWD: src -> data.  OP_FINAL: data (H_K psi
@@ -321,7 +338,8 @@ __device__ __forceinline__ void load_twiddles(cpx<R>* tw_s, const cpx<R>* tw) {
 template <typename R, int N, int OP, bool VREAL, bool NEXT = false, int V = 0>
 __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bid) {
   using G = Geom<R, N, V>;
-  constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
+  constexpr int PL = G::PLAN;
+  constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0, PL), RL = plan_radix(N, S - 1, PL);
   constexpr bool FIN = is_final(OP);
   constexpr bool INV = FIN || OP == OP_INV;
   constexpr bool WRITE = (OP == OP_FINAL || OP == OP_FINAL_SUMS);
@@ -334,14 +352,14 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
   const int line = threadIdx.x / G::TL, g = threadIdx.x % G::TL;
   const long long gline = (long long)bid * G::LC + line;
   const long long base = gline * N;
-  load_twiddles<R, N>(tw_s, a.twiddle);
+  load_twiddles<R, N, V>(tw_s, a.twiddle);
 
   const cpx<R>* __restrict__ in = (OP == OP_FWD && a.src) ? a.src : a.data;
   cpx<R> v[EPT];
 #pragma unroll
   for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
-    for (int r = 0; r < R0; ++r) v[b * R0 + r] = in[base + e_in<N, 0>(g, b, r)];
+    for (int r = 0; r < R0; ++r) v[b * R0 + r] = in[base + e_in<N, 0, PL>(g, b, r)];
 
   // final pass: psi and V at the sites this thread will write (natural order)
   cpx<R> pv[FIN ? EPT : 1];
@@ -352,19 +370,19 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
 #pragma unroll
     for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) pv[b * RL + r] = psi_in[base + e_out<N, S - 1>(g, b, r)];
+      for (int r = 0; r < RL; ++r) pv[b * RL + r] = psi_in[base + e_out<N, S - 1, PL>(g, b, r)];
     if constexpr (VREAL) {
       const R* __restrict__ vr = reinterpret_cast<const R*>(a.v);
 #pragma unroll
       for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-        for (int r = 0; r < RL; ++r) vr_[b * RL + r] = vr[base + e_out<N, S - 1>(g, b, r)];
+        for (int r = 0; r < RL; ++r) vr_[b * RL + r] = vr[base + e_out<N, S - 1, PL>(g, b, r)];
     } else {
       const cpx<R>* __restrict__ vc = reinterpret_cast<const cpx<R>*>(a.v);
 #pragma unroll
       for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-        for (int r = 0; r < RL; ++r) vv[b * RL + r] = vc[base + e_out<N, S - 1>(g, b, r)];
+        for (int r = 0; r < RL; ++r) vv[b * RL + r] = vc[base + e_out<N, S - 1, PL>(g, b, r)];
     }
   }
   __syncthreads();  // twiddles visible
@@ -376,7 +394,7 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
 #pragma unroll
     for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-      for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r)] = v[b * RL + r];
+      for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1, PL>(g, b, r)] = v[b * RL + r];
   } else {
     // v = H_K psi at the sites of this line (the 1/N^3 is inside T).
     auto vat = [&](int i) { return VREAL ? mk<R>(vr_[VREAL ? i : 0], R(0)) : vv[VREAL ? 0 : i]; };
@@ -411,7 +429,7 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
             else inv = sc / (d.x * d.x + d.y * d.y);
             v[i] = cscale<R>(cmulc<R>(num, d), inv);
           }  // v[i] = psi_{t+1}
-          a.psi[base + e_out<N, S - 1>(g, b, r)] = v[i];
+          a.psi[base + e_out<N, S - 1, PL>(g, b, r)] = v[i];
         }
       if constexpr (NEXT) {
         // forward x transform of psi_{t+1} for the next step (its first pass)
@@ -420,19 +438,19 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
 #pragma unroll
           for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-            for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1>(g, b, r), v[b * RL + r]);
+            for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1, PL>(g, b, r), v[b * RL + r]);
           __syncthreads();
 #pragma unroll
           for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
-            for (int r = 0; r < R0; ++r) v[b * R0 + r] = t.ld(e_in<N, 0>(g, b, r));
+            for (int r = 0; r < R0; ++r) v[b * R0 + r] = t.ld(e_in<N, 0, PL>(g, b, r));
         }
         // (equal first and last radix: the thread already holds the first stage's inputs)
         run_stages<R, N, false, false, 0, S - 1, V>(v, g, t, tw_s);
 #pragma unroll
         for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-          for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r)] = v[b * RL + r];
+          for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1, PL>(g, b, r)] = v[b * RL + r];
       }
     }
   }
@@ -443,7 +461,8 @@ __device__ __forceinline__ void fft_x_body(const FftPassArgs<R>& a, const int bi
 template <typename R, int N, int AXIS, int OP, int V = 0>
 __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bid) {
   using G = Geom<R, N, V>;
-  constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0), RL = plan_radix(N, S - 1);
+  constexpr int PL = G::PLAN;
+  constexpr int EPT = G::EPT, S = G::S, R0 = plan_radix(N, 0, PL), RL = plan_radix(N, S - 1, PL);
   constexpr long long PSTRIDE = AXIS == 1 ? N : (long long)N * N;
   constexpr long long OSTRIDE = AXIS == 1 ? (long long)N * N : N;
   constexpr bool INV = (OP == OP_INV);
@@ -458,7 +477,7 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
   const int xb = bid % XB, ob = bid / XB;
   const int x = xb * G::L + l, o = ob * G::P + p;
   const long long base = (long long)o * OSTRIDE + x;
-  load_twiddles<R, N>(tw_s, a.twiddle);
+  load_twiddles<R, N, V>(tw_s, a.twiddle);
   if (OP == OP_MID)
     for (int i = threadIdx.x; i < N; i += blockDim.x) sym_s[i] = a.symbol[i];
 
@@ -466,7 +485,7 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
 #pragma unroll
   for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
-    for (int r = 0; r < R0; ++r) v[b * R0 + r] = a.data[base + e_in<N, 0>(g, b, r) * PSTRIDE];
+    for (int r = 0; r < R0; ++r) v[b * R0 + r] = a.data[base + e_in<N, 0, PL>(g, b, r) * PSTRIDE];
   __syncthreads();
 
   Tile<R, N, true, V> t{data_s, c};
@@ -481,7 +500,7 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
       for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
-          const int kz = e_out<N, S - 1>(g, b, r);
+          const int kz = e_out<N, S - 1, PL>(g, b, r);
           v[b * RL + r] = cscale<R>(v[b * RL + r], kin_mult<R>(a.kinetic, sxy, sym_s[kz], a.tcoef, a.am2));
         }
     } else {
@@ -489,13 +508,13 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
 #pragma unroll
       for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-        for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1>(g, b, r), v[b * RL + r]);
+        for (int r = 0; r < RL; ++r) t.st(e_out<N, S - 1, PL>(g, b, r), v[b * RL + r]);
       __syncthreads();
 #pragma unroll
       for (int b = 0; b < EPT / R0; ++b)
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
-          const int kz = e_in<N, 0>(g, b, r);
+          const int kz = e_in<N, 0, PL>(g, b, r);
           const R tm = kin_mult<R>(a.kinetic, sxy, sym_s[kz], a.tcoef, a.am2);
           v[b * R0 + r] = cscale<R>(t.ld(kz), tm);
         }
@@ -507,7 +526,7 @@ __device__ __forceinline__ void fft_s_body(const FftPassArgs<R>& a, const int bi
 #pragma unroll
   for (int b = 0; b < EPT / RL; ++b)
 #pragma unroll
-    for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1>(g, b, r) * PSTRIDE] = v[b * RL + r];
+    for (int r = 0; r < RL; ++r) a.data[base + e_out<N, S - 1, PL>(g, b, r) * PSTRIDE] = v[b * RL + r];
 }
 
 // Entry points: one lattice (arguments by value), or a group of up to kGroupMax lattices
@@ -666,11 +685,14 @@ static cudaError_t group_pass_n(int pass, const FftGroup<R>& g, cudaStream_t st)
   return cudaGetLastError();
 }
 
-// Tile variant of the complex-FP32 four-pass kernels in use for size n (0 or 1; chosen
-// by the autotuner in the C ABI, qf_fft_f32.cu holds the table) and the launcher of
-// variant 1, compiled in its own translation unit (qf_fft_group_t1.cu).
+// Tile variant of the complex-FP32 four-pass kernels in use for size n (0-3: bit 0 the
+// tile geometry, bit 1 the radix plan; chosen by the autotuner in the C ABI, qf_fft_f32.cu
+// holds the table) and the launchers of variants 1 and 2-3, compiled in translation units
+// of their own (qf_fft_group_t1.cu, qf_fft_group_p1.cu).  Variants 2 and 3 read the
+// second twiddle table, stored right after the first.
 int fft_tile_variant(int n);
 cudaError_t launch_fft_group_pass_t1(int n, int pass, const FftGroup<float>& g, cudaStream_t st);
+cudaError_t launch_fft_group_pass_p1(int n, int variant, int pass, const FftGroup<float>& g, cudaStream_t st);
 
 // Partial-sum rows of the reducing x pass for size n with tile variant V.
 template <typename R, int V>
@@ -687,10 +709,15 @@ int fft_final_blocks_v(int n) {
   }
 }
 
+// alt_plan: whether the members' twiddle regions hold the second plan's table (the
+// lattices' do; the allocation-free entry point's holds the first only).
 template <typename R>
-cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st) {
+cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStream_t st, bool alt_plan) {
   if constexpr (sizeof(R) == 4) {
-    if (fft_tile_variant(n) == 1) return launch_fft_group_pass_t1(n, pass, g, st);
+    int v = fft_tile_variant(n);
+    if (!alt_plan) v &= 1;
+    if (v >= 2) return launch_fft_group_pass_p1(n, v, pass, g, st);
+    if (v == 1) return launch_fft_group_pass_t1(n, pass, g, st);
   }
   switch (n) {
 #define QF_CASE(NN) \
@@ -709,7 +736,7 @@ cudaError_t launch_fft_group_pass(int n, int pass, const FftGroup<R>& g, cudaStr
 template <typename R>
 int fft_final_blocks(int n) {
   if constexpr (sizeof(R) == 4) {
-    if (fft_tile_variant(n) == 1) return fft_final_blocks_v<R, 1>(n);
+    if (fft_tile_variant(n) & 1) return fft_final_blocks_v<R, 1>(n);  // (the plan bit does not change it)
   }
   return fft_final_blocks_v<R, 0>(n);
 }
@@ -728,7 +755,8 @@ int fft_final_blocks_max(int n) {
 // Complex-FP32 lattices always run the grouped kernels (a lone lattice is a group of one),
 // so a lattice executes the same machine code alone and inside a batch.
 template <typename R, int N>
-static cudaError_t single_pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
+static cudaError_t single_pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaStream_t st, int* nfinal,
+                                 bool alt_plan) {
   if constexpr (sizeof(R) == 4) {
     if (nfinal) *nfinal = fft_final_blocks<R>(N);
     FftGroup<R> g;
@@ -736,18 +764,19 @@ static cudaError_t single_pass_n(int pass, FftPassArgs<R> a, cpx<R>* tmp, cudaSt
     g.a[0] = a;
     g.a[0].data = tmp;
     g.a[0].src = (pass == 0) ? a.psi : nullptr;
-    return launch_fft_group_pass<R>(N, pass, g, st);
+    return launch_fft_group_pass<R>(N, pass, g, st, alt_plan);
   } else {
     return pass_n<R, N>(pass, a, tmp, st, nfinal);
   }
 }
 
 template <typename R>
-cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal) {
+cudaError_t launch_fft_pass(int n, int pass, FftPassArgs<R> args, cpx<R>* tmp, cudaStream_t st, int* nfinal,
+                            bool alt_plan) {
   switch (n) {
 #define QF_CASE(NN) \
   case NN:          \
-    return single_pass_n<R, NN>(pass, args, tmp, st, nfinal);
+    return single_pass_n<R, NN>(pass, args, tmp, st, nfinal, alt_plan);
     QF_CASE(8) QF_CASE(12) QF_CASE(16) QF_CASE(24) QF_CASE(32) QF_CASE(48) QF_CASE(64) QF_CASE(96)
     QF_CASE(128) QF_CASE(192) QF_CASE(256) QF_CASE(384) QF_CASE(512)
 #undef QF_CASE

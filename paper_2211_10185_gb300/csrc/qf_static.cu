@@ -144,7 +144,8 @@ extern "C" qf_status qf_fft_step_static(int n, double a, int kinetic, double mas
   cpx<float>* tmp = reinterpret_cast<cpx<float>*>(base);
   int nb = 0;
   for (int pass = 0; pass < kFftPasses; ++pass)
-    if (launch_fft_pass<float>(n, pass, p, tmp, st, &nb) != cudaSuccess) return QF_ECUDA;
+    // (its twiddle scratch holds the first radix plan's table only)
+    if (launch_fft_pass<float>(n, pass, p, tmp, st, &nb, false) != cudaSuccess) return QF_ECUDA;
   if (sums) {
     if (launch_finish(partials, nb, dsc, 0, st) != cudaSuccess) return QF_ECUDA;
     if (cudaMemcpyAsync(sums, dsc->sums, kNumSums * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess)

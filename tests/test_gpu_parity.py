@@ -381,3 +381,73 @@ def test_fft_tile_variants_agree_bitwise_and_match_oracle(n):
         lib.qf_set_fft_tiles(n, old.value)
     assert np.array_equal(fields[0], fields[1])
     assert lib.qf_set_fft_tiles(10, 0) == Q.QF_EINVAL and lib.qf_set_fft_tiles(n, 2) == Q.QF_EINVAL
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_fft_radix_plans_match_oracle(n):
+    """Sizes with a second radix plan (radix-16 first stage, 16 elements per thread):
+    all four variants the autotuner chooses from (two tile geometries x two plans) step
+    like the oracle; the two tile geometries of one plan agree bitwise.  The choice is
+    put back as it was."""
+    import ctypes as C
+
+    from paper_2211_10185_gb300 import qfdtd as Q
+
+    lib = Q.load()
+    old = C.c_int()
+    assert lib.qf_get_fft_tiles(n, C.byref(old)) == Q.QF_OK
+    a, m = 0.2, 1.3
+    v = I.cornell(n, a, 0.5, 0.2) - 0.03j * np.abs(I.cornell(n, a, 0.5, 0.2))
+    fields = []
+    try:
+        for variant in range(4):
+            assert lib.qf_set_fft_tiles(n, variant) == Q.QF_OK
+            ref, gpu = _pair(n, a, O.FFT_SYMANZIK, m, "c64", v, seed=n + 9)
+            gpu.use_two_pass_fft(False)
+            ref.step_n(3, check_every=2)
+            gpu.step_n(3, check_every=2)
+            got = gpu.get_wavefunction()
+            assert_field_close(got, ref.psi, FIELD_TOL["c64"] * 3 * (1 + math.log2(n)),
+                               what=f"N={n} variant {variant}")
+            assert abs(gpu.energies()["e"] - ref.energies()["e"]) < 1e-5 * abs(ref.energies()["e"])
+            fields.append(got)
+            gpu.close()
+    finally:
+        lib.qf_set_fft_tiles(n, old.value)
+    assert np.array_equal(fields[0], fields[1]) and np.array_equal(fields[2], fields[3])
+    assert lib.qf_set_fft_tiles(n, 4) == Q.QF_EINVAL and lib.qf_set_fft_tiles(48, 2) == Q.QF_EINVAL
+
+
+def test_fft_radix_plans_agree_at_n512():
+    """N = 512 (config 4's size): the second radix plan (16 x 8 x 4) against the first
+    (8 x 8 x 8) over three steps with a check, complex potential, Eq. HK2."""
+    import ctypes as C
+
+    from paper_2211_10185_gb300 import qfdtd as Q
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    n, a = 512, 0.04
+    lib = Q.load()
+    old = C.c_int()
+    assert lib.qf_get_fft_tiles(n, C.byref(old)) == Q.QF_OK
+    v = I.cornell(n, a, 0.5, 0.2) - 0.03j * np.abs(I.cornell(n, a, 0.5, 0.2))
+    psi0 = I.gaussian_field(n, 77)
+    out = {}
+    try:
+        for variant in (0, 2, 3):
+            assert lib.qf_set_fft_tiles(n, variant) == Q.QF_OK
+            lat = Lattice(n, a, precision="c64")
+            lat.set_potential(v)
+            lat.set_kinetic(O.FFT_SYMANZIK, 1.0)
+            lat.set_wavefunction(psi0)
+            lat.step_n(3, tol=0.0, check_every=2)
+            out[variant] = (lat.get_wavefunction(), lat.energies()["e"])
+            lat.close()
+    finally:
+        lib.qf_set_fft_tiles(n, old.value)
+    f0, e0 = out[0]
+    for variant in (2, 3):
+        f, e = out[variant]
+        assert_field_close(f, f0, 2 * FIELD_TOL["c64"] * 3 * (1 + math.log2(n)), what=f"N=512 variant {variant}")
+        assert abs(e - e0) < 1e-5 * abs(e0)
+    assert np.array_equal(out[2][0], out[3][0])
