@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--served-full", action="store_true",
                     help="only the served mix, at its stated size: 2000 Poisson requests (200/s), "
                          "N in {32..256}, cap 20000 steps, 170 GB; prints one JSON line")
+    ap.add_argument("--fft-variants", action="store_true",
+                    help="only the four-pass FFT step's tile and radix-plan variants (the autotuner's "
+                         "choices), timed per size; prints one JSON line")
     return ap.parse_args()
 
 
@@ -872,9 +875,66 @@ def run_served_full(args):
     print(json.dumps(line), flush=True)
 
 
+FFT_VARIANT_SIZES = (32, 48, 64, 96, 128, 192, 384, 512)
+
+
+def run_fft_variants(args):
+    """The complex-FP32 four-pass FFT step in every variant the autotuner chooses from:
+    tile geometry 0/1, and the second radix plan (variants 2/3) where a size has one.
+    Per size and variant: a lattice (a = 16/N, Cornell kappa 0.4 sigma 0.2, Eq. HK3, m = 1,
+    four-pass form), 130 warm-up steps, then 640 steps (checks every 64, CUDA-graph replay
+    between checks) timed with CUDA events on the lattice's stream.  The autotuner's
+    choice is put back to pending afterwards."""
+    import ctypes as C
+
+    import torch
+
+    from paper_2211_10185_gb300 import build as B
+    from paper_2211_10185_gb300 import qfdtd as Q
+    from paper_2211_10185_gb300.lattice import Lattice
+
+    torch.cuda.set_device(0)
+    B.build()
+    lib = Q.load()
+    clocks = ClockSampler(torch.cuda.current_device())
+    res = {}
+    for n in FFT_VARIANT_SIZES:
+        a = 16.0 / n
+        v = I.cornell(n, a, 0.4, 0.2)
+        psi0 = np.ones((n, n, n), complex)
+        per = {}
+        for variant in range(4):
+            if lib.qf_set_fft_tiles(n, variant) != Q.QF_OK:
+                continue  # (no second radix plan for this size)
+            lat = Lattice(n, a, precision="c64", n_snap=1)
+            lat.set_potential(v)
+            lat.set_kinetic(I.FFT_REL, 1.0)
+            lat.set_wavefunction(psi0)
+            lat.use_two_pass_fft(False)
+            lat.step_n(130, tol=0.0, check_every=CHUNK, snap_every=0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(lat.stream)
+            lat.step_n(640, tol=0.0, check_every=CHUNK, snap_every=0)
+            e1.record(lat.stream)
+            torch.cuda.synchronize()
+            per[str(variant)] = e0.elapsed_time(e1) / 640 * 1e3
+            lat.close()
+        lib.qf_set_fft_tiles(n, -1)
+        res[str(n)] = {"us_per_step": per, "fastest": min(per, key=per.get)}
+    line = {"metric": "four-pass FFT step time per tile / radix-plan variant", "unit": "us/step",
+            "n_gpus": 1, "higher_is_better": False, "data": "synthetic (Cornell, constant psi0)",
+            "variants": {"0": "tile 0, plan 0", "1": "tile 1, plan 0", "2": "tile 0, plan 1",
+                         "3": "tile 1, plan 1"},
+            "results": res, "clocks": clocks.stop()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.served_full:
+    if args.fft_variants:
+        run_fft_variants(args)
+    elif args.served_full:
         run_served_full(args)
     elif args.impl == "reference":
         run_reference(args)
