@@ -6,6 +6,28 @@
 
 namespace qf {
 
+// Every radix plan the library compiles: the radices multiply to N, each divides the
+// elements per thread, and the per-stage twiddle table has N - 1 entries (the sizes
+// the lattice workspaces and the allocation-free scratch reserve).
+constexpr bool plan_valid(int n, int p) {
+  int prod = 1;
+  for (int s = 0; s < plan_stages(n, p); ++s) {
+    const int r = plan_radix(n, s, p);
+    if (r < 2 || plan_ept(n, p) % r != 0) return false;
+    prod *= r;
+  }
+  return plan_stages(n, p) > 0 && prod == n && plan_tw_size(n, p) == n - 1;
+}
+constexpr bool all_plans_valid() {
+  constexpr int sizes[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
+  for (int n : sizes) {
+    if (!plan_valid(n, 0)) return false;
+    if (has_alt_plan(n) && (!plan_valid(n, 1) || plan_ept(n, 1) != 16 || plan_radix(n, 0, 1) != 16)) return false;
+  }
+  return true;
+}
+static_assert(all_plans_valid(), "radix plans");
+
 template <int N>
 static cudaError_t p1_pass(int variant, int pass, const FftGroup<float>& g, cudaStream_t st) {
   static_assert(has_alt_plan(N), "no second plan for this size");
