@@ -66,3 +66,26 @@ def test_null_arguments_fail_without_touching_the_gpu(lib):
     assert lib.qf_destroy_lattice(None) == Q.QF_OK
     assert lib.qf_step_n(None, 1, 0.0, 1, 1, None) == Q.QF_EINVAL
     assert lib.qf_last_error(None) == b"null handle"
+
+
+def test_fft_variant_choice_is_host_state(lib):
+    """qf_set_fft_tiles / qf_get_fft_tiles (no GPU involved): tile variants 0 and 1 for
+    every FFT size, the radix-plan variants 2 and 3 only for the sizes with a second plan
+    (32, 64, 512), -1 back to pending; other sizes and values are rejected.  Each choice
+    is put back as it was."""
+    v = C.c_int()
+    for n in (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512):
+        assert lib.qf_get_fft_tiles(n, C.byref(v)) == Q.QF_OK
+        old = v.value
+        try:
+            for var in (0, 1, -1):
+                assert lib.qf_set_fft_tiles(n, var) == Q.QF_OK
+                assert lib.qf_get_fft_tiles(n, C.byref(v)) == Q.QF_OK and v.value == var
+            for var in (2, 3):
+                want = Q.QF_OK if n in (32, 64, 512) else Q.QF_EINVAL
+                assert lib.qf_set_fft_tiles(n, var) == want, (n, var)
+            assert lib.qf_set_fft_tiles(n, 4) == Q.QF_EINVAL and lib.qf_set_fft_tiles(n, -2) == Q.QF_EINVAL
+        finally:
+            lib.qf_set_fft_tiles(n, old)
+    assert lib.qf_set_fft_tiles(10, 0) == Q.QF_EINVAL
+    assert lib.qf_get_fft_tiles(10, C.byref(v)) == Q.QF_EINVAL
